@@ -975,11 +975,17 @@ void or_reset_average(or_state* S)
     S->navg = 0;
 }
 
+/* total mass sum_x sum_i f_i, with Neumaier's compensated summation so that
+   the rounding of the 19N-term sum stays below the invariants it checks */
 double or_mass(const or_state* S)
 {
-    double m = 0.0;
-    for (size_t k = 0; k < (size_t)S->L.q * S->N; ++k) m += S->f[k];
-    return m;
+    double s = 0.0, comp = 0.0;
+    for (size_t k = 0; k < (size_t)S->L.q * S->N; ++k) {
+        double v = S->f[k], t = s + v;
+        comp += fabs(s) >= fabs(v) ? (s - t) + v : (v - t) + s;
+        s = t;
+    }
+    return s + comp;
 }
 
 /* geometry of the last porosity update: phi (binary32), d, flags, tag */
