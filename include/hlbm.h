@@ -1,0 +1,221 @@
+/*
+ * hlbm.h -- C ABI of the B300 (sm_103a) homogenized lattice Boltzmann rotor
+ * library: wall-modelled LES of rotating blades with the hybrid
+ * recursive-regularized collision (HHRRLBM-LES) of arXiv 2510.13726.
+ *
+ * The calls follow the statement of the problem in the paper: a lattice
+ * (Sec. 2.2), rotors given by a voxelised reference grid and prescribed
+ * rotation (Sec. 3.1), the time loop of the listing "HHRRLBM-FSI" (Sec. 3.2),
+ * and the per-rotor integral forces (Sec. 2.2.2).
+ *
+ * Conventions
+ *  - Lattice units: spacing 1, time step 1, cs^2 = 1/3.  Cells (x, y, z) with
+ *    x fastest in memory; cell index = (z * ny + y) * nx + x.
+ *  - Ownership: the caller allocates every device buffer (workspace, outputs,
+ *    state snapshots) and keeps it alive while the handle uses it.  The handle
+ *    itself is a small host object released by hl_destroy.  Host arrays passed
+ *    in (blade grid, inflow modes) are copied during the call.
+ *  - Streams: every device operation runs on the stream given to
+ *    hl_lattice_init (a cudaStream_t passed as void*; NULL = legacy default).
+ *  - Errors: every call returns an hl_status; none aborts, traps or exits.
+ *    hl_last_error() describes the last failure of a handle.
+ *  - Not thread-safe: one handle must not be used from two threads at once.
+ */
+#ifndef HLBM_H
+#define HLBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hl_lattice hl_lattice;
+
+typedef int hl_status;
+#define HL_OK 0
+#define HL_ERR_ARG (-1)         /* invalid argument or unsupported combination */
+#define HL_ERR_CUDA (-2)        /* a CUDA runtime call failed (see hl_last_error) */
+#define HL_ERR_NONFINITE (-3)   /* a non-finite density appeared on the device */
+#define HL_ERR_WORKSPACE (-4)   /* workspace or buffer smaller than required */
+#define HL_ERR_STATE (-5)       /* call not valid in the current state */
+#define HL_ERR_MASS (-8)        /* total mass drifted beyond mass_tol */
+
+#define HL_STORE_F32 0          /* populations stored as FP32 of f_i - w_i */
+#define HL_STORE_F16S 1         /* populations stored as FP16 of f_i - w_i */
+#define HL_STORE_BF16S 2        /* populations stored as BF16 of f_i - w_i */
+
+/* Lattice and model parameters.  Fill with hl_config_defaults() first.
+ *  q               19 (D3Q19, Fig. "D3Q19") or 27 (D3Q27)
+ *  storage         HL_STORE_*; arithmetic is FP32 in every case
+ *  flow_axis       streamwise axis 0/1/2; with open_boundaries the inlet is
+ *                  the plane at index 0 and the outlet the last plane
+ *  open_boundaries 1: equilibrium inlet (u_in + turbulence) and equilibrium
+ *                  outlet (velocity of the upstream neighbour of the previous
+ *                  step) on flow_axis, periodic laterally; 0: fully periodic
+ *  tau_mo, c_smag  molecular relaxation time and Smagorinsky constant,
+ *                  Eqs. (turbVisc), (tauEff)
+ *  u_in            inflow speed along +flow_axis (the initial state is the
+ *                  equilibrium at this velocity)
+ *  sigma_band      hybridisation factor of non-wall band cells (only 1.0 is
+ *                  supported: the finite-difference strain is provided on
+ *                  wall cells by the wall model)
+ *  eps_h           width of the porosity transition (Definition "Lattice Porosity")
+ *  transition      0 smoothstep t^2 (3 - 2t), 1 linear s = phi/eps + 1/2
+ *  wall_model      1: Spalding wall function on the wall cells (Sec. 2.2.1)
+ *  wm_E, wm_kappa  Eq. (spalding) constants (9.8, 0.41)
+ *  wm_ysample      sampling distance along the wall normal (cells)
+ *  wm_tol, wm_maxit  Newton stopping rule (1e-4, 10)
+ *  n_modes, modes  synthetic inflow turbulence: host array [n_modes][9] of
+ *                  k(3), a(3), b(3); u = U a + sum a cos(k.x') + b sin(k.x'),
+ *                  x' = x - U t a
+ *  mass_check_every  every K steps an FP64 mass total is taken (0 = never)
+ *  mass_tol        relative drift of the total mass that fails the check
+ */
+typedef struct hl_config {
+    int nx, ny, nz;
+    int q;
+    int storage;
+    int flow_axis;
+    int open_boundaries;
+    double tau_mo, c_smag, u_in;
+    double sigma_band, eps_h;
+    int transition;
+    int wall_model;
+    double wm_E, wm_kappa, wm_ysample, wm_tol;
+    int wm_maxit;
+    int n_modes;
+    const double* modes;
+    int mass_check_every;
+    double mass_tol;
+} hl_config;
+
+/* A rotor: n_blades copies of one blade grid plus a hub sphere (Sec. 3.1).
+ *  center          rotor centre (lattice coordinates, may be fractional)
+ *  axis            rotation axis 0/1/2 (positive rotation right-handed about +axis)
+ *  n_blades        1..8; blade k sits at azimuth phase0 + 2 pi k / n_blades
+ *  hub_radius      hub sphere radius (0: none)
+ *  phase0          rotor angle at t = 0
+ *  sdf             host pointer, float [gz][gy][gx]: signed distance of ONE
+ *                  blade, negative inside, on a grid in the blade frame
+ *                  (R = span, T = tangential, A = axial), node (i,j,k) at
+ *                  origin + spacing * (i, j, k); copied by hl_set_rotor
+ */
+typedef struct hl_rotor_geometry {
+    double center[3];
+    int axis;
+    int n_blades;
+    double hub_radius;
+    double phase0;
+    const float* sdf;
+    int gx, gy, gz;
+    double origin[3];
+    double spacing;
+} hl_rotor_geometry;
+
+/* Default parameters (D3Q19, FP32 storage, z streamwise, open boundaries,
+ * tau_mo 0.5005, C_S 0.1, u_in 0.05, smoothstep over eps_h = 2, wall model on
+ * with E 9.8, kappa 0.41, y_s 2, tol 1e-4, 10 iterations; mass check every 100
+ * steps with 5 % tolerance).  The grid size is left at 0 and must be set. */
+void hl_config_defaults(hl_config* cfg);
+
+/* Bytes of device workspace hl_lattice_init needs for cfg.  Host only. */
+hl_status hl_workspace_size(const hl_config* cfg, size_t* bytes);
+
+/* Create a lattice in the caller's device workspace (>= hl_workspace_size,
+ * 256-byte aligned) and set the initial state f = f^eq(1, u_in a), t = 0.
+ * stream: cudaStream_t (as void*) used by every later call.  Asynchronous. */
+hl_status hl_lattice_init(hl_lattice** out, const hl_config* cfg, void* d_workspace, size_t bytes,
+                          void* stream);
+
+/* Bytes of device workspace hl_set_rotor needs for this geometry: the blade
+ * grid copy plus the band arrays of the rotor's box of cells. */
+hl_status hl_rotor_workspace_size(const hl_lattice* lat, const hl_rotor_geometry* geom, size_t* bytes);
+
+/* Add a rotor turning at omega (rad per step) with blade pitch `pitch` (rad,
+ * a rigid rotation of each blade about its span axis that increases the
+ * section angle to the rotor plane).  The rotor's box of cells (every cell
+ * the blades or the hub can reach at any angle) must lie inside the lattice,
+ * at least 4 cells from the inlet/outlet planes, and not overlap another
+ * rotor's box; otherwise HL_ERR_ARG.  At most 8 rotors. */
+hl_status hl_set_rotor(hl_lattice* lat, int* rotor_id, const hl_rotor_geometry* geom, double omega,
+                       double pitch, void* d_workspace, size_t bytes);
+
+/* Advance n time steps in the order of the listing "HHRRLBM-FSI": porosity
+ * embedding of every rotor box and wall model on the wall cells; fused
+ * collide-and-stream; momentum-exchange force and torque per rotor; evolve
+ * the rotor angle.  Then synchronises the stream and reports the device
+ * error word (HL_ERR_NONFINITE, HL_ERR_MASS; sticky until hl_load_state or
+ * hl_lattice_init). */
+hl_status hl_step(hl_lattice* lat, int n);
+
+/* As hl_step without the final synchronisation; call hl_check later. */
+hl_status hl_step_async(hl_lattice* lat, int n);
+
+/* Synchronise the stream and report the device error word. */
+hl_status hl_check(hl_lattice* lat);
+
+/* Force on each rotor (FP64, lattice units, [n_rotors][3]) from the
+ * momentum exchange of the last step, and its mean over the steps since the
+ * last reset (Sec. 2.2.2).  Thrust = F . axis.  Either pointer may be NULL.
+ * reset_avg != 0 restarts the mean after reading.  Synchronises. */
+hl_status hl_forces(hl_lattice* lat, double* F, double* F_avg, int reset_avg);
+
+/* Torque about each rotor centre, [n_rotors][3], last step and mean. */
+hl_status hl_moments(hl_lattice* lat, double* M, double* M_avg);
+
+/* Density d_rho[N] and velocity d_u[3][N] (device, FP32) of the current
+ * populations.  Values on open boundary planes are not defined by the scheme. */
+hl_status hl_fields(hl_lattice* lat, float* d_rho, float* d_u);
+
+/* Replace the state by f = f^eq(rho, u) from device arrays d_rho[N] and
+ * d_u[3][N] (either may be NULL: rho = 1, u = 0); resets t to 0. */
+hl_status hl_init_fields(hl_lattice* lat, const float* d_rho, const float* d_u);
+
+/* FP64 total mass sum_x sum_i f_i of the stored populations.  Synchronises. */
+hl_status hl_mass(hl_lattice* lat, double* mass);
+
+/* Number of steps taken since init (or since the loaded state's time). */
+hl_status hl_get_time(const hl_lattice* lat, long long* t);
+
+/* Bytes of a state snapshot, and device-to-device save / restore of the
+ * complete dynamic state (populations, outlet plane, wall-model state, force
+ * accumulators, time).  Restoring reproduces later steps bit for bit. */
+hl_status hl_state_size(const hl_lattice* lat, size_t* bytes);
+hl_status hl_save_state(hl_lattice* lat, void* d_buf, size_t bytes);
+hl_status hl_load_state(hl_lattice* lat, const void* d_buf, size_t bytes);
+
+/* Box of rotor `rotor`: lo[3] first cell, n[3] extent (host outputs). */
+hl_status hl_rotor_box(const hl_lattice* lat, int rotor, int* lo, int* n);
+
+/* Copy the rotor's band arrays of the last porosity update into device
+ * buffers of box size: porosity d (float), flags (uint8: bit 0 force cell
+ * d < 1, bit 1 wall cell), wall-model output wm (float [9][box]: modelled
+ * velocity xyz, strain xx yy zz xy xz yz), friction velocity utau (float).
+ * Any pointer may be NULL. */
+hl_status hl_rotor_band(hl_lattice* lat, int rotor, float* d_d, unsigned char* d_flags, float* d_wm,
+                        float* d_utau);
+
+/* Velocity set of the library's slot order: c[q][3] and w[q] (host). */
+hl_status hl_velocity_set(int q, int* c, double* w);
+
+/* Collide n independent cells on the device (unit checks of Eq. (hlbm)).
+ * d_g_in / d_g_out: [n][q] shifted populations f_i - w_i in the slot order
+ * of hl_velocity_set.  Band data d_d[n], d_uB[n][3], d_sigma[n],
+ * d_S[n][6] (xx yy zz xy xz yz) select the homogenized branch; pass all four
+ * NULL for the bulk branch.  Runs on `stream`; does not synchronise. */
+hl_status hl_debug_collide(int q, int n, const float* d_g_in, const float* d_d, const float* d_uB,
+                           const float* d_sigma, const float* d_S, double tau_mo, double c_smag,
+                           float* d_g_out, void* stream);
+
+/* Text of the last error of the handle (never NULL). */
+const char* hl_last_error(const hl_lattice* lat);
+
+/* Release the handle (host memory).  Device buffers stay the caller's. */
+void hl_destroy(hl_lattice* lat);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HLBM_H */

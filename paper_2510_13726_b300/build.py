@@ -1,0 +1,46 @@
+"""Build the CUDA library libhlbm.so (sm_103a) in-tree.
+
+    python -m paper_2510_13726_b300.build [--force] [--verbose]
+
+Compiles the kernels and the C ABI (include/hlbm.h) with nvcc for
+``-gencode arch=compute_103a,code=sm_103a``.  Host code keeps IEEE semantics
+(no FMA contraction) because the rotor frames are rounded on the host.
+"""
+
+from __future__ import annotations
+
+import os
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(HERE, "csrc")
+SOURCES = [os.path.join(CSRC, f) for f in ("hl_kernels.cu", "hl_api.cu")]
+HEADERS = [os.path.join(CSRC, f) for f in ("hl_device.cuh", "hl_internal.h")] + [
+    os.path.join(ROOT, "include", "hlbm.h")]
+LIB = os.path.join(HERE, "libhlbm.so")
+NVCC = os.environ.get("NVCC", "nvcc")
+
+
+def _stale() -> bool:
+    if not os.path.exists(LIB):
+        return True
+    t = os.path.getmtime(LIB)
+    return any(os.path.getmtime(p) > t for p in SOURCES + HEADERS)
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    if not force and not _stale():
+        return LIB
+    cmd = [NVCC, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
+           "-Xcompiler", "-fPIC,-ffp-contract=off", "-shared", "-I", os.path.join(ROOT, "include"),
+           "-o", LIB] + SOURCES
+    if verbose:
+        cmd += ["-Xptxas", "-v"]
+    subprocess.run(cmd, check=True)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv, verbose="--verbose" in sys.argv))

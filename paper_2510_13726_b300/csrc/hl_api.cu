@@ -1,0 +1,677 @@
+// Host side of the C ABI declared in include/hlbm.h.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "hl_internal.h"
+#include "hlbm.h"
+
+using namespace hl;
+
+namespace {
+
+constexpr size_t ALIGN = 256;
+
+size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
+
+struct Layout {
+    size_t f, uplane0, uplane1, modes, err, mpartial, mdone, mout, total;
+};
+
+int store_bytes(int storage) { return storage == HL_STORE_F32 ? 4 : 2; }
+
+long long plane_cells(const hl_config& c) {
+    const int n[3] = {c.nx, c.ny, c.nz};
+    return (long long)n[(c.flow_axis + 1) % 3] * n[(c.flow_axis + 2) % 3];
+}
+
+Layout lattice_layout(const hl_config& c) {
+    Layout L{};
+    const long long N = (long long)c.nx * c.ny * c.nz;
+    size_t o = 0;
+    L.f = o; o = align_up(o + (size_t)c.q * N * store_bytes(c.storage));
+    L.uplane0 = o; o = align_up(o + sizeof(float) * 3 * plane_cells(c));
+    L.uplane1 = o; o = align_up(o + sizeof(float) * 3 * plane_cells(c));
+    L.modes = o; o = align_up(o + sizeof(float) * 9 * (c.n_modes > 0 ? c.n_modes : 1));
+    L.err = o; o = align_up(o + sizeof(unsigned));
+    L.mpartial = o; o = align_up(o + sizeof(double) * MASS_BLOCKS);
+    L.mdone = o; o = align_up(o + sizeof(unsigned));
+    L.mout = o; o = align_up(o + sizeof(double));
+    L.total = o;
+    return L;
+}
+
+struct RotorLayout {
+    size_t sdf, d, flags, wm, utau, active, list, count, done, partial, acc, total;
+};
+
+RotorLayout rotor_layout(long long ngrid, long long box) {
+    RotorLayout L{};
+    size_t o = 0;
+    L.sdf = o; o = align_up(o + sizeof(float) * ngrid);
+    L.d = o; o = align_up(o + sizeof(float) * box);
+    L.flags = o; o = align_up(o + box);
+    L.wm = o; o = align_up(o + sizeof(float) * 9 * box);
+    L.utau = o; o = align_up(o + sizeof(float) * box);
+    L.active = o; o = align_up(o + box);
+    L.list = o; o = align_up(o + sizeof(int) * box);
+    L.count = o; o = align_up(o + sizeof(int));
+    L.done = o; o = align_up(o + sizeof(unsigned));
+    L.partial = o; o = align_up(o + sizeof(double) * 6 * FORCE_BLOCKS);
+    L.acc = o; o = align_up(o + sizeof(double) * 12);
+    L.total = o;
+    return L;
+}
+
+struct RotorHost {
+    hl_rotor_geometry geom;
+    double omega, pitch;
+    RotorDev dev;
+    char* ws;
+    RotorLayout L;
+};
+
+}  // namespace
+
+struct hl_lattice {
+    hl_config cfg;
+    long long N;
+    cudaStream_t stream;
+    char* ws;
+    Layout L;
+    void* f;
+    float* uplane[2];
+    float* modes;
+    unsigned* err;
+    double mass_ref;
+    long long t;
+    long long n_avg;
+    int nrot;
+    RotorHost rot[MAXROT];
+    char msg[256];
+};
+
+namespace {
+
+hl_status fail(hl_lattice* lat, hl_status code, const char* what) {
+    if (lat) std::snprintf(lat->msg, sizeof lat->msg, "%s", what);
+    return code;
+}
+
+hl_status cuda_fail(hl_lattice* lat, cudaError_t e, const char* where) {
+    if (lat) std::snprintf(lat->msg, sizeof lat->msg, "%s: %s", where, cudaGetErrorString(e));
+    return HL_ERR_CUDA;
+}
+
+#define HL_CUDA(lat, call)                                       \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return cuda_fail(lat, e_, #call); \
+    } while (0)
+
+bool valid_config(const hl_config* c) {
+    if (!c) return false;
+    if (c->nx < 3 || c->ny < 3 || c->nz < 3) return false;
+    if ((long long)c->nx * c->ny * c->nz > (1LL << 31) - 1) return false;
+    if (c->nx > 65535 * 128 || c->ny > 65535 || c->nz > 65535) return false;
+    if (c->q != 19 && c->q != 27) return false;
+    if (c->storage < 0 || c->storage > 2) return false;
+    if (c->flow_axis < 0 || c->flow_axis > 2) return false;
+    if (!(c->tau_mo > 0.5) || !(c->c_smag >= 0.0) || !(c->eps_h > 0.0)) return false;
+    if (c->sigma_band != 1.0) return false;
+    if (c->n_modes < 0 || (c->n_modes > 0 && !c->modes)) return false;
+    if (c->wm_maxit < 0 || c->wm_maxit > 1000 || !(c->wm_ysample > 0.0)) return false;
+    if (c->mass_check_every < 0) return false;
+    return true;
+}
+
+StepArgs make_args(const hl_lattice* lat) {
+    const hl_config& c = lat->cfg;
+    StepArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.f = lat->f;
+    a.N = lat->N;
+    a.n[0] = c.nx; a.n[1] = c.ny; a.n[2] = c.nz;
+    a.phase = (int)(lat->t & 1);
+    a.t = lat->t;
+    a.flow_axis = c.flow_axis;
+    a.open = c.open_boundaries;
+    a.tau_mo = (float)c.tau_mo;
+    a.Ksmag = (float)(18.0 * std::sqrt(2.0) * c.c_smag * c.c_smag);
+    a.u_in = (float)c.u_in;
+    a.inflow_shift = (float)(c.u_in * (double)lat->t);
+    a.eps_half = (float)(0.5 * c.eps_h);
+    a.inv_eps = (float)(1.0 / c.eps_h);
+    a.transition = c.transition;
+    a.wall_model = c.wall_model;
+    a.wmE = (float)c.wm_E;
+    a.wmK = (float)c.wm_kappa;
+    a.wmYs = (float)c.wm_ysample;
+    a.wmTol = (float)c.wm_tol;
+    a.wmMaxit = c.wm_maxit;
+    a.nu = (float)((c.tau_mo - 0.5) / 3.0);
+    a.sigma_band = (float)c.sigma_band;
+    a.modes = lat->modes;
+    a.n_modes = c.n_modes;
+    a.uplane_prev = lat->uplane[(lat->t + 1) & 1];
+    a.uplane_cur = lat->uplane[lat->t & 1];
+    a.err = lat->err;
+    a.nrot = lat->nrot;
+    for (int k = 0; k < lat->nrot; ++k) {
+        const RotorHost& R = lat->rot[k];
+        a.rot[k] = R.dev;
+        // rotor kinematics: theta = theta0 + Omega t, blade k at theta + 2 pi k / n_blades;
+        // the binary32 frames are rounded once from FP64
+        const double th = R.geom.phase0 + R.omega * (double)lat->t;
+        for (int b = 0; b < R.geom.n_blades; ++b) {
+            const double ang = th + 2.0 * M_PI * (double)b / (double)R.geom.n_blades;
+            a.rot[k].ck[b] = (float)std::cos(ang);
+            a.rot[k].sk[b] = (float)std::sin(ang);
+        }
+        a.rot[k].cp = (float)std::cos(R.pitch);
+        a.rot[k].sp = (float)std::sin(R.pitch);
+    }
+    return a;
+}
+
+double shift_mass(const hl_lattice* lat) {
+    std::vector<int> c(3 * lat->cfg.q);
+    std::vector<double> w(lat->cfg.q);
+    hl_velocity_set(lat->cfg.q, c.data(), w.data());
+    double s = 0.0;
+    for (double v : w) s += v;
+    return s * (double)lat->N;
+}
+
+hl_status compute_mass(hl_lattice* lat, double tol, double* out) {
+    MassArgs m;
+    m.f = lat->f;
+    m.count = (long long)lat->cfg.q * lat->N;
+    m.shift_mass = shift_mass(lat);
+    m.ref = lat->mass_ref;
+    m.tol = tol;
+    m.partial = reinterpret_cast<double*>(lat->ws + lat->L.mpartial);
+    m.done = reinterpret_cast<unsigned*>(lat->ws + lat->L.mdone);
+    m.out = reinterpret_cast<double*>(lat->ws + lat->L.mout);
+    m.err = lat->err;
+    HL_CUDA(lat, launch_mass(lat->cfg.q, lat->cfg.storage, m, lat->stream));
+    if (out) {
+        HL_CUDA(lat, cudaMemcpyAsync(out, m.out, sizeof(double), cudaMemcpyDeviceToHost, lat->stream));
+        HL_CUDA(lat, cudaStreamSynchronize(lat->stream));
+    }
+    return HL_OK;
+}
+
+hl_status reset_outlet_plane(hl_lattice* lat, const float u0[3]) {
+    const long long np = plane_cells(lat->cfg);
+    std::vector<float> h(3 * np);
+    for (int k = 0; k < 3; ++k)
+        for (long long p = 0; p < np; ++p) h[k * np + p] = u0[k];
+    for (int b = 0; b < 2; ++b)
+        HL_CUDA(lat, cudaMemcpyAsync(lat->uplane[b], h.data(), sizeof(float) * h.size(),
+                                     cudaMemcpyHostToDevice, lat->stream));
+    HL_CUDA(lat, cudaStreamSynchronize(lat->stream));
+    return HL_OK;
+}
+
+hl_status read_error_word(hl_lattice* lat) {
+    unsigned e = 0;
+    HL_CUDA(lat, cudaMemcpyAsync(&e, lat->err, sizeof e, cudaMemcpyDeviceToHost, lat->stream));
+    HL_CUDA(lat, cudaStreamSynchronize(lat->stream));
+    if (e & ERR_NONFINITE) return fail(lat, HL_ERR_NONFINITE, "non-finite density on the device");
+    if (e & ERR_MASS) return fail(lat, HL_ERR_MASS, "total mass drifted beyond mass_tol");
+    return HL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void hl_config_defaults(hl_config* c) {
+    if (!c) return;
+    std::memset(c, 0, sizeof *c);
+    c->q = 19;
+    c->storage = HL_STORE_F32;
+    c->flow_axis = 2;
+    c->open_boundaries = 1;
+    c->tau_mo = 0.5005;
+    c->c_smag = 0.1;
+    c->u_in = 0.05;
+    c->sigma_band = 1.0;
+    c->eps_h = 2.0;
+    c->transition = 0;
+    c->wall_model = 1;
+    c->wm_E = 9.8;
+    c->wm_kappa = 0.41;
+    c->wm_ysample = 2.0;
+    c->wm_tol = 1e-4;
+    c->wm_maxit = 10;
+    c->mass_check_every = 100;
+    c->mass_tol = 0.05;
+}
+
+hl_status hl_workspace_size(const hl_config* cfg, size_t* bytes) {
+    if (!valid_config(cfg) || !bytes) return HL_ERR_ARG;
+    *bytes = lattice_layout(*cfg).total;
+    return HL_OK;
+}
+
+hl_status hl_lattice_init(hl_lattice** out, const hl_config* cfg, void* d_workspace, size_t bytes,
+                          void* stream) {
+    if (!out || !valid_config(cfg) || !d_workspace) return HL_ERR_ARG;
+    if (reinterpret_cast<size_t>(d_workspace) % ALIGN) return HL_ERR_ARG;
+    const Layout L = lattice_layout(*cfg);
+    if (bytes < L.total) return HL_ERR_WORKSPACE;
+    hl_lattice* lat = new (std::nothrow) hl_lattice;
+    if (!lat) return HL_ERR_ARG;
+    std::memset(lat, 0, sizeof *lat);
+    lat->cfg = *cfg;
+    lat->cfg.modes = nullptr;
+    lat->N = (long long)cfg->nx * cfg->ny * cfg->nz;
+    lat->stream = static_cast<cudaStream_t>(stream);
+    lat->ws = static_cast<char*>(d_workspace);
+    lat->L = L;
+    lat->f = lat->ws + L.f;
+    lat->uplane[0] = reinterpret_cast<float*>(lat->ws + L.uplane0);
+    lat->uplane[1] = reinterpret_cast<float*>(lat->ws + L.uplane1);
+    lat->modes = reinterpret_cast<float*>(lat->ws + L.modes);
+    lat->err = reinterpret_cast<unsigned*>(lat->ws + L.err);
+    std::snprintf(lat->msg, sizeof lat->msg, "no error");
+    hl_status st;
+    if (cfg->n_modes > 0) {
+        std::vector<float> m(9 * cfg->n_modes);
+        for (size_t i = 0; i < m.size(); ++i) m[i] = (float)cfg->modes[i];
+        cudaError_t e = cudaMemcpyAsync(lat->modes, m.data(), sizeof(float) * m.size(),
+                                        cudaMemcpyHostToDevice, lat->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(lat->stream);
+        if (e != cudaSuccess) { delete lat; return HL_ERR_CUDA; }
+    }
+    cudaError_t e = cudaMemsetAsync(lat->ws + L.err, 0, L.total - L.err, lat->stream);
+    if (e != cudaSuccess) { delete lat; return HL_ERR_CUDA; }
+    float u0[3] = {0.f, 0.f, 0.f};
+    u0[cfg->flow_axis] = (float)cfg->u_in;
+    const int n[3] = {cfg->nx, cfg->ny, cfg->nz};
+    e = launch_init(cfg->q, cfg->storage, lat->f, lat->N, n, nullptr, nullptr, 0.0f, u0, lat->stream);
+    if (e != cudaSuccess) { delete lat; return HL_ERR_CUDA; }
+    if ((st = reset_outlet_plane(lat, u0)) != HL_OK) { delete lat; return st; }
+    double m0 = 0.0;
+    if ((st = compute_mass(lat, -1.0, &m0)) != HL_OK) { delete lat; return st; }
+    lat->mass_ref = m0;
+    *out = lat;
+    return HL_OK;
+}
+
+static bool rotor_box(const hl_lattice* lat, const hl_rotor_geometry* g, int lo[3], int nn[3]) {
+    const double h = g->spacing;
+    const double R0 = g->origin[0], R1 = g->origin[0] + h * (g->gx - 1);
+    const double T0 = g->origin[1], T1 = g->origin[1] + h * (g->gy - 1);
+    const double A0 = g->origin[2], A1 = g->origin[2] + h * (g->gz - 1);
+    const double rmax = std::fmax(std::fabs(R0), std::fabs(R1));
+    const double tmax = std::fmax(std::fabs(T0), std::fabs(T1));
+    const double amax = std::fmax(std::fabs(A0), std::fabs(A1));
+    const double w = std::hypot(tmax, amax);     // the pitch rotation mixes T and A
+    const double hubr = g->hub_radius > 0 ? g->hub_radius + 0.5 * lat->cfg.eps_h : 0.0;
+    const double reach_plane = std::fmax(g->n_blades > 0 ? std::hypot(rmax, w) : 0.0, hubr) + 2.0;
+    const double reach_axial = std::fmax(g->n_blades > 0 ? w : 0.0, hubr) + 2.0;
+    const int dims[3] = {lat->cfg.nx, lat->cfg.ny, lat->cfg.nz};
+    for (int k = 0; k < 3; ++k) {
+        const double r = (k == g->axis) ? reach_axial : reach_plane;
+        const int a = (int)std::floor(g->center[k] - r);
+        const int b = (int)std::ceil(g->center[k] + r);
+        const bool open = lat->cfg.open_boundaries && k == lat->cfg.flow_axis;
+        const int margin = open ? 4 : 0;
+        if (a < margin || b > dims[k] - 1 - margin) return false;
+        lo[k] = a;
+        nn[k] = b - a + 1;
+    }
+    return true;
+}
+
+static bool valid_geometry(const hl_rotor_geometry* g) {
+    if (!g) return false;
+    if (g->axis < 0 || g->axis > 2 || g->n_blades < 0 || g->n_blades > MAXBLADES) return false;
+    if (g->n_blades > 0 && (!g->sdf || g->gx < 2 || g->gy < 2 || g->gz < 2)) return false;
+    if (!(g->spacing > 0.0) || !(g->hub_radius >= 0.0)) return false;
+    if (g->n_blades == 0 && !(g->hub_radius > 0.0)) return false;
+    return true;
+}
+
+hl_status hl_rotor_workspace_size(const hl_lattice* lat, const hl_rotor_geometry* geom, size_t* bytes) {
+    if (!lat || !valid_geometry(geom) || !bytes) return HL_ERR_ARG;
+    int lo[3], nn[3];
+    if (!rotor_box(lat, geom, lo, nn)) return HL_ERR_ARG;
+    const long long box = (long long)nn[0] * nn[1] * nn[2];
+    const long long ng = geom->n_blades > 0 ? (long long)geom->gx * geom->gy * geom->gz : 1;
+    *bytes = rotor_layout(ng, box).total;
+    return HL_OK;
+}
+
+hl_status hl_set_rotor(hl_lattice* lat, int* rotor_id, const hl_rotor_geometry* geom, double omega,
+                       double pitch, void* d_workspace, size_t bytes) {
+    if (!lat) return HL_ERR_ARG;
+    if (!valid_geometry(geom) || !d_workspace || !std::isfinite(omega) || !std::isfinite(pitch))
+        return fail(lat, HL_ERR_ARG, "hl_set_rotor: invalid geometry or arguments");
+    if (reinterpret_cast<size_t>(d_workspace) % ALIGN) return fail(lat, HL_ERR_ARG, "workspace not aligned");
+    if (lat->nrot >= MAXROT) return fail(lat, HL_ERR_ARG, "too many rotors");
+    int lo[3], nn[3];
+    if (!rotor_box(lat, geom, lo, nn))
+        return fail(lat, HL_ERR_ARG, "rotor box leaves the lattice or touches an open boundary");
+    for (int k = 0; k < lat->nrot; ++k) {
+        const RotorDev& o = lat->rot[k].dev;
+        bool overlap = true;
+        for (int d = 0; d < 3; ++d)
+            if (lo[d] + nn[d] <= o.lo[d] || o.lo[d] + o.n[d] <= lo[d]) overlap = false;
+        if (overlap) return fail(lat, HL_ERR_ARG, "rotor boxes overlap");
+    }
+    const long long box = (long long)nn[0] * nn[1] * nn[2];
+    const long long ng = geom->n_blades > 0 ? (long long)geom->gx * geom->gy * geom->gz : 1;
+    const RotorLayout L = rotor_layout(ng, box);
+    if (bytes < L.total) return fail(lat, HL_ERR_WORKSPACE, "rotor workspace too small");
+    RotorHost& R = lat->rot[lat->nrot];
+    std::memset(&R, 0, sizeof R);
+    R.geom = *geom;
+    R.geom.sdf = nullptr;
+    R.omega = omega;
+    R.pitch = pitch;
+    R.ws = static_cast<char*>(d_workspace);
+    R.L = L;
+    RotorDev& D = R.dev;
+    for (int k = 0; k < 3; ++k) {
+        D.lo[k] = lo[k];
+        D.n[k] = nn[k];
+        D.cf[k] = (float)geom->center[k];
+        D.g[k] = k == 0 ? geom->gx : (k == 1 ? geom->gy : geom->gz);
+        D.origin[k] = (float)geom->origin[k];
+    }
+    if (geom->n_blades == 0) D.g[0] = D.g[1] = D.g[2] = 2;
+    D.box_cells = box;
+    D.omega = (float)omega;
+    D.axis = geom->axis;
+    D.n_blades = geom->n_blades;
+    D.hub = (float)geom->hub_radius;
+    D.inv_h = (float)(1.0 / geom->spacing);
+    D.h = (float)geom->spacing;
+    D.sdf = reinterpret_cast<const float*>(R.ws + L.sdf);
+    D.d = reinterpret_cast<float*>(R.ws + L.d);
+    D.flags = reinterpret_cast<uint8_t*>(R.ws + L.flags);
+    D.wm = reinterpret_cast<float*>(R.ws + L.wm);
+    D.utau = reinterpret_cast<float*>(R.ws + L.utau);
+    D.active = reinterpret_cast<uint8_t*>(R.ws + L.active);
+    D.list = reinterpret_cast<int*>(R.ws + L.list);
+    D.count = reinterpret_cast<int*>(R.ws + L.count);
+    D.done = reinterpret_cast<unsigned*>(R.ws + L.done);
+    D.partial = reinterpret_cast<double*>(R.ws + L.partial);
+    D.acc = reinterpret_cast<double*>(R.ws + L.acc);
+    HL_CUDA(lat, cudaMemsetAsync(R.ws, 0, L.total, lat->stream));
+    if (geom->n_blades > 0)
+        HL_CUDA(lat, cudaMemcpyAsync(R.ws + L.sdf, geom->sdf, sizeof(float) * ng, cudaMemcpyHostToDevice,
+                                     lat->stream));
+    HL_CUDA(lat, cudaStreamSynchronize(lat->stream));
+    if (rotor_id) *rotor_id = lat->nrot;
+    lat->nrot += 1;
+    return HL_OK;
+}
+
+hl_status hl_step_async(hl_lattice* lat, int n) {
+    if (!lat || n < 0) return HL_ERR_ARG;
+    const int Q = lat->cfg.q, S = lat->cfg.storage;
+    for (int s = 0; s < n; ++s) {
+        const StepArgs a = make_args(lat);
+        if (lat->nrot > 0) HL_CUDA(lat, launch_band(Q, S, a, lat->stream));
+        HL_CUDA(lat, launch_collide(Q, S, a, lat->stream));
+        if (lat->nrot > 0) HL_CUDA(lat, launch_force(Q, S, a, lat->stream));
+        lat->t += 1;
+        lat->n_avg += 1;
+        const int K = lat->cfg.mass_check_every;
+        if (K > 0 && lat->t % K == 0) {
+            hl_status st = compute_mass(lat, lat->cfg.mass_tol, nullptr);
+            if (st != HL_OK) return st;
+        }
+    }
+    return HL_OK;
+}
+
+hl_status hl_check(hl_lattice* lat) {
+    if (!lat) return HL_ERR_ARG;
+    return read_error_word(lat);
+}
+
+hl_status hl_step(hl_lattice* lat, int n) {
+    hl_status st = hl_step_async(lat, n);
+    if (st != HL_OK) return st;
+    return read_error_word(lat);
+}
+
+static hl_status read_acc(hl_lattice* lat, std::vector<double>& acc) {
+    acc.assign(12 * (size_t)lat->nrot, 0.0);
+    for (int k = 0; k < lat->nrot; ++k)
+        HL_CUDA(lat, cudaMemcpyAsync(acc.data() + 12 * k, lat->rot[k].dev.acc, 12 * sizeof(double),
+                                     cudaMemcpyDeviceToHost, lat->stream));
+    HL_CUDA(lat, cudaStreamSynchronize(lat->stream));
+    return HL_OK;
+}
+
+hl_status hl_forces(hl_lattice* lat, double* F, double* F_avg, int reset_avg) {
+    if (!lat) return HL_ERR_ARG;
+    std::vector<double> acc;
+    hl_status st = read_acc(lat, acc);
+    if (st != HL_OK) return st;
+    const double na = lat->n_avg > 0 ? (double)lat->n_avg : 1.0;
+    for (int k = 0; k < lat->nrot; ++k)
+        for (int a = 0; a < 3; ++a) {
+            if (F) F[3 * k + a] = acc[12 * k + a];
+            if (F_avg) F_avg[3 * k + a] = lat->n_avg > 0 ? acc[12 * k + 6 + a] / na : 0.0;
+        }
+    if (reset_avg) {
+        for (int k = 0; k < lat->nrot; ++k)
+            HL_CUDA(lat, cudaMemsetAsync(lat->rot[k].dev.acc + 6, 0, 6 * sizeof(double), lat->stream));
+        HL_CUDA(lat, cudaStreamSynchronize(lat->stream));
+        lat->n_avg = 0;
+    }
+    return HL_OK;
+}
+
+hl_status hl_moments(hl_lattice* lat, double* M, double* M_avg) {
+    if (!lat) return HL_ERR_ARG;
+    std::vector<double> acc;
+    hl_status st = read_acc(lat, acc);
+    if (st != HL_OK) return st;
+    const double na = lat->n_avg > 0 ? (double)lat->n_avg : 1.0;
+    for (int k = 0; k < lat->nrot; ++k)
+        for (int a = 0; a < 3; ++a) {
+            if (M) M[3 * k + a] = acc[12 * k + 3 + a];
+            if (M_avg) M_avg[3 * k + a] = lat->n_avg > 0 ? acc[12 * k + 9 + a] / na : 0.0;
+        }
+    return HL_OK;
+}
+
+hl_status hl_fields(hl_lattice* lat, float* d_rho, float* d_u) {
+    if (!lat || !d_rho || !d_u) return HL_ERR_ARG;
+    const StepArgs a = make_args(lat);
+    HL_CUDA(lat, launch_fields(lat->cfg.q, lat->cfg.storage, a, d_rho, d_u, lat->stream));
+    return HL_OK;
+}
+
+hl_status hl_init_fields(hl_lattice* lat, const float* d_rho, const float* d_u) {
+    if (!lat) return HL_ERR_ARG;
+    const float u0[3] = {0.f, 0.f, 0.f};
+    const int n[3] = {lat->cfg.nx, lat->cfg.ny, lat->cfg.nz};
+    HL_CUDA(lat, launch_init(lat->cfg.q, lat->cfg.storage, lat->f, lat->N, n, d_rho, d_u, 0.0f, u0,
+                             lat->stream));
+    lat->t = 0;
+    lat->n_avg = 0;
+    HL_CUDA(lat, cudaMemsetAsync(lat->err, 0, sizeof(unsigned), lat->stream));
+    for (int k = 0; k < lat->nrot; ++k)
+        HL_CUDA(lat, cudaMemsetAsync(lat->rot[k].dev.acc, 0, 12 * sizeof(double), lat->stream));
+    double m0 = 0.0;
+    hl_status st = compute_mass(lat, -1.0, &m0);
+    if (st != HL_OK) return st;
+    lat->mass_ref = m0;
+    return HL_OK;
+}
+
+hl_status hl_mass(hl_lattice* lat, double* mass) {
+    if (!lat || !mass) return HL_ERR_ARG;
+    return compute_mass(lat, -1.0, mass);
+}
+
+hl_status hl_get_time(const hl_lattice* lat, long long* t) {
+    if (!lat || !t) return HL_ERR_ARG;
+    *t = lat->t;
+    return HL_OK;
+}
+
+// snapshot layout: header | populations | outlet planes | per rotor: utau, active, acc
+struct StateHeader {
+    long long magic, t, n_avg, N;
+    int q, storage, nrot, pad;
+    double mass_ref;
+};
+static const long long STATE_MAGIC = 0x484c424d53544154LL;
+
+static size_t state_bytes(const hl_lattice* lat) {
+    size_t o = align_up(sizeof(StateHeader));
+    o = align_up(o + (size_t)lat->cfg.q * lat->N * store_bytes(lat->cfg.storage));
+    o = align_up(o + 2 * sizeof(float) * 3 * plane_cells(lat->cfg));
+    for (int k = 0; k < lat->nrot; ++k) {
+        const long long b = lat->rot[k].dev.box_cells;
+        o = align_up(o + sizeof(float) * b);
+        o = align_up(o + b);
+        o = align_up(o + sizeof(double) * 12);
+    }
+    return o;
+}
+
+hl_status hl_state_size(const hl_lattice* lat, size_t* bytes) {
+    if (!lat || !bytes) return HL_ERR_ARG;
+    *bytes = state_bytes(lat);
+    return HL_OK;
+}
+
+static hl_status state_copy(hl_lattice* lat, char* buf, bool save) {
+    const cudaMemcpyKind kd = cudaMemcpyDeviceToDevice;
+    size_t o = align_up(sizeof(StateHeader));
+    auto cp = [&](void* dev, size_t n) -> cudaError_t {
+        cudaError_t e = save ? cudaMemcpyAsync(buf + o, dev, n, kd, lat->stream)
+                             : cudaMemcpyAsync(dev, buf + o, n, kd, lat->stream);
+        o = align_up(o + n);
+        return e;
+    };
+    HL_CUDA(lat, cp(lat->f, (size_t)lat->cfg.q * lat->N * store_bytes(lat->cfg.storage)));
+    const size_t pb = sizeof(float) * 3 * plane_cells(lat->cfg);
+    // both outlet planes, in the order (previous, current) of the saved time
+    {
+        float* first = lat->uplane[(lat->t + 1) & 1];
+        float* second = lat->uplane[lat->t & 1];
+        cudaError_t e = save ? cudaMemcpyAsync(buf + o, first, pb, kd, lat->stream)
+                             : cudaMemcpyAsync(first, buf + o, pb, kd, lat->stream);
+        HL_CUDA(lat, e);
+        e = save ? cudaMemcpyAsync(buf + o + pb, second, pb, kd, lat->stream)
+                 : cudaMemcpyAsync(second, buf + o + pb, pb, kd, lat->stream);
+        HL_CUDA(lat, e);
+        o = align_up(o + 2 * pb);
+    }
+    for (int k = 0; k < lat->nrot; ++k) {
+        RotorDev& D = lat->rot[k].dev;
+        HL_CUDA(lat, cp(D.utau, sizeof(float) * D.box_cells));
+        HL_CUDA(lat, cp(D.active, (size_t)D.box_cells));
+        HL_CUDA(lat, cp(D.acc, sizeof(double) * 12));
+    }
+    return HL_OK;
+}
+
+hl_status hl_save_state(hl_lattice* lat, void* d_buf, size_t bytes) {
+    if (!lat || !d_buf) return HL_ERR_ARG;
+    if (bytes < state_bytes(lat)) return fail(lat, HL_ERR_WORKSPACE, "state buffer too small");
+    StateHeader h{STATE_MAGIC, lat->t, lat->n_avg, lat->N, lat->cfg.q, lat->cfg.storage, lat->nrot, 0,
+                  lat->mass_ref};
+    HL_CUDA(lat, cudaMemcpyAsync(d_buf, &h, sizeof h, cudaMemcpyHostToDevice, lat->stream));
+    hl_status st = state_copy(lat, static_cast<char*>(d_buf), true);
+    if (st != HL_OK) return st;
+    HL_CUDA(lat, cudaStreamSynchronize(lat->stream));
+    return HL_OK;
+}
+
+hl_status hl_load_state(hl_lattice* lat, const void* d_buf, size_t bytes) {
+    if (!lat || !d_buf) return HL_ERR_ARG;
+    if (bytes < state_bytes(lat)) return fail(lat, HL_ERR_WORKSPACE, "state buffer too small");
+    StateHeader h;
+    HL_CUDA(lat, cudaMemcpyAsync(&h, d_buf, sizeof h, cudaMemcpyDeviceToHost, lat->stream));
+    HL_CUDA(lat, cudaStreamSynchronize(lat->stream));
+    if (h.magic != STATE_MAGIC || h.N != lat->N || h.q != lat->cfg.q || h.storage != lat->cfg.storage ||
+        h.nrot != lat->nrot)
+        return fail(lat, HL_ERR_STATE, "state snapshot does not match this lattice");
+    lat->t = h.t;
+    lat->n_avg = h.n_avg;
+    lat->mass_ref = h.mass_ref;
+    hl_status st = state_copy(lat, const_cast<char*>(static_cast<const char*>(d_buf)), false);
+    if (st != HL_OK) return st;
+    HL_CUDA(lat, cudaMemsetAsync(lat->err, 0, sizeof(unsigned), lat->stream));
+    HL_CUDA(lat, cudaStreamSynchronize(lat->stream));
+    return HL_OK;
+}
+
+hl_status hl_rotor_box(const hl_lattice* lat, int rotor, int* lo, int* n) {
+    if (!lat || rotor < 0 || rotor >= lat->nrot || !lo || !n) return HL_ERR_ARG;
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = lat->rot[rotor].dev.lo[k];
+        n[k] = lat->rot[rotor].dev.n[k];
+    }
+    return HL_OK;
+}
+
+hl_status hl_rotor_band(hl_lattice* lat, int rotor, float* d_d, unsigned char* d_flags, float* d_wm,
+                        float* d_utau) {
+    if (!lat || rotor < 0 || rotor >= lat->nrot) return HL_ERR_ARG;
+    const RotorDev& D = lat->rot[rotor].dev;
+    const size_t b = (size_t)D.box_cells;
+    const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
+    if (d_d) HL_CUDA(lat, cudaMemcpyAsync(d_d, D.d, sizeof(float) * b, k, lat->stream));
+    if (d_flags) HL_CUDA(lat, cudaMemcpyAsync(d_flags, D.flags, b, k, lat->stream));
+    if (d_wm) HL_CUDA(lat, cudaMemcpyAsync(d_wm, D.wm, sizeof(float) * 9 * b, k, lat->stream));
+    if (d_utau) HL_CUDA(lat, cudaMemcpyAsync(d_utau, D.utau, sizeof(float) * b, k, lat->stream));
+    return HL_OK;
+}
+
+hl_status hl_velocity_set(int q, int* c, double* w) {
+    if ((q != 19 && q != 27) || !c) return HL_ERR_ARG;
+    const int P = (q - 1) / 2;
+    for (int s = 0; s < q; ++s)
+        for (int a = 0; a < 3; ++a) {
+            int v = 0;
+            if (s >= 1) {
+                const int p = s <= P ? s - 1 : s - 1 - P;
+                v = q == 19 ? Lat<19>::c[p][a] : Lat<27>::c[p][a];
+                if (s > P) v = -v;
+            }
+            c[3 * s + a] = v;
+        }
+    // exact rational weights by shell |c|^2
+    if (w)
+        for (int s = 0; s < q; ++s) {
+            const int sh = c[3 * s] * c[3 * s] + c[3 * s + 1] * c[3 * s + 1] + c[3 * s + 2] * c[3 * s + 2];
+            if (q == 19) w[s] = sh == 0 ? 1.0 / 3.0 : (sh == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
+            else w[s] = sh == 0 ? 8.0 / 27.0 : (sh == 1 ? 2.0 / 27.0 : (sh == 2 ? 1.0 / 54.0 : 1.0 / 216.0));
+        }
+    return HL_OK;
+}
+
+hl_status hl_debug_collide(int q, int n, const float* d_g_in, const float* d_d, const float* d_uB,
+                           const float* d_sigma, const float* d_S, double tau_mo, double c_smag,
+                           float* d_g_out, void* stream) {
+    if ((q != 19 && q != 27) || n < 0 || (n > 0 && (!d_g_in || !d_g_out))) return HL_ERR_ARG;
+    const bool band = d_d || d_uB || d_sigma || d_S;
+    if (band && !(d_d && d_uB && d_sigma && d_S)) return HL_ERR_ARG;
+    const float K = (float)(18.0 * std::sqrt(2.0) * c_smag * c_smag);
+    cudaError_t e = launch_debug_collide(q, n, d_g_in, d_d, d_uB, d_sigma, d_S, (float)tau_mo, K, d_g_out,
+                                         static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? HL_OK : HL_ERR_CUDA;
+}
+
+const char* hl_last_error(const hl_lattice* lat) { return lat ? lat->msg : "null handle"; }
+
+void hl_destroy(hl_lattice* lat) { delete lat; }
+
+}  // extern "C"

@@ -1,0 +1,429 @@
+// Device-side building blocks of the HHRRLBM-LES rotor step (sm_103a).
+//
+// Population slots: 0 = rest, 1..P = the P "positive" velocities c_p,
+// P+1..2P = their opposites -c_p.  Populations are stored shifted by their
+// rest weight, g_i = f_i - w_i, in FP32, FP16 or BF16; all arithmetic is FP32.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <type_traits>
+#include <utility>
+
+namespace hl {
+
+// ---------------------------------------------------------------------------
+// velocity sets (Sec. 2.2, Fig. "D3Q19"; D3Q27 is its product-lattice sibling)
+// ---------------------------------------------------------------------------
+template <int Q>
+struct Lat;
+
+template <>
+struct Lat<19> {
+    static constexpr int Q = 19, P = 9;
+    static constexpr int c[P][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {1, 1, 0}, {1, -1, 0},
+                                    {1, 0, 1}, {1, 0, -1}, {0, 1, 1}, {0, 1, -1}};
+    __host__ __device__ static constexpr float w0() { return 1.0f / 3.0f; }
+    __host__ __device__ static constexpr float wp(int p) {
+        return (c[p][0] * c[p][0] + c[p][1] * c[p][1] + c[p][2] * c[p][2]) == 1 ? 1.0f / 18.0f
+                                                                               : 1.0f / 36.0f;
+    }
+};
+
+template <>
+struct Lat<27> {
+    static constexpr int Q = 27, P = 13;
+    static constexpr int c[P][3] = {{1, 0, 0},  {0, 1, 0},  {0, 0, 1},  {1, 1, 0},  {1, -1, 0},
+                                    {1, 0, 1},  {1, 0, -1}, {0, 1, 1},  {0, 1, -1}, {1, 1, 1},
+                                    {1, 1, -1}, {1, -1, 1}, {1, -1, -1}};
+    __host__ __device__ static constexpr float w0() { return 8.0f / 27.0f; }
+    __host__ __device__ static constexpr float wp(int p) {
+        return (c[p][0] * c[p][0] + c[p][1] * c[p][1] + c[p][2] * c[p][2]) == 1   ? 2.0f / 27.0f
+               : (c[p][0] * c[p][0] + c[p][1] * c[p][1] + c[p][2] * c[p][2]) == 2 ? 1.0f / 54.0f
+                                                                                  : 1.0f / 216.0f;
+    }
+};
+
+// slot s -> velocity component a (s = 0 rest, 1..P plus, P+1..2P minus)
+template <int Q>
+__host__ __device__ constexpr int slot_c(int s, int a) {
+    return s == 0 ? 0 : (s <= Lat<Q>::P ? Lat<Q>::c[s - 1][a] : -Lat<Q>::c[s - 1 - Lat<Q>::P][a]);
+}
+template <int Q>
+__host__ __device__ constexpr int slot_opp(int s) {
+    return s == 0 ? 0 : (s <= Lat<Q>::P ? s + Lat<Q>::P : s - Lat<Q>::P);
+}
+template <int Q>
+__host__ __device__ constexpr float slot_w(int s) {
+    return s == 0 ? Lat<Q>::w0() : Lat<Q>::wp(s <= Lat<Q>::P ? s - 1 : s - 1 - Lat<Q>::P);
+}
+
+// compile-time loop: f(std::integral_constant<int, i>) for i = 0..N-1
+template <class F, int... I>
+__device__ __forceinline__ void sfor_impl(F& f, std::integer_sequence<int, I...>) {
+    (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, class F>
+__device__ __forceinline__ void sfor(F&& f) {
+    sfor_impl(f, std::make_integer_sequence<int, N>{});
+}
+
+// ---------------------------------------------------------------------------
+// population storage: FP32, or FP16/BF16 of the weight-shifted value
+// ---------------------------------------------------------------------------
+enum StoreKind { ST_F32 = 0, ST_F16S = 1, ST_BF16S = 2 };
+
+template <int S>
+struct Store;
+template <>
+struct Store<ST_F32> {
+    using T = float;
+    static __device__ __forceinline__ float ld(const T* p) { return *p; }
+    static __device__ __forceinline__ void st(T* p, float v) { *p = v; }
+};
+template <>
+struct Store<ST_F16S> {
+    using T = __half;
+    static __device__ __forceinline__ float ld(const T* p) { return __half2float(*p); }
+    static __device__ __forceinline__ void st(T* p, float v) { *p = __float2half_rn(v); }
+};
+template <>
+struct Store<ST_BF16S> {
+    using T = __nv_bfloat16;
+    static __device__ __forceinline__ float ld(const T* p) { return __bfloat162float(*p); }
+    static __device__ __forceinline__ void st(T* p, float v) { *p = __float2bfloat16_rn(v); }
+};
+
+// ---------------------------------------------------------------------------
+// local cell model, Eq. (hlbm) with the hybrid recursive-regularized
+// non-equilibrium and the third-order equilibrium (Sec. 2.2)
+// ---------------------------------------------------------------------------
+struct Band {
+    float d;       // lattice porosity, 1 = fluid
+    float uB[3];   // solid velocity + wall-model velocity
+    float sigma;   // hybridisation factor
+    float S[6];    // FD strain rate xx, yy, zz, xy, xz, yz
+};
+
+// Writes g*_i - the shifted post-collision populations - given the
+// coefficient tensors of the Hermite expansion:
+//   f*_i = w_i [ rho + 3 rho c.u + 9/2 H2:A + 9/2 H3:A3 ]
+// with A = rho u u + (1-1/tau)(sigma Pi_neq - (1-sigma) 2 cs2 rho tau S) and
+// A3 = rho u u u + (1-1/tau) sigma a1^(3).  For c in {-1,0,1}^3,
+// H2:A = sum_a c_a^2 A_aa - tr(A)/3 + 2 sum_{a<b} c_a c_b A_ab and
+// H3:A3 = sum_{a!=b} (3 c_a^2 - 1) c_b A3_aab + 6 c_x c_y c_z A3_xyz.
+template <int Q>
+__device__ __forceinline__ void assemble(float (&g)[Q], float drho, float rho, const float (&u)[3],
+                                         const float (&A)[6], const float (&M)[6], float Axyz) {
+    using L = Lat<Q>;
+    constexpr int P = L::P;
+    const float trA = A[0] + A[1] + A[2];
+    g[0] = L::w0() * (drho - 1.5f * trA);
+    const float r3 = 3.0f * rho;
+    sfor<P>([&](auto I) {
+        constexpr int p = decltype(I)::value;
+        constexpr int cx = L::c[p][0], cy = L::c[p][1], cz = L::c[p][2];
+        constexpr float w = L::wp(p);
+        // even part: rho + 9/2 H2:A
+        float h2 = -trA * (1.0f / 3.0f);
+        if constexpr (cx != 0) h2 += A[0];
+        if constexpr (cy != 0) h2 += A[1];
+        if constexpr (cz != 0) h2 += A[2];
+        if constexpr (cx * cy != 0) h2 += float(2 * cx * cy) * A[3];
+        if constexpr (cx * cz != 0) h2 += float(2 * cx * cz) * A[4];
+        if constexpr (cy * cz != 0) h2 += float(2 * cy * cz) * A[5];
+        // odd part: 3 rho c.u + 9/2 H3:A3; M = (A3_xxy, A3_yyx, A3_xxz, A3_zzx, A3_yyz, A3_zzy)
+        float cu = 0.0f;
+        if constexpr (cx != 0) cu += float(cx) * u[0];
+        if constexpr (cy != 0) cu += float(cy) * u[1];
+        if constexpr (cz != 0) cu += float(cz) * u[2];
+        float h3 = 0.0f;
+        if constexpr (cy != 0) h3 += float((3 * cx * cx - 1) * cy) * M[0];
+        if constexpr (cx != 0) h3 += float((3 * cy * cy - 1) * cx) * M[1];
+        if constexpr (cz != 0) h3 += float((3 * cx * cx - 1) * cz) * M[2];
+        if constexpr (cx != 0) h3 += float((3 * cz * cz - 1) * cx) * M[3];
+        if constexpr (cz != 0) h3 += float((3 * cy * cy - 1) * cz) * M[4];
+        if constexpr (cy != 0) h3 += float((3 * cz * cz - 1) * cy) * M[5];
+        if constexpr (Q == 27 && cx * cy * cz != 0) h3 += float(6 * cx * cy * cz) * Axyz;
+        const float E = w * (drho + 4.5f * h2);
+        const float O = w * (r3 * cu + 4.5f * h3);
+        g[1 + p] = E + O;
+        g[1 + P + p] = E - O;
+    });
+}
+
+// Shifted third-order equilibrium g^eq_i = f^eq_i(rho, u) - w_i.
+template <int Q>
+__device__ __forceinline__ void equilibrium(float (&g)[Q], float drho, const float (&u)[3]) {
+    const float rho = 1.0f + drho;
+    float A[6] = {rho * u[0] * u[0], rho * u[1] * u[1], rho * u[2] * u[2],
+                  rho * u[0] * u[1], rho * u[0] * u[2], rho * u[1] * u[2]};
+    float M[6] = {A[0] * u[1], A[1] * u[0], A[0] * u[2], A[2] * u[0], A[1] * u[2], A[2] * u[1]};
+    float Axyz = A[3] * u[2];
+    assemble<Q>(g, drho, rho, u, A, M, Axyz);
+}
+
+// One collision in place on shifted populations.  BAND selects the
+// homogenized (HLBM) branch; the bulk branch is d = 1, sigma = 1.
+// Returns rho; u_out = fluid velocity of the pre-collision state.
+template <int Q, bool BAND>
+__device__ __forceinline__ float collide(float (&g)[Q], const Band& B, float tau_mo, float Ksmag,
+                                         float (&u_out)[3]) {
+    using L = Lat<Q>;
+    constexpr int P = L::P;
+    float drho = g[0];
+    float j[3] = {0.f, 0.f, 0.f};
+    float pg[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // sum c_a c_b g: xx yy zz xy xz yz
+    sfor<P>([&](auto I) {
+        constexpr int p = decltype(I)::value;
+        constexpr int cx = L::c[p][0], cy = L::c[p][1], cz = L::c[p][2];
+        const float s = g[1 + p] + g[1 + P + p];
+        const float d = g[1 + p] - g[1 + P + p];
+        drho += s;
+        if constexpr (cx != 0) { j[0] += float(cx) * d; pg[0] += s; }
+        if constexpr (cy != 0) { j[1] += float(cy) * d; pg[1] += s; }
+        if constexpr (cz != 0) { j[2] += float(cz) * d; pg[2] += s; }
+        if constexpr (cx * cy != 0) pg[3] += float(cx * cy) * s;
+        if constexpr (cx * cz != 0) pg[4] += float(cx * cz) * s;
+        if constexpr (cy * cz != 0) pg[5] += float(cy * cz) * s;
+    });
+    const float rho = 1.0f + drho;
+    const float inv = 1.0f / rho;
+    float u[3] = {j[0] * inv, j[1] * inv, j[2] * inv};
+    u_out[0] = u[0]; u_out[1] = u[1]; u_out[2] = u[2];
+    // non-equilibrium stress Pi_neq = Pi - rho cs2 I - rho u u (fluid velocity)
+    const float dr3 = drho * (1.0f / 3.0f);
+    float N[6] = {pg[0] - dr3 - j[0] * u[0], pg[1] - dr3 - j[1] * u[1], pg[2] - dr3 - j[2] * u[2],
+                  pg[3] - j[0] * u[1],       pg[4] - j[0] * u[2],       pg[5] - j[1] * u[2]};
+    // Smagorinsky, Eqs. (turbVisc), (tauEff): positive root of
+    // tau = tau_mo + 3 C_S^2 |S|, S = -Pi_neq / (2 rho cs2 tau)
+    const float Qn = N[0] * N[0] + N[1] * N[1] + N[2] * N[2] +
+                     2.0f * (N[3] * N[3] + N[4] * N[4] + N[5] * N[5]);
+    const float tau = 0.5f * (tau_mo + sqrtf(tau_mo * tau_mo + Ksmag * sqrtf(Qn) * inv));
+    const float om = 1.0f - 1.0f / tau;
+    float uh[3] = {u[0], u[1], u[2]};
+    float os = om;
+    float A[6];
+    if constexpr (BAND) {
+        // Eq. (convexVelocity), d = 1 in the fluid
+        const float e = 1.0f - B.d;
+        uh[0] = B.d * u[0] + e * B.uB[0];
+        uh[1] = B.d * u[1] + e * B.uB[1];
+        uh[2] = B.d * u[2] + e * B.uB[2];
+        os = om * B.sigma;
+        const float fd = om * (1.0f - B.sigma) * (2.0f / 3.0f) * rho * tau;
+        A[0] = rho * uh[0] * uh[0] + os * N[0] - fd * B.S[0];
+        A[1] = rho * uh[1] * uh[1] + os * N[1] - fd * B.S[1];
+        A[2] = rho * uh[2] * uh[2] + os * N[2] - fd * B.S[2];
+        A[3] = rho * uh[0] * uh[1] + os * N[3] - fd * B.S[3];
+        A[4] = rho * uh[0] * uh[2] + os * N[4] - fd * B.S[4];
+        A[5] = rho * uh[1] * uh[2] + os * N[5] - fd * B.S[5];
+    } else {
+        A[0] = rho * uh[0] * uh[0] + os * N[0];
+        A[1] = rho * uh[1] * uh[1] + os * N[1];
+        A[2] = rho * uh[2] * uh[2] + os * N[2];
+        A[3] = rho * uh[0] * uh[1] + os * N[3];
+        A[4] = rho * uh[0] * uh[2] + os * N[4];
+        A[5] = rho * uh[1] * uh[2] + os * N[5];
+    }
+    // third order: A3_aab = rho u_a^2 u_b + om sigma (2 u_a N_ab + u_b N_aa) (recursion with u^)
+    const float rxx = rho * uh[0] * uh[0], ryy = rho * uh[1] * uh[1], rzz = rho * uh[2] * uh[2];
+    float M[6] = {rxx * uh[1] + os * (2.0f * uh[0] * N[3] + uh[1] * N[0]),
+                  ryy * uh[0] + os * (2.0f * uh[1] * N[3] + uh[0] * N[1]),
+                  rxx * uh[2] + os * (2.0f * uh[0] * N[4] + uh[2] * N[0]),
+                  rzz * uh[0] + os * (2.0f * uh[2] * N[4] + uh[0] * N[2]),
+                  ryy * uh[2] + os * (2.0f * uh[1] * N[5] + uh[2] * N[1]),
+                  rzz * uh[1] + os * (2.0f * uh[2] * N[5] + uh[1] * N[2])};
+    float Axyz = 0.0f;
+    if constexpr (Q == 27)
+        Axyz = rho * uh[0] * uh[1] * uh[2] + os * (uh[0] * N[5] + uh[1] * N[4] + uh[2] * N[3]);
+    assemble<Q>(g, drho, rho, uh, A, M, Axyz);
+    return rho;
+}
+
+// ---------------------------------------------------------------------------
+// rotor geometry: binary32 decision value with a fixed operation order
+// (explicit round-to-nearest intrinsics, no contraction), Sec. 3.1
+// ---------------------------------------------------------------------------
+constexpr int MAXROT = 8;
+constexpr int MAXBLADES = 8;
+
+struct RotorDev {
+    int lo[3], n[3];            // box of lattice cells that may be touched
+    long long box_cells;
+    float cf[3];                // centre (binary32)
+    float omega;
+    int axis, n_blades;
+    float hub;                  // hub sphere radius
+    const float* sdf;           // blade grid [gz][gy][gx], frame (R, T, A)
+    int g[3];
+    float origin[3];
+    float inv_h, h;
+    float ck[MAXBLADES], sk[MAXBLADES], cp, sp;   // per-step frames
+    float* d;                   // [box] porosity
+    uint8_t* flags;             // [box] bit0: d<1 (force set), bit1: wall cell
+    float* wm;                  // [9][box]: du_x du_y du_z S_xx S_yy S_zz S_xy S_xz S_yz
+    float* utau;                // [box]
+    uint8_t* active;            // [box]
+    int* list;                  // [box] force cells of this step
+    int* count;                 // [1]
+    double* partial;            // [FORCE_BLOCKS][6]
+    unsigned* done;             // [1]
+    double* acc;                // F(3) M(3) | F_sum(3) M_sum(3)
+};
+
+constexpr uint8_t FL_B = 1, FL_W = 2;
+
+__device__ __forceinline__ float lerp_rn(float a, float b, float t) {
+    return __fmaf_rn(t, __fsub_rn(b, a), a);
+}
+
+__device__ __forceinline__ float blade_sample(const RotorDev& R, float pR, float qT, float qA) {
+    const float g0 = __fmul_rn(__fsub_rn(pR, R.origin[0]), R.inv_h);
+    const float g1 = __fmul_rn(__fsub_rn(qT, R.origin[1]), R.inv_h);
+    const float g2 = __fmul_rn(__fsub_rn(qA, R.origin[2]), R.inv_h);
+    const float f0 = floorf(g0), f1 = floorf(g1), f2 = floorf(g2);
+    if (!(f0 >= 0.0f && f0 <= (float)(R.g[0] - 2) && f1 >= 0.0f && f1 <= (float)(R.g[1] - 2) &&
+          f2 >= 0.0f && f2 <= (float)(R.g[2] - 2)))
+        return __int_as_float(0x7f800000);
+    const int i0 = (int)f0, j0 = (int)f1, k0 = (int)f2;
+    const float tx = __fsub_rn(g0, f0), ty = __fsub_rn(g1, f1), tz = __fsub_rn(g2, f2);
+    const long long sy = R.g[0], sz = (long long)R.g[0] * R.g[1];
+    const float* s = R.sdf + (long long)k0 * sz + (long long)j0 * sy + i0;
+    const float v00 = lerp_rn(__ldg(s), __ldg(s + 1), tx);
+    const float v10 = lerp_rn(__ldg(s + sy), __ldg(s + sy + 1), tx);
+    const float v01 = lerp_rn(__ldg(s + sz), __ldg(s + sz + 1), tx);
+    const float v11 = lerp_rn(__ldg(s + sz + sy), __ldg(s + sz + sy + 1), tx);
+    const float w0 = lerp_rn(v00, v10, ty);
+    const float w1 = lerp_rn(v01, v11, ty);
+    return lerp_rn(w0, w1, tz);
+}
+
+// Signed distance of cell (x,y,z) to the rotor; which = blade, or n_blades for the hub.
+__device__ __forceinline__ float rotor_phi(const RotorDev& R, int x, int y, int z, int& which) {
+    const float rl[3] = {__fsub_rn((float)x, R.cf[0]), __fsub_rn((float)y, R.cf[1]),
+                         __fsub_rn((float)z, R.cf[2])};
+    const int a = R.axis, b = (a + 1) % 3, c = (a + 2) % 3;
+    const float rb = rl[b], rc = rl[c], ra = rl[a];
+    float best = __int_as_float(0x7f800000);
+    which = -1;
+    for (int k = 0; k < R.n_blades; ++k) {
+        const float pR = __fmaf_rn(R.ck[k], rb, __fmul_rn(R.sk[k], rc));
+        const float pT = __fmaf_rn(R.ck[k], rc, -__fmul_rn(R.sk[k], rb));
+        const float qT = __fmaf_rn(R.cp, pT, -__fmul_rn(R.sp, ra));
+        const float qA = __fmaf_rn(R.cp, ra, __fmul_rn(R.sp, pT));
+        const float v = blade_sample(R, pR, qT, qA);
+        if (v < best) { best = v; which = k; }
+    }
+    if (R.hub > 0.0f) {
+        const float r2 = __fmaf_rn(rb, rb, __fmaf_rn(rc, rc, __fmul_rn(ra, ra)));
+        const float v = __fsub_rn(__fsqrt_rn(r2), R.hub);
+        if (v < best) { best = v; which = R.n_blades; }
+    }
+    return best;
+}
+
+// Outward unit normal (lab frame): trilinear interpolation of the grid's
+// central-difference gradient, rotated back through pitch and azimuth.
+__device__ inline void rotor_normal(const RotorDev& R, int which, int x, int y, int z, float n[3]) {
+    const int a = R.axis, b = (a + 1) % 3, c = (a + 2) % 3;
+    const float rl[3] = {(float)x - R.cf[0], (float)y - R.cf[1], (float)z - R.cf[2]};
+    float v[3];
+    if (which >= R.n_blades) {
+        v[0] = rl[0]; v[1] = rl[1]; v[2] = rl[2];
+    } else {
+        const float ck = R.ck[which], sk = R.sk[which], cp = R.cp, sp = R.sp;
+        const float rb = rl[b], rc = rl[c], ra = rl[a];
+        const float pR = ck * rb + sk * rc, pT = ck * rc - sk * rb;
+        const float qT = cp * pT - sp * ra, qA = cp * ra + sp * pT;
+        const float gg[3] = {(pR - R.origin[0]) * R.inv_h, (qT - R.origin[1]) * R.inv_h,
+                             (qA - R.origin[2]) * R.inv_h};
+        int i0[3];
+        float t[3];
+        for (int k = 0; k < 3; ++k) {
+            int f = (int)floorf(gg[k]);
+            f = f < 0 ? 0 : (f > R.g[k] - 2 ? R.g[k] - 2 : f);
+            i0[k] = f;
+            t[k] = gg[k] - (float)f;
+        }
+        float gb[3] = {0.f, 0.f, 0.f};
+        for (int cz = 0; cz < 2; ++cz)
+            for (int cy = 0; cy < 2; ++cy)
+                for (int cx = 0; cx < 2; ++cx) {
+                    const int node[3] = {i0[0] + cx, i0[1] + cy, i0[2] + cz};
+                    const float wgt = (cx ? t[0] : 1.f - t[0]) * (cy ? t[1] : 1.f - t[1]) *
+                                      (cz ? t[2] : 1.f - t[2]);
+                    for (int d = 0; d < 3; ++d) {
+                        int lo[3] = {node[0], node[1], node[2]}, hi[3] = {node[0], node[1], node[2]};
+                        lo[d] = node[d] > 0 ? node[d] - 1 : node[d];
+                        hi[d] = node[d] < R.g[d] - 1 ? node[d] + 1 : node[d];
+                        const long long olo = ((long long)lo[2] * R.g[1] + lo[1]) * R.g[0] + lo[0];
+                        const long long ohi = ((long long)hi[2] * R.g[1] + hi[1]) * R.g[0] + hi[0];
+                        gb[d] += wgt * (__ldg(R.sdf + ohi) - __ldg(R.sdf + olo)) /
+                                 ((float)(hi[d] - lo[d]) * R.h);
+                    }
+                }
+        const float vT = cp * gb[1] + sp * gb[2];
+        const float vA = -sp * gb[1] + cp * gb[2];
+        const float vR = gb[0];
+        float lab[3];
+        lab[b] = ck * vR - sk * vT;
+        lab[c] = sk * vR + ck * vT;
+        lab[a] = vA;
+        v[0] = lab[0]; v[1] = lab[1]; v[2] = lab[2];
+    }
+    const float nrm = sqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    const float inv = nrm > 0.f ? 1.0f / nrm : 0.f;
+    n[0] = v[0] * inv; n[1] = v[1] * inv; n[2] = v[2] * inv;
+}
+
+// ---------------------------------------------------------------------------
+// wall function, Sec. 2.2.1 (FP32)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float spalding_yplus(float up, float E, float kappa) {
+    const float k = kappa * up;
+    return up + (expf(k) - 1.0f - k - 0.5f * k * k - k * k * k * (1.0f / 6.0f)) / E;
+}
+__device__ __forceinline__ float spalding_dyplus(float up, float E, float kappa) {
+    const float k = kappa * up;
+    return 1.0f + kappa / E * (expf(k) - 1.0f - k - 0.5f * k * k);
+}
+
+// Newton-Raphson on Eq. (implicitWF): stop when the residual changes by less
+// than tol, at most maxit iterations; a non-positive iterate is halved.
+__device__ inline float wall_newton(float u, float y, float nu, float guess, float E, float kappa,
+                                    float tol, int maxit) {
+    float ut = guess;
+    float fv = spalding_yplus(u / ut, E, kappa) - y * ut / nu;
+    for (int it = 0; it < maxit; ++it) {
+        const float fp = -spalding_dyplus(u / ut, E, kappa) * u / (ut * ut) - y / nu;
+        float un = ut - fv / fp;
+        if (!(un > 0.0f)) un = 0.5f * ut;
+        const float fn = spalding_yplus(u / un, E, kappa) - y * un / nu;
+        ut = un;
+        if (fabsf(fn - fv) < tol) break;
+        fv = fn;
+    }
+    return ut;
+}
+
+// inverse of Eq. (spalding): u+ for y+, Newton from the right of the root
+__device__ inline float spalding_uplus(float yp, float E, float kappa, float tol, int maxit) {
+    const float lg = logf(1.0f + E * yp) / kappa;
+    float up = yp < lg ? yp : lg;
+    float g = spalding_yplus(up, E, kappa) - yp;
+    for (int it = 0; it < maxit; ++it) {
+        float un = up - g / spalding_dyplus(up, E, kappa);
+        if (!(un > 0.0f)) un = 0.5f * up;
+        const float gn = spalding_yplus(un, E, kappa) - yp;
+        up = un;
+        if (fabsf(gn - g) < tol) break;
+        g = gn;
+    }
+    return up;
+}
+
+}  // namespace hl

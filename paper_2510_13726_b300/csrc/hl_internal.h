@@ -1,0 +1,64 @@
+// Launch-side interface between the C ABI (hl_api.cu) and the kernels
+// (hl_kernels.cu).  Not part of the public header.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "hl_device.cuh"
+
+namespace hl {
+
+constexpr int FORCE_BLOCKS = 64;     // blocks per rotor in the force reduction
+constexpr int MASS_BLOCKS = 592;     // 4 x 148 SMs
+constexpr int BAND_THREADS = 256;
+
+enum ErrBits : unsigned { ERR_NONFINITE = 1u, ERR_MASS = 2u };
+
+struct StepArgs {
+    void* f;                 // populations [Q][N], storage type
+    long long N;
+    int n[3];
+    int phase;               // t & 1: AA layout of the pre-collision state
+    long long t;
+    int flow_axis, open;
+    float tau_mo, Ksmag;     // Ksmag = 18 sqrt(2) C_S^2
+    float u_in, inflow_shift;   // inflow_shift = u_in * t
+    float eps_half, inv_eps;
+    int transition, wall_model;
+    float wmE, wmK, wmYs, wmTol, nu;
+    int wmMaxit;
+    float sigma_band;
+    const float* modes;      // [n_modes][9]
+    int n_modes;
+    const float* uplane_prev;  // [3][plane]
+    float* uplane_cur;
+    unsigned* err;
+    int nrot;
+    RotorDev rot[MAXROT];
+};
+
+struct MassArgs {
+    const void* f;
+    long long count;         // Q * N stored values
+    double shift_mass;       // N * sum_i w_i (the storage shift)
+    double ref, tol;         // reference mass and allowed relative drift (tol < 0: no check)
+    double* partial;         // [MASS_BLOCKS]
+    unsigned* done;
+    double* out;
+    unsigned* err;
+};
+
+// launchers: return the launch error of the last kernel
+cudaError_t launch_band(int Q, int storage, const StepArgs& a, cudaStream_t s);
+cudaError_t launch_collide(int Q, int storage, const StepArgs& a, cudaStream_t s);
+cudaError_t launch_force(int Q, int storage, const StepArgs& a, cudaStream_t s);
+cudaError_t launch_mass(int Q, int storage, const MassArgs& m, cudaStream_t s);
+cudaError_t launch_init(int Q, int storage, void* f, long long N, const int n[3], const float* rho,
+                        const float* u, float drho0, const float u0[3], cudaStream_t s);
+cudaError_t launch_fields(int Q, int storage, const StepArgs& a, float* rho, float* u,
+                          cudaStream_t s);
+cudaError_t launch_debug_collide(int Q, int n, const float* g_in, const float* d, const float* uB,
+                                 const float* sigma, const float* S, float tau_mo, float Ksmag,
+                                 float* g_out, cudaStream_t s);
+
+}  // namespace hl

@@ -1,0 +1,643 @@
+// Kernels of the HHRRLBM-LES rotor step on B300 (sm_103a).
+//
+// Per time step (listing "HHRRLBM-FSI", Sec. 3.2), on one stream:
+//   band_kernel     porosity embedding of the rotor boxes + wall model on the
+//                   wall cells + list of force cells          (Sec. 2.2.1/2.2.2/3.1)
+//   collide_kernel  fused collide-and-stream, single-buffer AA pattern,
+//                   bulk (RRLBM-LES) and band (HHRRLBM-LES) branches,
+//                   equilibrium inlet/outlet planes            (Eq. (hlbm))
+//   force_kernel    momentum exchange over the force cells, FP64 block
+//                   reduction, deterministic last-block combine (Sec. 2.2.2)
+//   mass_kernel     (every K steps) FP64 mass total + non-finite check
+//
+// AA pattern: with phase p = t & 1 of the step,
+//   p = 0: f_i(x) is read from slot i of x, f*_i(x) written to slot ibar of x;
+//   p = 1: f_i(x) is read from slot ibar of x - c_i, f*_i(x) written to slot i
+//          of x + c_i.
+// Every memory location is read and written by the same thread, so one
+// buffer suffices and no synchronisation is needed inside the kernel.
+#include "hl_internal.h"
+
+namespace hl {
+
+// index contributions of the three neighbours (-1, 0, +1) along each axis;
+// an open (inlet/outlet) face has no neighbour beyond it
+struct Nbr {
+    long long off[3][3];
+    bool ok[3][3];
+};
+
+__device__ __forceinline__ void make_nbr(const StepArgs& a, int x, int y, int z, Nbr& nb) {
+    const int v[3] = {x, y, z};
+    const long long stride[3] = {1, a.n[0], (long long)a.n[0] * a.n[1]};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const bool op = a.open && k == a.flow_axis;
+        const int n = a.n[k];
+        int m = v[k] - 1, p = v[k] + 1;
+        nb.ok[k][0] = true;
+        nb.ok[k][2] = true;
+        nb.ok[k][1] = true;
+        if (m < 0) { if (op) { nb.ok[k][0] = false; m = v[k]; } else m = n - 1; }
+        if (p >= n) { if (op) { nb.ok[k][2] = false; p = v[k]; } else p = 0; }
+        nb.off[k][0] = m * stride[k];
+        nb.off[k][1] = (long long)v[k] * stride[k];
+        nb.off[k][2] = p * stride[k];
+    }
+}
+
+template <int Q, int s, int sign>
+__device__ __forceinline__ long long nbr_index(const Nbr& nb, bool& ok) {
+    constexpr int cx = sign * slot_c<Q>(s, 0), cy = sign * slot_c<Q>(s, 1), cz = sign * slot_c<Q>(s, 2);
+    ok = nb.ok[0][cx + 1] && nb.ok[1][cy + 1] && nb.ok[2][cz + 1];
+    return nb.off[0][cx + 1] + nb.off[1][cy + 1] + nb.off[2][cz + 1];
+}
+
+// pre-collision populations of a cell in the layout of phase p
+template <int Q, int S>
+__device__ __forceinline__ void load_pre(const StepArgs& a, long long cell, const Nbr& nb, float (&g)[Q]) {
+    using T = typename Store<S>::T;
+    const T* f = static_cast<const T*>(a.f);
+    if (a.phase == 0) {
+        sfor<Q>([&](auto I) {
+            constexpr int s = decltype(I)::value;
+            g[s] = Store<S>::ld(f + (long long)s * a.N + cell);
+        });
+    } else {
+        sfor<Q>([&](auto I) {
+            constexpr int s = decltype(I)::value;
+            constexpr int o = slot_opp<Q>(s);
+            bool ok;
+            long long src = nbr_index<Q, s, -1>(nb, ok);
+            if (!ok) src = cell;   // enters through an open face: undefined, keep finite
+            g[s] = Store<S>::ld(f + (long long)o * a.N + src);
+        });
+    }
+}
+
+__device__ __forceinline__ void solid_velocity(const RotorDev& R, int x, int y, int z, float us[3]) {
+    const float r[3] = {(float)x - R.cf[0], (float)y - R.cf[1], (float)z - R.cf[2]};
+    const int ax = R.axis, b = (ax + 1) % 3, c = (ax + 2) % 3;
+    us[ax] = 0.0f;
+    us[b] = -R.omega * r[c];
+    us[c] = R.omega * r[b];
+}
+
+// ---------------------------------------------------------------------------
+// fused collide and stream
+// ---------------------------------------------------------------------------
+template <int Q, int S>
+__global__ void __launch_bounds__(128) collide_kernel(const StepArgs a) {
+    using T = typename Store<S>::T;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= a.n[0] || y >= a.n[1]) return;
+    const long long cell = ((long long)z * a.n[1] + y) * a.n[0] + x;
+    const int xi[3] = {x, y, z};
+    const int ax = a.flow_axis, bx = (ax + 1) % 3, cxs = (ax + 2) % 3;
+    const int ca = xi[ax];
+    const bool inlet = a.open && ca == 0;
+    const bool outlet = a.open && ca == a.n[ax] - 1;
+    Nbr nb;
+    make_nbr(a, x, y, z, nb);
+    float g[Q];
+    if (!inlet && !outlet) {
+        load_pre<Q, S>(a, cell, nb, g);
+        int rk = -1;
+        long long bi = 0;
+        for (int k = 0; k < a.nrot; ++k) {
+            const RotorDev& R = a.rot[k];
+            const unsigned dx = (unsigned)(x - R.lo[0]), dy = (unsigned)(y - R.lo[1]),
+                           dz = (unsigned)(z - R.lo[2]);
+            if (dx < (unsigned)R.n[0] && dy < (unsigned)R.n[1] && dz < (unsigned)R.n[2]) {
+                rk = k;
+                bi = ((long long)dz * R.n[1] + dy) * R.n[0] + dx;
+                break;
+            }
+        }
+        float u[3];
+        float rho;
+        if (rk >= 0) {
+            const RotorDev& R = a.rot[rk];
+            Band B;
+            B.d = R.d[bi];
+            const uint8_t fl = R.flags[bi];
+            solid_velocity(R, x, y, z, B.uB);
+            B.sigma = a.sigma_band;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) B.S[k] = 0.0f;
+            if (a.wall_model && (fl & FL_W)) {
+                const float* wm = R.wm + bi;
+                B.uB[0] += wm[0];
+                B.uB[1] += wm[R.box_cells];
+                B.uB[2] += wm[2 * R.box_cells];
+#pragma unroll
+                for (int k = 0; k < 6; ++k) B.S[k] = wm[(3 + k) * R.box_cells];
+                B.sigma = 0.0f;
+            }
+            rho = collide<Q, true>(g, B, a.tau_mo, a.Ksmag, u);
+        } else {
+            Band B0;
+            rho = collide<Q, false>(g, B0, a.tau_mo, a.Ksmag, u);
+        }
+        if (!(fabsf(rho) < 1e30f)) atomicOr(a.err, ERR_NONFINITE);
+        if (a.open && ca == a.n[ax] - 2) {
+            const long long np = (long long)a.n[bx] * a.n[cxs];
+            const long long pl = (long long)xi[cxs] * a.n[bx] + xi[bx];
+            a.uplane_cur[pl] = u[0];
+            a.uplane_cur[np + pl] = u[1];
+            a.uplane_cur[2 * np + pl] = u[2];
+        }
+    } else if (inlet) {
+        // equilibrium inflow: U a + sum_m a_m cos(k.x') + b_m sin(k.x'), x' = x - U t a
+        float u[3] = {0.f, 0.f, 0.f};
+        u[ax] = a.u_in;
+        float xp[3] = {(float)x, (float)y, (float)z};
+        xp[ax] -= a.inflow_shift;
+        for (int m = 0; m < a.n_modes; ++m) {
+            const float* md = a.modes + 9 * m;
+            const float ph = md[0] * xp[0] + md[1] * xp[1] + md[2] * xp[2];
+            float sn, cs;
+            sincosf(ph, &sn, &cs);
+            u[0] += md[3] * cs + md[6] * sn;
+            u[1] += md[4] * cs + md[7] * sn;
+            u[2] += md[5] * cs + md[8] * sn;
+        }
+        equilibrium<Q>(g, 0.0f, u);
+    } else {
+        // equilibrium outflow at the velocity of the upstream neighbour, previous step
+        const long long np = (long long)a.n[bx] * a.n[cxs];
+        const long long pl = (long long)xi[cxs] * a.n[bx] + xi[bx];
+        const float u[3] = {a.uplane_prev[pl], a.uplane_prev[np + pl], a.uplane_prev[2 * np + pl]};
+        equilibrium<Q>(g, 0.0f, u);
+    }
+    T* f = static_cast<T*>(a.f);
+    if (a.phase == 0) {
+        sfor<Q>([&](auto I) {
+            constexpr int s = decltype(I)::value;
+            Store<S>::st(f + (long long)slot_opp<Q>(s) * a.N + cell, g[s]);
+        });
+    } else {
+        sfor<Q>([&](auto I) {
+            constexpr int s = decltype(I)::value;
+            bool ok;
+            const long long dst = nbr_index<Q, s, +1>(nb, ok);
+            if (ok) Store<S>::st(f + (long long)s * a.N + dst, g[s]);
+        });
+    }
+}
+
+// ---------------------------------------------------------------------------
+// porosity embedding, wall model, force-cell list (rotor boxes)
+// ---------------------------------------------------------------------------
+template <int Q, int S>
+__device__ void cell_velocity(const StepArgs& a, int x, int y, int z, float u[3]) {
+    Nbr nb;
+    make_nbr(a, x, y, z, nb);
+    const long long cell = ((long long)z * a.n[1] + y) * a.n[0] + x;
+    float g[Q];
+    load_pre<Q, S>(a, cell, nb, g);
+    float drho = 0.f, j[3] = {0.f, 0.f, 0.f};
+    sfor<Q>([&](auto I) {
+        constexpr int s = decltype(I)::value;
+        drho += g[s];
+        if constexpr (slot_c<Q>(s, 0) != 0) j[0] += float(slot_c<Q>(s, 0)) * g[s];
+        if constexpr (slot_c<Q>(s, 1) != 0) j[1] += float(slot_c<Q>(s, 1)) * g[s];
+        if constexpr (slot_c<Q>(s, 2) != 0) j[2] += float(slot_c<Q>(s, 2)) * g[s];
+    });
+    const float inv = 1.0f / (1.0f + drho);
+    u[0] = j[0] * inv; u[1] = j[1] * inv; u[2] = j[2] * inv;
+}
+
+template <int Q, int S>
+__device__ void wall_model_cell(const StepArgs& a, const RotorDev& R, long long bi, int x, int y, int z,
+                                float phi, int which) {
+    float n[3];
+    rotor_normal(R, which, x, y, z, n);
+    const float y1 = phi > 0.5f ? phi : 0.5f;
+    // sampling point x_s = x + y_s n and trilinear fluid velocity there
+    const float xs[3] = {x + a.wmYs * n[0], y + a.wmYs * n[1], z + a.wmYs * n[2]};
+    int i0[3];
+    float t[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float fl = floorf(xs[k]);
+        i0[k] = (int)fl;
+        t[k] = xs[k] - fl;
+        if (a.open && k == a.flow_axis) {
+            if (i0[k] < 0) { i0[k] = 0; t[k] = 0.f; }
+            if (i0[k] > a.n[k] - 2) { i0[k] = a.n[k] - 2; t[k] = 1.f; }
+        }
+    }
+    float us[3] = {0.f, 0.f, 0.f};
+    for (int cz = 0; cz < 2; ++cz)
+        for (int cy = 0; cy < 2; ++cy)
+            for (int cx = 0; cx < 2; ++cx) {
+                int p[3] = {i0[0] + cx, i0[1] + cy, i0[2] + cz};
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+                    if (!(a.open && k == a.flow_axis)) p[k] = ((p[k] % a.n[k]) + a.n[k]) % a.n[k];
+                const float wgt = (cx ? t[0] : 1.f - t[0]) * (cy ? t[1] : 1.f - t[1]) * (cz ? t[2] : 1.f - t[2]);
+                float uc[3];
+                cell_velocity<Q, S>(a, p[0], p[1], p[2], uc);
+                us[0] += wgt * uc[0]; us[1] += wgt * uc[1]; us[2] += wgt * uc[2];
+            }
+    float usol[3];
+    solid_velocity(R, x, y, z, usol);
+    const float ur[3] = {us[0] - usol[0], us[1] - usol[1], us[2] - usol[2]};
+    const float un = ur[0] * n[0] + ur[1] * n[1] + ur[2] * n[2];
+    const float ut[3] = {ur[0] - un * n[0], ur[1] - un * n[1], ur[2] - un * n[2]};
+    const float utm = sqrtf(ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2]);
+    const long long B = R.box_cells;
+    float* wm = R.wm + bi;
+    if (!(utm >= 1e-12f)) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) wm[k * B] = 0.f;
+        R.active[bi] = 0;
+        R.utau[bi] = 0.f;
+        return;
+    }
+    const float th[3] = {ut[0] / utm, ut[1] / utm, ut[2] / utm};
+    const float ysamp = y1 + a.wmYs;
+    // Eq. (guess): previous value if the wall function was active last step
+    const float guess = R.active[bi] ? R.utau[bi] : sqrtf(a.nu * utm / a.wmYs);
+    const float utau = wall_newton(utm, ysamp, a.nu, guess, a.wmE, a.wmK, a.wmTol, a.wmMaxit);
+    const float up = spalding_uplus(y1 * utau / a.nu, a.wmE, a.wmK, a.wmTol, a.wmMaxit);
+    const float uw = utau * up;
+    const float gs = 0.5f * (utm - uw) / a.wmYs;
+    wm[0] = uw * th[0];
+    wm[B] = uw * th[1];
+    wm[2 * B] = uw * th[2];
+    wm[3 * B] = gs * 2.0f * th[0] * n[0];
+    wm[4 * B] = gs * 2.0f * th[1] * n[1];
+    wm[5 * B] = gs * 2.0f * th[2] * n[2];
+    wm[6 * B] = gs * (th[0] * n[1] + n[0] * th[1]);
+    wm[7 * B] = gs * (th[0] * n[2] + n[0] * th[2]);
+    wm[8 * B] = gs * (th[1] * n[2] + n[1] * th[2]);
+    R.active[bi] = 1;
+    R.utau[bi] = utau;
+}
+
+template <int Q, int S>
+__global__ void __launch_bounds__(BAND_THREADS) band_kernel(const StepArgs a) {
+    const RotorDev& R = a.rot[blockIdx.y];
+    const long long nbox = R.box_cells;
+    const int lane = threadIdx.x & 31;
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < nbox;
+         base += (long long)gridDim.x * blockDim.x) {
+        const long long bi = base + threadIdx.x;
+        bool isB = false;
+        if (bi < nbox) {
+            const int bx = (int)(bi % R.n[0]);
+            const long long r2 = bi / R.n[0];
+            const int by = (int)(r2 % R.n[1]);
+            const int bz = (int)(r2 / R.n[1]);
+            const int x = R.lo[0] + bx, y = R.lo[1] + by, z = R.lo[2] + bz;
+            int which;
+            const float phi = rotor_phi(R, x, y, z, which);
+            uint8_t fl = 0;
+            float d = 1.0f;
+            if (phi < a.eps_half) {
+                fl |= FL_B;
+                if (phi <= -a.eps_half) {
+                    d = 0.0f;
+                } else {
+                    const float tt = phi * a.inv_eps + 0.5f;
+                    d = a.transition ? tt : tt * tt * (3.0f - 2.0f * tt);
+                }
+                if (phi >= 0.0f) fl |= FL_W;
+            }
+            R.d[bi] = d;
+            R.flags[bi] = fl;
+            isB = (fl & FL_B) != 0;
+            if (a.wall_model && (fl & FL_W))
+                wall_model_cell<Q, S>(a, R, bi, x, y, z, phi, which);
+            else
+                R.active[bi] = 0;
+        }
+        // warp-aggregated append to the force-cell list
+        const unsigned mask = __ballot_sync(0xffffffffu, isB);
+        if (mask) {
+            int start = 0;
+            if (lane == 0) start = atomicAdd(R.count, __popc(mask));
+            start = __shfl_sync(0xffffffffu, start, 0);
+            const long long slot = (long long)start + __popc(mask & ((1u << lane) - 1u));
+            if (isB && slot < nbox) R.list[slot] = (int)bi;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// momentum exchange (Galilean-invariant link form) over the force cells
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int Q, int S>
+__global__ void __launch_bounds__(256) force_kernel(const StepArgs a) {
+    using T = typename Store<S>::T;
+    const RotorDev& R = a.rot[blockIdx.y];
+    const T* f = static_cast<const T*>(a.f);
+    int count = *((volatile int*)R.count);
+    if ((long long)count > R.box_cells) count = (int)R.box_cells;   // never read past the list
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < count; idx += gridDim.x * blockDim.x) {
+        const long long bi = R.list[idx];
+        const int bx = (int)(bi % R.n[0]);
+        const long long r2 = bi / R.n[0];
+        const int by = (int)(r2 % R.n[1]);
+        const int bz = (int)(r2 / R.n[1]);
+        const int x = R.lo[0] + bx, y = R.lo[1] + by, z = R.lo[2] + bz;
+        const long long cell = ((long long)z * a.n[1] + y) * a.n[0] + x;
+        Nbr nb;
+        make_nbr(a, x, y, z, nb);
+        const double r[3] = {(double)((float)x - R.cf[0]), (double)((float)y - R.cf[1]),
+                             (double)((float)z - R.cf[2])};
+        double us[3];
+        {
+            const int ax = R.axis, b = (ax + 1) % 3, c = (ax + 2) % 3;
+            us[ax] = 0.0;
+            us[b] = -(double)R.omega * r[c];
+            us[c] = (double)R.omega * r[b];
+        }
+        double Fc[3] = {0.0, 0.0, 0.0};
+        // shifted populations: the rest-weight parts of the link terms cancel
+        sfor<Q - 1>([&](auto I) {
+            constexpr int s = decltype(I)::value + 1;
+            constexpr int o = slot_opp<Q>(s);
+            bool ok;
+            const long long nbx = nbr_index<Q, s, +1>(nb, ok);
+            if (!ok) return;
+            double out_s, in_o;   // f*_s(x) and f*_o(x + c_s)
+            if (a.phase == 0) {
+                out_s = Store<S>::ld(f + (long long)o * a.N + cell);
+                in_o = Store<S>::ld(f + (long long)s * a.N + nbx);
+            } else {
+                out_s = Store<S>::ld(f + (long long)s * a.N + nbx);
+                in_o = Store<S>::ld(f + (long long)o * a.N + cell);
+            }
+            constexpr double c0 = slot_c<Q>(s, 0), c1 = slot_c<Q>(s, 1), c2 = slot_c<Q>(s, 2);
+            Fc[0] += (-c0 - us[0]) * in_o - (c0 - us[0]) * out_s;
+            Fc[1] += (-c1 - us[1]) * in_o - (c1 - us[1]) * out_s;
+            Fc[2] += (-c2 - us[2]) * in_o - (c2 - us[2]) * out_s;
+        });
+        acc[0] += Fc[0]; acc[1] += Fc[1]; acc[2] += Fc[2];
+        acc[3] += r[1] * Fc[2] - r[2] * Fc[1];
+        acc[4] += r[2] * Fc[0] - r[0] * Fc[2];
+        acc[5] += r[0] * Fc[1] - r[1] * Fc[0];
+    }
+    __shared__ double sh[8][6];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const double v = warp_sum(acc[k]);
+        if (lane == 0) sh[warp][k] = v;
+    }
+    __syncthreads();
+    __shared__ bool last;
+    if (threadIdx.x < 6) {
+        double v = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += sh[w][threadIdx.x];
+        R.partial[blockIdx.x * 6 + threadIdx.x] = v;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(R.done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        if (threadIdx.x < 6) {
+            double v = 0.0;
+            for (int b = 0; b < (int)gridDim.x; ++b) v += ((volatile double*)R.partial)[b * 6 + threadIdx.x];
+            R.acc[threadIdx.x] = v;
+            R.acc[6 + threadIdx.x] += v;
+        }
+        if (threadIdx.x == 0) {
+            *R.done = 0u;
+            *R.count = 0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 mass total (deterministic two-stage reduction) and drift check
+// ---------------------------------------------------------------------------
+template <int S>
+__global__ void __launch_bounds__(256) mass_kernel(const MassArgs m) {
+    using T = typename Store<S>::T;
+    const T* f = static_cast<const T*>(m.f);
+    double v = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m.count;
+         i += (long long)gridDim.x * blockDim.x)
+        v += (double)Store<S>::ld(f + i);
+    __shared__ double sh[8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    v = warp_sum(v);
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
+        m.partial[blockIdx.x] = s;
+        __threadfence();
+        last = atomicAdd(m.done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        double s = 0.0;
+        for (int b = 0; b < (int)gridDim.x; ++b) s += ((volatile double*)m.partial)[b];
+        s += m.shift_mass;
+        *m.out = s;
+        if (!(fabs(s) < 1e300)) atomicOr(m.err, ERR_NONFINITE);
+        else if (m.tol >= 0.0 && fabs(s - m.ref) > m.tol * fabs(m.ref)) atomicOr(m.err, ERR_MASS);
+        *m.done = 0u;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// initial state, macroscopic fields, single-cell collisions (unit checks)
+// ---------------------------------------------------------------------------
+template <int Q, int S>
+__global__ void init_kernel(void* fv, long long N, int nx, int ny, int nz, const float* rho, const float* u,
+                            float drho0, float u0x, float u0y, float u0z) {
+    using T = typename Store<S>::T;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    const int z = blockIdx.z;
+    if (x >= nx) return;
+    const long long cell = ((long long)z * ny + y) * nx + x;
+    float uu[3] = {u0x, u0y, u0z};
+    float drho = drho0;
+    if (rho) drho = rho[cell] - 1.0f;
+    if (u) { uu[0] = u[cell]; uu[1] = u[N + cell]; uu[2] = u[2 * N + cell]; }
+    float g[Q];
+    equilibrium<Q>(g, drho, uu);
+    T* f = static_cast<T*>(fv);
+    sfor<Q>([&](auto I) {
+        constexpr int s = decltype(I)::value;
+        Store<S>::st(f + (long long)s * N + cell, g[s]);
+    });
+}
+
+template <int Q, int S>
+__global__ void fields_kernel(const StepArgs a, float* rho, float* u) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    const int z = blockIdx.z;
+    if (x >= a.n[0]) return;
+    const long long cell = ((long long)z * a.n[1] + y) * a.n[0] + x;
+    Nbr nb;
+    make_nbr(a, x, y, z, nb);
+    float g[Q];
+    load_pre<Q, S>(a, cell, nb, g);
+    float drho = 0.f, j[3] = {0.f, 0.f, 0.f};
+    sfor<Q>([&](auto I) {
+        constexpr int s = decltype(I)::value;
+        drho += g[s];
+        if constexpr (slot_c<Q>(s, 0) != 0) j[0] += float(slot_c<Q>(s, 0)) * g[s];
+        if constexpr (slot_c<Q>(s, 1) != 0) j[1] += float(slot_c<Q>(s, 1)) * g[s];
+        if constexpr (slot_c<Q>(s, 2) != 0) j[2] += float(slot_c<Q>(s, 2)) * g[s];
+    });
+    const float r = 1.0f + drho;
+    rho[cell] = r;
+    u[cell] = j[0] / r;
+    u[a.N + cell] = j[1] / r;
+    u[2 * a.N + cell] = j[2] / r;
+}
+
+template <int Q>
+__global__ void debug_collide_kernel(int n, const float* gin, const float* d, const float* uB, const float* sigma,
+                                     const float* S, float tau_mo, float Ksmag, float* gout) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    float g[Q];
+#pragma unroll
+    for (int s = 0; s < Q; ++s) g[s] = gin[(long long)c * Q + s];
+    float u[3];
+    if (d) {
+        Band B;
+        B.d = d[c];
+        B.uB[0] = uB[3 * c]; B.uB[1] = uB[3 * c + 1]; B.uB[2] = uB[3 * c + 2];
+        B.sigma = sigma[c];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) B.S[k] = S[6 * c + k];
+        collide<Q, true>(g, B, tau_mo, Ksmag, u);
+    } else {
+        Band B0;
+        collide<Q, false>(g, B0, tau_mo, Ksmag, u);
+    }
+#pragma unroll
+    for (int s = 0; s < Q; ++s) gout[(long long)c * Q + s] = g[s];
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static dim3 cell_block(int nx) {
+    if (nx >= 128) return dim3(128, 1, 1);
+    const int bx = ((nx + 31) / 32) * 32;
+    return dim3(bx, 128 / bx >= 1 ? 128 / bx : 1, 1);
+}
+
+template <int Q, int S>
+static cudaError_t launch_collide_t(const StepArgs& a, cudaStream_t s) {
+    const dim3 blk = cell_block(a.n[0]);
+    const dim3 grd((a.n[0] + blk.x - 1) / blk.x, (a.n[1] + blk.y - 1) / blk.y, a.n[2]);
+    collide_kernel<Q, S><<<grd, blk, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int Q, int S>
+static cudaError_t launch_band_t(const StepArgs& a, cudaStream_t s) {
+    if (a.nrot == 0) return cudaSuccess;
+    long long maxbox = 0;
+    for (int k = 0; k < a.nrot; ++k) maxbox = a.rot[k].box_cells > maxbox ? a.rot[k].box_cells : maxbox;
+    long long blocks = (maxbox + BAND_THREADS - 1) / BAND_THREADS;
+    if (blocks > 148 * 16) blocks = 148 * 16;
+    if (blocks < 1) blocks = 1;
+    band_kernel<Q, S><<<dim3((unsigned)blocks, a.nrot), BAND_THREADS, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int Q, int S>
+static cudaError_t launch_force_t(const StepArgs& a, cudaStream_t s) {
+    if (a.nrot == 0) return cudaSuccess;
+    force_kernel<Q, S><<<dim3(FORCE_BLOCKS, a.nrot), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+#define HL_DISPATCH(Q, S, FN, ...)                                                   \
+    do {                                                                             \
+        if (Q == 19 && S == ST_F32) return FN<19, ST_F32>(__VA_ARGS__);              \
+        if (Q == 19 && S == ST_F16S) return FN<19, ST_F16S>(__VA_ARGS__);            \
+        if (Q == 19 && S == ST_BF16S) return FN<19, ST_BF16S>(__VA_ARGS__);          \
+        if (Q == 27 && S == ST_F32) return FN<27, ST_F32>(__VA_ARGS__);              \
+        if (Q == 27 && S == ST_F16S) return FN<27, ST_F16S>(__VA_ARGS__);            \
+        if (Q == 27 && S == ST_BF16S) return FN<27, ST_BF16S>(__VA_ARGS__);          \
+        return cudaErrorInvalidValue;                                                \
+    } while (0)
+
+cudaError_t launch_collide(int Q, int S, const StepArgs& a, cudaStream_t s) {
+    HL_DISPATCH(Q, S, launch_collide_t, a, s);
+}
+cudaError_t launch_band(int Q, int S, const StepArgs& a, cudaStream_t s) {
+    HL_DISPATCH(Q, S, launch_band_t, a, s);
+}
+cudaError_t launch_force(int Q, int S, const StepArgs& a, cudaStream_t s) {
+    HL_DISPATCH(Q, S, launch_force_t, a, s);
+}
+
+cudaError_t launch_mass(int Q, int S, const MassArgs& m, cudaStream_t s) {
+    (void)Q;
+    switch (S) {
+        case ST_F32: mass_kernel<ST_F32><<<MASS_BLOCKS, 256, 0, s>>>(m); break;
+        case ST_F16S: mass_kernel<ST_F16S><<<MASS_BLOCKS, 256, 0, s>>>(m); break;
+        case ST_BF16S: mass_kernel<ST_BF16S><<<MASS_BLOCKS, 256, 0, s>>>(m); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <int Q, int S>
+static cudaError_t launch_init_t(void* f, long long N, const int n[3], const float* rho, const float* u,
+                                 float drho0, const float u0[3], cudaStream_t s) {
+    const dim3 grd((n[0] + 127) / 128, n[1], n[2]);
+    init_kernel<Q, S><<<grd, 128, 0, s>>>(f, N, n[0], n[1], n[2], rho, u, drho0, u0[0], u0[1], u0[2]);
+    return cudaGetLastError();
+}
+cudaError_t launch_init(int Q, int S, void* f, long long N, const int n[3], const float* rho, const float* u,
+                        float drho0, const float u0[3], cudaStream_t s) {
+    HL_DISPATCH(Q, S, launch_init_t, f, N, n, rho, u, drho0, u0, s);
+}
+
+template <int Q, int S>
+static cudaError_t launch_fields_t(const StepArgs& a, float* rho, float* u, cudaStream_t s) {
+    const dim3 grd((a.n[0] + 127) / 128, a.n[1], a.n[2]);
+    fields_kernel<Q, S><<<grd, 128, 0, s>>>(a, rho, u);
+    return cudaGetLastError();
+}
+cudaError_t launch_fields(int Q, int S, const StepArgs& a, float* rho, float* u, cudaStream_t s) {
+    HL_DISPATCH(Q, S, launch_fields_t, a, rho, u, s);
+}
+
+cudaError_t launch_debug_collide(int Q, int n, const float* g_in, const float* d, const float* uB,
+                                 const float* sigma, const float* S, float tau_mo, float Ksmag, float* g_out,
+                                 cudaStream_t s) {
+    const int blocks = (n + 127) / 128;
+    if (n <= 0) return cudaSuccess;
+    if (Q == 19)
+        debug_collide_kernel<19><<<blocks, 128, 0, s>>>(n, g_in, d, uB, sigma, S, tau_mo, Ksmag, g_out);
+    else if (Q == 27)
+        debug_collide_kernel<27><<<blocks, 128, 0, s>>>(n, g_in, d, uB, sigma, S, tau_mo, Ksmag, g_out);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+}  // namespace hl

@@ -1,0 +1,230 @@
+"""Python face of the C ABI: a lattice whose device memory comes from PyTorch.
+
+Every step of the time loop runs in the library's CUDA kernels; this module
+only allocates buffers with torch, passes pointers and sizes, and reshapes
+results.  Arrays follow the lattice order (x fastest): fields have shape
+(nz, ny, nx), vectors (3, nz, ny, nx).
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from ._lib import STORAGE, HlConfig, HlRotorGeometry, check, lib
+
+_ALIGN = 256
+
+
+def _aligned_bytes(nbytes: int, device):
+    import torch
+    buf = torch.empty(int(nbytes) + _ALIGN, dtype=torch.uint8, device=device)
+    off = (-buf.data_ptr()) % _ALIGN
+    return buf, buf.data_ptr() + off
+
+
+class Lattice:
+    """A lattice with rotors, advanced on one CUDA stream of one device."""
+
+    def __init__(self, nx, ny, nz, q=19, storage="f32", flow_axis=2, open_boundaries=True,
+                 tau_mo=0.5005, c_smag=0.1, u_in=0.05, eps_h=2.0, transition="smoothstep",
+                 wall_model=True, wm_E=9.8, wm_kappa=0.41, wm_ysample=2.0, wm_tol=1e-4,
+                 wm_maxit=10, modes=None, mass_check_every=100, mass_tol=0.05,
+                 device=None, stream=None):
+        import torch
+        self.device = torch.device(device if device is not None else "cuda")
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        L = lib()
+        cfg = HlConfig()
+        L.hl_config_defaults(C.byref(cfg))
+        cfg.nx, cfg.ny, cfg.nz, cfg.q = int(nx), int(ny), int(nz), int(q)
+        cfg.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
+        cfg.flow_axis = int(flow_axis)
+        cfg.open_boundaries = int(bool(open_boundaries))
+        cfg.tau_mo, cfg.c_smag, cfg.u_in, cfg.eps_h = float(tau_mo), float(c_smag), float(u_in), float(eps_h)
+        cfg.transition = 1 if transition == "linear" else 0
+        cfg.wall_model = int(bool(wall_model))
+        cfg.wm_E, cfg.wm_kappa, cfg.wm_ysample = float(wm_E), float(wm_kappa), float(wm_ysample)
+        cfg.wm_tol, cfg.wm_maxit = float(wm_tol), int(wm_maxit)
+        cfg.mass_check_every, cfg.mass_tol = int(mass_check_every), float(mass_tol)
+        self._modes = None
+        if modes is not None and len(modes):
+            self._modes = np.ascontiguousarray(modes, dtype=np.float64).reshape(-1, 9)
+            cfg.n_modes = self._modes.shape[0]
+            cfg.modes = self._modes.ctypes.data_as(C.POINTER(C.c_double))
+        self.cfg = cfg
+        self.shape = (int(nz), int(ny), int(nx))
+        self.N = int(nx) * int(ny) * int(nz)
+        self.q = int(q)
+        size = C.c_size_t()
+        check(L.hl_workspace_size(C.byref(cfg), C.byref(size)))
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            self._ws, ptr = _aligned_bytes(size.value, self.device)
+            h = C.c_void_p()
+            check(L.hl_lattice_init(C.byref(h), C.byref(cfg), C.c_void_p(ptr), size.value,
+                                    C.c_void_p(self.stream.cuda_stream)))
+        self._h = h
+        self._rotor_ws = []
+        self.nrot = 0
+
+    # -- lifetime -----------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().hl_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def _check(self, code):
+        check(code, self._h)
+
+    # -- rotors -------------------------------------------------------------
+    def add_rotor(self, grid, center, omega, pitch=0.0, phase0=0.0, axis=None, n_blades=3,
+                  hub_radius=None) -> int:
+        """Add a rotor built from a ``workloads.BladeGrid`` (one blade, Sec. 3.1)."""
+        import torch
+        sdf = np.ascontiguousarray(grid.sdf, dtype=np.float32)
+        g = HlRotorGeometry()
+        g.center = (C.c_double * 3)(*[float(v) for v in center])
+        g.axis = int(self.cfg.flow_axis if axis is None else axis)
+        g.n_blades = int(n_blades)
+        g.hub_radius = float(grid.hub_radius if hub_radius is None else hub_radius)
+        g.phase0 = float(phase0)
+        g.sdf = sdf.ctypes.data_as(C.POINTER(C.c_float))
+        g.gz, g.gy, g.gx = sdf.shape
+        g.origin = (C.c_double * 3)(*[float(v) for v in grid.origin])
+        g.spacing = float(grid.spacing)
+        size = C.c_size_t()
+        self._check(lib().hl_rotor_workspace_size(self._h, C.byref(g), C.byref(size)))
+        with torch.cuda.device(self.device):
+            buf, ptr = _aligned_bytes(size.value, self.device)
+            rid = C.c_int()
+            self._check(lib().hl_set_rotor(self._h, C.byref(rid), C.byref(g), float(omega), float(pitch),
+                                           C.c_void_p(ptr), size.value))
+        self._rotor_ws.append(buf)
+        self.nrot += 1
+        return rid.value
+
+    def rotor_box(self, k: int):
+        lo = (C.c_int * 3)()
+        n = (C.c_int * 3)()
+        self._check(lib().hl_rotor_box(self._h, int(k), lo, n))
+        return tuple(lo), tuple(n)
+
+    def rotor_band(self, k: int):
+        """Band arrays of the last porosity update, shaped (nbz, nby, nbx)."""
+        import torch
+        lo, n = self.rotor_box(k)
+        box = n[0] * n[1] * n[2]
+        dev = self.device
+        d = torch.empty(box, dtype=torch.float32, device=dev)
+        fl = torch.empty(box, dtype=torch.uint8, device=dev)
+        wm = torch.empty(9 * box, dtype=torch.float32, device=dev)
+        ut = torch.empty(box, dtype=torch.float32, device=dev)
+        with torch.cuda.device(dev):
+            self._check(lib().hl_rotor_band(self._h, int(k), d.data_ptr(), fl.data_ptr(), wm.data_ptr(),
+                                            ut.data_ptr()))
+        self.stream.synchronize()
+        shp = (n[2], n[1], n[0])
+        return dict(lo=lo, n=n, d=d.view(shp), flags=fl.view(shp), wm=wm.view((9,) + shp), utau=ut.view(shp))
+
+    # -- time loop ----------------------------------------------------------
+    def step(self, n: int = 1):
+        import torch
+        with torch.cuda.device(self.device):
+            self._check(lib().hl_step(self._h, int(n)))
+
+    def step_async(self, n: int = 1):
+        import torch
+        with torch.cuda.device(self.device):
+            self._check(lib().hl_step_async(self._h, int(n)))
+
+    def check(self):
+        self._check(lib().hl_check(self._h))
+
+    @property
+    def t(self) -> int:
+        v = C.c_longlong()
+        self._check(lib().hl_get_time(self._h, C.byref(v)))
+        return v.value
+
+    # -- results ------------------------------------------------------------
+    def forces(self, reset_avg: bool = False):
+        """(F, F_avg): force on each rotor in the last step and its running mean, (nrot, 3)."""
+        F = np.zeros((max(1, self.nrot), 3))
+        Fa = np.zeros_like(F)
+        self._check(lib().hl_forces(self._h, F.ctypes.data_as(C.POINTER(C.c_double)),
+                                    Fa.ctypes.data_as(C.POINTER(C.c_double)), int(reset_avg)))
+        return F[:self.nrot], Fa[:self.nrot]
+
+    def moments(self):
+        """(M, M_avg): torque about each rotor centre, (nrot, 3)."""
+        M = np.zeros((max(1, self.nrot), 3))
+        Ma = np.zeros_like(M)
+        self._check(lib().hl_moments(self._h, M.ctypes.data_as(C.POINTER(C.c_double)),
+                                     Ma.ctypes.data_as(C.POINTER(C.c_double))))
+        return M[:self.nrot], Ma[:self.nrot]
+
+    def fields(self):
+        """Density (nz, ny, nx) and velocity (3, nz, ny, nx) as FP32 device tensors."""
+        import torch
+        rho = torch.empty(self.N, dtype=torch.float32, device=self.device)
+        u = torch.empty(3 * self.N, dtype=torch.float32, device=self.device)
+        with torch.cuda.device(self.device):
+            self._check(lib().hl_fields(self._h, rho.data_ptr(), u.data_ptr()))
+        self.stream.synchronize()
+        return rho.view(self.shape), u.view((3,) + self.shape)
+
+    def init_fields(self, rho=None, u=None):
+        """Set f = f^eq(rho, u) from device tensors and reset t to 0."""
+        import torch
+        r = None if rho is None else torch.as_tensor(rho, dtype=torch.float32, device=self.device).contiguous()
+        v = None if u is None else torch.as_tensor(u, dtype=torch.float32, device=self.device).contiguous()
+        with torch.cuda.device(self.device):
+            self._check(lib().hl_init_fields(self._h, 0 if r is None else r.data_ptr(),
+                                             0 if v is None else v.data_ptr()))
+        self.stream.synchronize()
+
+    def mass(self) -> float:
+        m = C.c_double()
+        self._check(lib().hl_mass(self._h, C.byref(m)))
+        return m.value
+
+    # -- checkpoints --------------------------------------------------------
+    def state_size(self) -> int:
+        s = C.c_size_t()
+        self._check(lib().hl_state_size(self._h, C.byref(s)))
+        return s.value
+
+    def save_state(self, buf=None):
+        import torch
+        n = self.state_size()
+        if buf is None:
+            buf = torch.empty(n, dtype=torch.uint8, device=self.device)
+        with torch.cuda.device(self.device):
+            self._check(lib().hl_save_state(self._h, buf.data_ptr(), buf.numel()))
+        return buf
+
+    def load_state(self, buf):
+        import torch
+        with torch.cuda.device(self.device):
+            self._check(lib().hl_load_state(self._h, buf.data_ptr(), buf.numel()))
+
+    @classmethod
+    def from_workload(cls, wl, storage="f32", q=None, rotor_kw=None, **overrides):
+        """Lattice and rotors of a ``workloads.Workload``."""
+        kw = dict(q=wl.q if q is None else q, storage=storage, flow_axis=wl.flow_axis,
+                  tau_mo=wl.tau_mo, c_smag=wl.c_smag, u_in=wl.u_in, eps_h=wl.eps_h, modes=wl.modes())
+        kw.update(overrides)
+        lat = cls(wl.nx, wl.ny, wl.nz, **kw)
+        for spec, g in zip(wl.rotors, wl.blade_grids()):
+            rk = dict(center=spec.center, omega=spec.omega(wl.u_in), pitch=spec.pitch,
+                      phase0=spec.phase0, n_blades=spec.n_blades)
+            if rotor_kw:
+                rk.update(rotor_kw)
+            lat.add_rotor(g, **rk)
+        return lat
