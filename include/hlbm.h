@@ -191,10 +191,10 @@ hl_status hl_rotor_box(const hl_lattice* lat, int rotor, int* lo, int* n);
 /* Copy the rotor's band arrays of the last porosity update into device
  * buffers of box size: porosity d (float), flags (uint8: bit 0 force cell
  * d < 1, bit 1 wall cell), wall-model output wm (float [9][box]: modelled
- * velocity xyz, strain xx yy zz xy xz yz), friction velocity utau (float).
+ * velocity xyz, strain xx yy zz xy xz yz), friction velocity utau (double).
  * Any pointer may be NULL. */
 hl_status hl_rotor_band(hl_lattice* lat, int rotor, float* d_d, unsigned char* d_flags, float* d_wm,
-                        float* d_utau);
+                        double* d_utau);
 
 /* Velocity set of the library's slot order: c[q][3] and w[q] (host). */
 hl_status hl_velocity_set(int q, int* c, double* w);

@@ -54,7 +54,7 @@ RotorLayout rotor_layout(long long ngrid, long long box) {
     L.d = o; o = align_up(o + sizeof(float) * box);
     L.flags = o; o = align_up(o + box);
     L.wm = o; o = align_up(o + sizeof(float) * 9 * box);
-    L.utau = o; o = align_up(o + sizeof(float) * box);
+    L.utau = o; o = align_up(o + sizeof(double) * box);
     L.active = o; o = align_up(o + box);
     L.list = o; o = align_up(o + sizeof(int) * box);
     L.count = o; o = align_up(o + sizeof(int));
@@ -146,12 +146,12 @@ StepArgs make_args(const hl_lattice* lat) {
     a.inv_eps = (float)(1.0 / c.eps_h);
     a.transition = c.transition;
     a.wall_model = c.wall_model;
-    a.wmE = (float)c.wm_E;
-    a.wmK = (float)c.wm_kappa;
+    a.wmE = c.wm_E;
+    a.wmK = c.wm_kappa;
     a.wmYs = (float)c.wm_ysample;
-    a.wmTol = (float)c.wm_tol;
+    a.wmTol = c.wm_tol;
     a.wmMaxit = c.wm_maxit;
-    a.nu = (float)((c.tau_mo - 0.5) / 3.0);
+    a.nu = (c.tau_mo - 0.5) / 3.0;
     a.sigma_band = (float)c.sigma_band;
     a.modes = lat->modes;
     a.n_modes = c.n_modes;
@@ -397,7 +397,7 @@ hl_status hl_set_rotor(hl_lattice* lat, int* rotor_id, const hl_rotor_geometry* 
     D.d = reinterpret_cast<float*>(R.ws + L.d);
     D.flags = reinterpret_cast<uint8_t*>(R.ws + L.flags);
     D.wm = reinterpret_cast<float*>(R.ws + L.wm);
-    D.utau = reinterpret_cast<float*>(R.ws + L.utau);
+    D.utau = reinterpret_cast<double*>(R.ws + L.utau);
     D.active = reinterpret_cast<uint8_t*>(R.ws + L.active);
     D.list = reinterpret_cast<int*>(R.ws + L.list);
     D.count = reinterpret_cast<int*>(R.ws + L.count);
@@ -537,7 +537,7 @@ static size_t state_bytes(const hl_lattice* lat) {
     o = align_up(o + 2 * sizeof(float) * 3 * plane_cells(lat->cfg));
     for (int k = 0; k < lat->nrot; ++k) {
         const long long b = lat->rot[k].dev.box_cells;
-        o = align_up(o + sizeof(float) * b);
+        o = align_up(o + sizeof(double) * b);
         o = align_up(o + b);
         o = align_up(o + sizeof(double) * 12);
     }
@@ -575,7 +575,7 @@ static hl_status state_copy(hl_lattice* lat, char* buf, bool save) {
     }
     for (int k = 0; k < lat->nrot; ++k) {
         RotorDev& D = lat->rot[k].dev;
-        HL_CUDA(lat, cp(D.utau, sizeof(float) * D.box_cells));
+        HL_CUDA(lat, cp(D.utau, sizeof(double) * D.box_cells));
         HL_CUDA(lat, cp(D.active, (size_t)D.box_cells));
         HL_CUDA(lat, cp(D.acc, sizeof(double) * 12));
     }
@@ -623,7 +623,7 @@ hl_status hl_rotor_box(const hl_lattice* lat, int rotor, int* lo, int* n) {
 }
 
 hl_status hl_rotor_band(hl_lattice* lat, int rotor, float* d_d, unsigned char* d_flags, float* d_wm,
-                        float* d_utau) {
+                        double* d_utau) {
     if (!lat || rotor < 0 || rotor >= lat->nrot) return HL_ERR_ARG;
     const RotorDev& D = lat->rot[rotor].dev;
     const size_t b = (size_t)D.box_cells;
@@ -631,7 +631,7 @@ hl_status hl_rotor_band(hl_lattice* lat, int rotor, float* d_d, unsigned char* d
     if (d_d) HL_CUDA(lat, cudaMemcpyAsync(d_d, D.d, sizeof(float) * b, k, lat->stream));
     if (d_flags) HL_CUDA(lat, cudaMemcpyAsync(d_flags, D.flags, b, k, lat->stream));
     if (d_wm) HL_CUDA(lat, cudaMemcpyAsync(d_wm, D.wm, sizeof(float) * 9 * b, k, lat->stream));
-    if (d_utau) HL_CUDA(lat, cudaMemcpyAsync(d_utau, D.utau, sizeof(float) * b, k, lat->stream));
+    if (d_utau) HL_CUDA(lat, cudaMemcpyAsync(d_utau, D.utau, sizeof(double) * b, k, lat->stream));
     return HL_OK;
 }
 

@@ -266,7 +266,7 @@ struct RotorDev {
     float* d;                   // [box] porosity
     uint8_t* flags;             // [box] bit0: d<1 (force set), bit1: wall cell
     float* wm;                  // [9][box]: du_x du_y du_z S_xx S_yy S_zz S_xy S_xz S_yz
-    float* utau;                // [box]
+    double* utau;               // [box] friction velocity (Newton warm start)
     uint8_t* active;            // [box]
     int* list;                  // [box] force cells of this step
     int* count;                 // [1]
@@ -381,46 +381,51 @@ __device__ inline void rotor_normal(const RotorDev& R, int which, int x, int y, 
 }
 
 // ---------------------------------------------------------------------------
-// wall function, Sec. 2.2.1 (FP32)
+// wall function, Sec. 2.2.1.  The Newton iterations run in FP64: their
+// stopping rule, the halving guard and the overflow of exp(kappa u+) are
+// decisions taken in floating point, and they must be taken in the same
+// precision as the FP64 statement of the scheme (FP32 exp overflows at
+// u+ ~ 216, which the iterates of a cold start do reach).  Only the few
+// wall cells run this code.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float spalding_yplus(float up, float E, float kappa) {
-    const float k = kappa * up;
-    return up + (expf(k) - 1.0f - k - 0.5f * k * k - k * k * k * (1.0f / 6.0f)) / E;
+__device__ __forceinline__ double spalding_yplus(double up, double E, double kappa) {
+    const double k = kappa * up;
+    return up + (exp(k) - 1.0 - k - 0.5 * k * k - k * k * k / 6.0) / E;
 }
-__device__ __forceinline__ float spalding_dyplus(float up, float E, float kappa) {
-    const float k = kappa * up;
-    return 1.0f + kappa / E * (expf(k) - 1.0f - k - 0.5f * k * k);
+__device__ __forceinline__ double spalding_dyplus(double up, double E, double kappa) {
+    const double k = kappa * up;
+    return 1.0 + kappa / E * (exp(k) - 1.0 - k - 0.5 * k * k);
 }
 
 // Newton-Raphson on Eq. (implicitWF): stop when the residual changes by less
 // than tol, at most maxit iterations; a non-positive iterate is halved.
-__device__ inline float wall_newton(float u, float y, float nu, float guess, float E, float kappa,
-                                    float tol, int maxit) {
-    float ut = guess;
-    float fv = spalding_yplus(u / ut, E, kappa) - y * ut / nu;
+__device__ inline double wall_newton(double u, double y, double nu, double guess, double E, double kappa,
+                                     double tol, int maxit) {
+    double ut = guess;
+    double fv = spalding_yplus(u / ut, E, kappa) - y * ut / nu;
     for (int it = 0; it < maxit; ++it) {
-        const float fp = -spalding_dyplus(u / ut, E, kappa) * u / (ut * ut) - y / nu;
-        float un = ut - fv / fp;
-        if (!(un > 0.0f)) un = 0.5f * ut;
-        const float fn = spalding_yplus(u / un, E, kappa) - y * un / nu;
+        const double fp = -spalding_dyplus(u / ut, E, kappa) * u / (ut * ut) - y / nu;
+        double un = ut - fv / fp;
+        if (!(un > 0.0)) un = 0.5 * ut;
+        const double fn = spalding_yplus(u / un, E, kappa) - y * un / nu;
         ut = un;
-        if (fabsf(fn - fv) < tol) break;
+        if (fabs(fn - fv) < tol) break;
         fv = fn;
     }
     return ut;
 }
 
 // inverse of Eq. (spalding): u+ for y+, Newton from the right of the root
-__device__ inline float spalding_uplus(float yp, float E, float kappa, float tol, int maxit) {
-    const float lg = logf(1.0f + E * yp) / kappa;
-    float up = yp < lg ? yp : lg;
-    float g = spalding_yplus(up, E, kappa) - yp;
+__device__ inline double spalding_uplus(double yp, double E, double kappa, double tol, int maxit) {
+    const double lg = log(1.0 + E * yp) / kappa;
+    double up = yp < lg ? yp : lg;
+    double g = spalding_yplus(up, E, kappa) - yp;
     for (int it = 0; it < maxit; ++it) {
-        float un = up - g / spalding_dyplus(up, E, kappa);
-        if (!(un > 0.0f)) un = 0.5f * up;
-        const float gn = spalding_yplus(un, E, kappa) - yp;
+        double un = up - g / spalding_dyplus(up, E, kappa);
+        if (!(un > 0.0)) un = 0.5 * up;
+        const double gn = spalding_yplus(un, E, kappa) - yp;
         up = un;
-        if (fabsf(gn - g) < tol) break;
+        if (fabs(gn - g) < tol) break;
         g = gn;
     }
     return up;

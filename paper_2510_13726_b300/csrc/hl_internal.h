@@ -25,7 +25,8 @@ struct StepArgs {
     float u_in, inflow_shift;   // inflow_shift = u_in * t
     float eps_half, inv_eps;
     int transition, wall_model;
-    float wmE, wmK, wmYs, wmTol, nu;
+    float wmYs;
+    double wmE, wmK, wmTol, nu;      // wall-function solve runs in FP64
     int wmMaxit;
     float sigma_band;
     const float* modes;      // [n_modes][9]

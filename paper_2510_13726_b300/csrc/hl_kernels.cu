@@ -255,17 +255,17 @@ __device__ void wall_model_cell(const StepArgs& a, const RotorDev& R, long long 
 #pragma unroll
         for (int k = 0; k < 9; ++k) wm[k * B] = 0.f;
         R.active[bi] = 0;
-        R.utau[bi] = 0.f;
+        R.utau[bi] = 0.0;
         return;
     }
     const float th[3] = {ut[0] / utm, ut[1] / utm, ut[2] / utm};
-    const float ysamp = y1 + a.wmYs;
+    const double ysamp = (double)y1 + (double)a.wmYs;
     // Eq. (guess): previous value if the wall function was active last step
-    const float guess = R.active[bi] ? R.utau[bi] : sqrtf(a.nu * utm / a.wmYs);
-    const float utau = wall_newton(utm, ysamp, a.nu, guess, a.wmE, a.wmK, a.wmTol, a.wmMaxit);
-    const float up = spalding_uplus(y1 * utau / a.nu, a.wmE, a.wmK, a.wmTol, a.wmMaxit);
-    const float uw = utau * up;
-    const float gs = 0.5f * (utm - uw) / a.wmYs;
+    const double guess = R.active[bi] ? R.utau[bi] : sqrt(a.nu * (double)utm / (double)a.wmYs);
+    const double utau = wall_newton((double)utm, ysamp, a.nu, guess, a.wmE, a.wmK, a.wmTol, a.wmMaxit);
+    const double up = spalding_uplus((double)y1 * utau / a.nu, a.wmE, a.wmK, a.wmTol, a.wmMaxit);
+    const float uw = (float)(utau * up);
+    const float gs = (float)(0.5 * ((double)utm - utau * up) / (double)a.wmYs);
     wm[0] = uw * th[0];
     wm[B] = uw * th[1];
     wm[2 * B] = uw * th[2];

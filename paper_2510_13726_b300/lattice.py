@@ -124,7 +124,7 @@ class Lattice:
         d = torch.empty(box, dtype=torch.float32, device=dev)
         fl = torch.empty(box, dtype=torch.uint8, device=dev)
         wm = torch.empty(9 * box, dtype=torch.float32, device=dev)
-        ut = torch.empty(box, dtype=torch.float32, device=dev)
+        ut = torch.empty(box, dtype=torch.float64, device=dev)
         with torch.cuda.device(dev):
             self._check(lib().hl_rotor_band(self._h, int(k), d.data_ptr(), fl.data_ptr(), wm.data_ptr(),
                                             ut.data_ptr()))
