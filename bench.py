@@ -1,0 +1,330 @@
+#!/usr/bin/env python3
+"""Benchmark of the homogenized LB rotor time step on B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cuda|reference]
+
+A step is one pass of the whole hot path (listing "HHRRLBM-FSI"): porosity
+embedding + wall model of the rotor box, fused collide-and-stream of every
+cell, momentum-exchange force/torque reduction, and the FP64 mass check
+every 100 steps.  Workload: the 256x256x512 D3Q19 rotor (FP32 populations,
+single-buffer AA pattern, R = 64 NACA 4412 three-bladed rotor at TSR 6,
+5 % synthetic turbulent inflow).  Prints one JSON line (rank 0).
+
+Under torchrun (N > 1) every rank advances its own replica of the workload
+on its own GPU (the path has no exchange step in this configuration); the
+timed region is bracketed by barriers and the max over ranks is reported.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS & % HBM roofline (FP32 vs 16-bit store); adjoint/forward step ratio"
+UNIT = "MLUPS"
+WORKLOAD_DESC = ("rotor256: 256x256x512 cells (33.5M), D3Q19, FP32 weight-shifted populations, "
+                 "AA single buffer, one 3-blade NACA4412 rotor R=64 at TSR 6, 5% turbulent inflow "
+                 "(64 Fourier modes), tau_mo 0.5005, C_S 0.1, Spalding wall model")
+
+
+# --------------------------------------------------------------------------
+# distributed helpers (replicas; barrier + max over ranks)
+# --------------------------------------------------------------------------
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def dist_init(backend: str):
+    import torch.distributed as dist
+    world, rank, _ = dist_env()
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return world, rank
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def max_over_ranks(x: float, device="cpu") -> float:
+    import torch
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+    return float(x)
+
+
+def aggregate(elapsed_s: float, cells: int, steps: int, world: int, device="cpu"):
+    """Whole-job throughput: all ranks' cell updates over the slowest rank's time."""
+    t = max_over_ranks(elapsed_s, device)
+    return world * cells * steps / t / 1e6, t
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------
+# CPU baseline / reference arm: the FP64 oracle on a bounded sample
+# --------------------------------------------------------------------------
+def oracle_sample(steps: int, crop=(160, 160, 72), warmup: int = 1):
+    """Time the oracle on a crop of the rotor256 workload centred on the rotor
+    (same rotor, inflow table and parameters; the crop's lateral faces are
+    periodic).  Returns (MLUPS, seconds, threads, description)."""
+    cores = len(os.sched_getaffinity(0))
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    import oracle as O
+    import workloads as W
+    wl = W.workload("rotor256")
+    nx, ny, nz = crop
+    spec = wl.rotors[0]
+    grid = wl.blade_grids()[0]
+    center = (0.5 * (nx - 1), 0.5 * (ny - 1), 0.5 * nz)
+    rot = O.make_rotor(grid, center=center, axis=2, omega=spec.omega(wl.u_in), phase0=spec.phase0)
+    o = O.Oracle(nx, ny, nz, tau_mo=wl.tau_mo, c_smag=wl.c_smag, u_in=wl.u_in, eps_h=wl.eps_h,
+                 modes=wl.modes(), rotors=[rot])
+    o.step(max(1, warmup))         # includes the first touch of the FP64 arrays
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    cells = nx * ny * nz
+    whole = min(nx, ny) > 2 * (spec.radius + 4)
+    what = "the whole rotor" if whole else "the hub and inner blade span"
+    threads = int(os.environ["OMP_NUM_THREADS"])
+    desc = (f"FP64 oracle, {steps} steps (after {max(1, warmup)} warm-up) of a {nx}x{ny}x{nz} crop of "
+            f"rotor256 containing {what} (same rotor, inflow modes and parameters), {threads} OpenMP threads")
+    return cells * steps / dt / 1e6, dt, threads, desc
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if world > 1 and rank != 0:
+        return 0
+    steps = max(1, args.steps)
+    # each step is one oracle step on the crop; the crop shrinks for long runs
+    crop = (160, 160, 72) if steps <= 200 else (96, 96, 48)
+    mlups, dt, cores, desc = oracle_sample(steps, crop, warmup=args.warmup)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(mlups, 4), "unit": UNIT,
+        "n_gpus": args.gpus, "steps": steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * dt / steps, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "sample": desc},
+        "cpu_baseline": {"value": round(mlups, 4), "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+        "e2e": {"value": round(mlups, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------
+# CUDA arm
+# --------------------------------------------------------------------------
+# DRAM traffic of one collide-and-stream launch of this workload from an ncu
+# capture, valid for the kernel source of the given hash (else reported null)
+NCU_TRAFFIC = {"source_sha": None, "bytes_per_launch": None}
+
+
+def kernel_source_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("hl_device.cuh", "hl_kernels.cu", "hl_internal.h"):
+        with open(os.path.join(ROOT, "paper_2510_13726_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def run_cuda(args):
+    import torch
+    import workloads as W
+    from paper_2510_13726_b300 import Lattice
+    from paper_2510_13726_b300.perf import collide_bytes
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist_init("nccl")
+    dev = torch.device("cuda", local)
+
+    wl = W.workload(args.workload)
+    lat = Lattice.from_workload(wl, storage=args.storage, device=dev)
+    stream = lat.stream
+    K, Wm = args.steps, args.warmup
+    lat.step(Wm)
+
+    # ---- device-timed region ------------------------------------------------
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    lat.profile_begin(4 * K + 16)
+    e0.record(stream)
+    lat.step_async(K)
+    e1.record(stream)
+    e1.synchronize()
+    prof = lat.profile_end()
+    lat.check()
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    barrier()
+    elapsed = e0.elapsed_time(e1) / 1e3
+    value, t_max = aggregate(elapsed, wl.cells, K, world, device=dev)
+
+    # ---- roofline of the dominant kernel (collide-and-stream) ----------------
+    band = lat.rotor_band(0)
+    box_cells = int(band["d"].numel())
+    wall_cells = int(((band["flags"] & 2) > 0).sum().item())
+    alg_bytes = collide_bytes(wl.q, args.storage, wl.cells, box_cells, wall_cells)
+    c_ms, c_n = prof["collide"]
+    per_launch_s = c_ms / c_n / 1e3
+    achieved = alg_bytes / per_launch_s / 1e9
+    peak, peak_src = measured_peaks()
+    sha = kernel_source_sha()
+    traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["source_sha"] == sha else None
+    total_kernel_ms = sum(v[0] for v in prof.values())
+    kernels = {k: {"launches": n, "ms_per_launch": round(ms / n, 4) if n else None,
+                   "share": round(ms / total_kernel_ms, 4) if total_kernel_ms else None}
+               for k, (ms, n) in prof.items()}
+    launches = sum(n for _, n in prof.values())
+
+    # ---- end to end through the public API with host buffers ----------------
+    # per step: hl_step (launches + stream sync + device error word to host)
+    # and hl_forces / hl_moments into host arrays (thrust and torque every step)
+    K2 = max(1, min(K, 200))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(K2):
+        lat.step(1)
+        F, Fa = lat.forces()
+        M, Ma = lat.moments()
+    t_e2e = time.perf_counter() - t0
+    e2e_value, _ = aggregate(t_e2e, wl.cells, K2, world, device=dev)
+    d2h = 4 + 2 * 12 * 8 * lat.nrot      # error word + two reads of 12 doubles per rotor
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            mlups, dt, cores, desc = oracle_sample(args.cpu_steps)
+            cpu = {"value": round(mlups, 4), "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+        line = {
+            "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": Wm, "ms_per_step": round(1e3 * t_max / K, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.storage == "f32" else "f32-math/" + args.storage,
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC if args.workload == "rotor256" else wl.note,
+                       "name": args.workload, "cells": wl.cells, "q": wl.q, "storage": args.storage,
+                       "rotors": len(wl.rotors), "parallelism": f"replicas x{world}",
+                       "l2": "no flush: the populations (%.2f GB) exceed the 126 MB L2" %
+                             (wl.cells * wl.q * (4 if args.storage == "f32" else 2) / 1e9)},
+            "roofline": {"bound": "hbm", "kernel": "collide_kernel", "achieved": round(achieved, 1),
+                         "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                         "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
+                         else "fallback", "traffic": traffic,
+                         "alg_bytes_per_launch": alg_bytes,
+                         "frac_of_8TBps_nominal": round(achieved / 8000.0, 4)},
+            "kernels": kernels,
+            "gpu_launches": launches,
+            "clocks": clk,
+            "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": d2h, "steps": K2,
+                    "per_step": "hl_step (sync + error word) + hl_forces + hl_moments to host"},
+            "thrust_last": float(F[0, wl.flow_axis]) if lat.nrot else None,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    lat.close()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
+    ap.add_argument("--workload", default="rotor256")
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16s", "bf16s"])
+    ap.add_argument("--cpu-steps", type=int, default=40)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3 and args.impl == "cuda":
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_cuda(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

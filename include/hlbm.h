@@ -208,6 +208,16 @@ hl_status hl_debug_collide(int q, int n, const float* d_g_in, const float* d_d, 
                            const float* d_sigma, const float* d_S, double tau_mo, double c_smag,
                            float* d_g_out, void* stream);
 
+/* Per-kernel timing with CUDA events recorded on the lattice's stream around
+ * each launch of the time loop.  hl_profile_begin(lat, capacity) starts
+ * recording (at most `capacity` launches per kernel kind; it creates CUDA
+ * events, it allocates no device memory); hl_profile_end synchronises,
+ * returns for each kind (0 band: embedding + wall model, 1 collide-and-stream,
+ * 2 force reduction, 3 mass check) the summed duration in ms and the number of
+ * launches, and releases the events.  Either output may be NULL. */
+hl_status hl_profile_begin(hl_lattice* lat, int capacity);
+hl_status hl_profile_end(hl_lattice* lat, double* ms, long long* launches);
+
 /* Text of the last error of the handle (never NULL). */
 const char* hl_last_error(const hl_lattice* lat);
 

@@ -74,6 +74,8 @@ SIGNATURES = {
     "hl_velocity_set": (C.c_int, [C.c_int, _ip, _dp]),
     "hl_debug_collide": (C.c_int, [C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, C.c_double, C.c_double,
                                    _vp, _vp]),
+    "hl_profile_begin": (C.c_int, [_vp, C.c_int]),
+    "hl_profile_end": (C.c_int, [_vp, _dp, C.POINTER(C.c_longlong)]),
     "hl_last_error": (C.c_char_p, [_vp]),
     "hl_destroy": (None, [_vp]),
 }

@@ -91,6 +91,10 @@ struct hl_lattice {
     int nrot;
     RotorHost rot[MAXROT];
     char msg[256];
+    // per-kernel event timing (hl_profile_begin / hl_profile_end)
+    bool prof_on;
+    int prof_cap;
+    std::vector<cudaEvent_t> prof_ev[4];   // start/stop pairs per kernel kind
 };
 
 namespace {
@@ -264,9 +268,8 @@ hl_status hl_lattice_init(hl_lattice** out, const hl_config* cfg, void* d_worksp
     if (reinterpret_cast<size_t>(d_workspace) % ALIGN) return HL_ERR_ARG;
     const Layout L = lattice_layout(*cfg);
     if (bytes < L.total) return HL_ERR_WORKSPACE;
-    hl_lattice* lat = new (std::nothrow) hl_lattice;
+    hl_lattice* lat = new (std::nothrow) hl_lattice();
     if (!lat) return HL_ERR_ARG;
-    std::memset(lat, 0, sizeof *lat);
     lat->cfg = *cfg;
     lat->cfg.modes = nullptr;
     lat->N = (long long)cfg->nx * cfg->ny * cfg->nz;
@@ -414,23 +417,81 @@ hl_status hl_set_rotor(hl_lattice* lat, int* rotor_id, const hl_rotor_geometry* 
     return HL_OK;
 }
 
+// records one event of kind k when profiling (start: even index, stop: odd)
+static cudaError_t prof_mark(hl_lattice* lat, int k) {
+    if (!lat->prof_on) return cudaSuccess;
+    std::vector<cudaEvent_t>& v = lat->prof_ev[k];
+    if ((int)v.size() >= 2 * lat->prof_cap) return cudaSuccess;
+    cudaEvent_t e;
+    cudaError_t err = cudaEventCreate(&e);
+    if (err != cudaSuccess) return err;
+    v.push_back(e);
+    return cudaEventRecord(e, lat->stream);
+}
+
 hl_status hl_step_async(hl_lattice* lat, int n) {
     if (!lat || n < 0) return HL_ERR_ARG;
     const int Q = lat->cfg.q, S = lat->cfg.storage;
     for (int s = 0; s < n; ++s) {
         const StepArgs a = make_args(lat);
-        if (lat->nrot > 0) HL_CUDA(lat, launch_band(Q, S, a, lat->stream));
+        if (lat->nrot > 0) {
+            HL_CUDA(lat, prof_mark(lat, 0));
+            HL_CUDA(lat, launch_band(Q, S, a, lat->stream));
+            HL_CUDA(lat, prof_mark(lat, 0));
+        }
+        HL_CUDA(lat, prof_mark(lat, 1));
         HL_CUDA(lat, launch_collide(Q, S, a, lat->stream));
-        if (lat->nrot > 0) HL_CUDA(lat, launch_force(Q, S, a, lat->stream));
+        HL_CUDA(lat, prof_mark(lat, 1));
+        if (lat->nrot > 0) {
+            HL_CUDA(lat, prof_mark(lat, 2));
+            HL_CUDA(lat, launch_force(Q, S, a, lat->stream));
+            HL_CUDA(lat, prof_mark(lat, 2));
+        }
         lat->t += 1;
         lat->n_avg += 1;
         const int K = lat->cfg.mass_check_every;
         if (K > 0 && lat->t % K == 0) {
+            HL_CUDA(lat, prof_mark(lat, 3));
             hl_status st = compute_mass(lat, lat->cfg.mass_tol, nullptr);
             if (st != HL_OK) return st;
+            HL_CUDA(lat, prof_mark(lat, 3));
         }
     }
     return HL_OK;
+}
+
+hl_status hl_profile_begin(hl_lattice* lat, int capacity) {
+    if (!lat || capacity < 0) return HL_ERR_ARG;
+    for (auto& v : lat->prof_ev) {
+        for (cudaEvent_t e : v) cudaEventDestroy(e);
+        v.clear();
+    }
+    lat->prof_cap = capacity;
+    lat->prof_on = true;
+    return HL_OK;
+}
+
+hl_status hl_profile_end(hl_lattice* lat, double* ms, long long* launches) {
+    if (!lat) return HL_ERR_ARG;
+    lat->prof_on = false;
+    HL_CUDA(lat, cudaStreamSynchronize(lat->stream));
+    hl_status st = HL_OK;
+    for (int k = 0; k < 4; ++k) {
+        std::vector<cudaEvent_t>& v = lat->prof_ev[k];
+        double sum = 0.0;
+        const size_t pairs = v.size() / 2;
+        for (size_t i = 0; i < pairs; ++i) {
+            float t = 0.f;
+            cudaError_t e = cudaEventElapsedTime(&t, v[2 * i], v[2 * i + 1]);
+            if (e != cudaSuccess && st == HL_OK) st = cuda_fail(lat, e, "cudaEventElapsedTime");
+            sum += t;
+        }
+        if (ms) ms[k] = sum;
+        if (launches) launches[k] = (long long)pairs;
+        for (cudaEvent_t e : v) cudaEventDestroy(e);
+        v.clear();
+    }
+    return st;
 }
 
 hl_status hl_check(hl_lattice* lat) {
@@ -672,6 +733,11 @@ hl_status hl_debug_collide(int q, int n, const float* d_g_in, const float* d_d, 
 
 const char* hl_last_error(const hl_lattice* lat) { return lat ? lat->msg : "null handle"; }
 
-void hl_destroy(hl_lattice* lat) { delete lat; }
+void hl_destroy(hl_lattice* lat) {
+    if (!lat) return;
+    for (auto& v : lat->prof_ev)
+        for (cudaEvent_t e : v) cudaEventDestroy(e);
+    delete lat;
+}
 
 }  // extern "C"

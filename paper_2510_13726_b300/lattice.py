@@ -194,6 +194,19 @@ class Lattice:
         self._check(lib().hl_mass(self._h, C.byref(m)))
         return m.value
 
+    # -- per-kernel timing ----------------------------------------------------
+    KERNELS = ("band", "collide", "force", "mass")
+
+    def profile_begin(self, capacity: int = 100000):
+        self._check(lib().hl_profile_begin(self._h, int(capacity)))
+
+    def profile_end(self):
+        """{kernel: (total ms, launches)} of the launches since profile_begin."""
+        ms = np.zeros(4)
+        n = (C.c_longlong * 4)()
+        self._check(lib().hl_profile_end(self._h, ms.ctypes.data_as(C.POINTER(C.c_double)), n))
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(self.KERNELS)}
+
     # -- checkpoints --------------------------------------------------------
     def state_size(self) -> int:
         s = C.c_size_t()
