@@ -218,6 +218,28 @@ hl_status hl_debug_collide(int q, int n, const float* d_g_in, const float* d_d, 
 hl_status hl_profile_begin(hl_lattice* lat, int capacity);
 hl_status hl_profile_end(hl_lattice* lat, double* ms, long long* launches);
 
+/* Total mass of a population array, without allocating anything.
+ * The paper has no counterpart: this is a service for callers that cannot
+ * allocate device memory when they need the total (code inside a memory pool
+ * that forbids new allocations, a driver that has given all device memory to
+ * the lattice, a callback whose allocator is not re-entrant).  The block
+ * partial sums live in a fixed array in the library's own static device
+ * memory (4096 doubles plus a counter, held by every GPU that loads the
+ * library until the process exits); nothing is allocated, by the library or
+ * by any library it calls.
+ *  q, storage  lattice (19 or 27) and storage kind (HL_STORE_*) of d_f
+ *  d_f         device populations [q][n_cells], stored as f_i - w_i
+ *  d_mass      device output: sum_x sum_i f_i in FP64
+ *  stream      cudaStream_t as void*; the call is asynchronous
+ * At most 2^32 stored values (q * n_cells) are accepted: larger arrays return
+ * HL_ERR_WORKSPACE.  The first call on a device looks up the array's device
+ * address (once per device, with that device current), so make that first
+ * call before any stream capture.  All calls share the one array: calls that
+ * overlap on the GPU (two streams, or two threads) race and must be ordered
+ * by the caller. */
+hl_status hl_mass_noalloc(int q, int storage, const void* d_f, long long n_cells, double* d_mass,
+                          void* stream);
+
 /* Text of the last error of the handle (never NULL). */
 const char* hl_last_error(const hl_lattice* lat);
 

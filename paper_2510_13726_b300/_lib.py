@@ -76,6 +76,7 @@ SIGNATURES = {
                                    _vp, _vp]),
     "hl_profile_begin": (C.c_int, [_vp, C.c_int]),
     "hl_profile_end": (C.c_int, [_vp, _dp, C.POINTER(C.c_longlong)]),
+    "hl_mass_noalloc": (C.c_int, [C.c_int, C.c_int, _vp, C.c_longlong, _vp, _vp]),
     "hl_last_error": (C.c_char_p, [_vp]),
     "hl_destroy": (None, [_vp]),
 }

@@ -16,7 +16,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
-SOURCES = [os.path.join(CSRC, f) for f in ("hl_kernels.cu", "hl_api.cu")]
+SOURCES = [os.path.join(CSRC, f) for f in ("hl_kernels.cu", "hl_api.cu", "hl_noalloc.cu")]
 HEADERS = [os.path.join(CSRC, f) for f in ("hl_device.cuh", "hl_internal.h")] + [
     os.path.join(ROOT, "include", "hlbm.h")]
 LIB = os.path.join(HERE, "libhlbm.so")
