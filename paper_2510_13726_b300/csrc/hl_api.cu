@@ -44,7 +44,7 @@ Layout lattice_layout(const hl_config& c) {
 }
 
 struct RotorLayout {
-    size_t sdf, d, flags, wm, utau, active, list, count, done, partial, acc, total;
+    size_t sdf, d, flags, wm, utau, active, list, wlist, wphi, wwhich, count, done, partial, acc, total;
 };
 
 RotorLayout rotor_layout(long long ngrid, long long box) {
@@ -57,7 +57,10 @@ RotorLayout rotor_layout(long long ngrid, long long box) {
     L.utau = o; o = align_up(o + sizeof(double) * box);
     L.active = o; o = align_up(o + box);
     L.list = o; o = align_up(o + sizeof(int) * box);
-    L.count = o; o = align_up(o + sizeof(int));
+    L.wlist = o; o = align_up(o + sizeof(int) * box);
+    L.wphi = o; o = align_up(o + sizeof(float) * box);
+    L.wwhich = o; o = align_up(o + box);
+    L.count = o; o = align_up(o + 2 * sizeof(int));
     L.done = o; o = align_up(o + sizeof(unsigned));
     L.partial = o; o = align_up(o + sizeof(double) * 6 * FORCE_BLOCKS);
     L.acc = o; o = align_up(o + sizeof(double) * 12);
@@ -137,7 +140,11 @@ StepArgs make_args(const hl_lattice* lat) {
     std::memset(&a, 0, sizeof a);
     a.f = lat->f;
     a.N = lat->N;
+    for (int q = 0; q < c.q; ++q)
+        a.slot[q] = static_cast<char*>(lat->f) + (size_t)q * lat->N * store_bytes(c.storage);
     a.n[0] = c.nx; a.n[1] = c.ny; a.n[2] = c.nz;
+    a.nxy = c.nx * c.ny;
+    a.nplane = (int)plane_cells(c);
     a.phase = (int)(lat->t & 1);
     a.t = lat->t;
     a.flow_axis = c.flow_axis;
@@ -295,8 +302,7 @@ hl_status hl_lattice_init(hl_lattice** out, const hl_config* cfg, void* d_worksp
     if (e != cudaSuccess) { delete lat; return HL_ERR_CUDA; }
     float u0[3] = {0.f, 0.f, 0.f};
     u0[cfg->flow_axis] = (float)cfg->u_in;
-    const int n[3] = {cfg->nx, cfg->ny, cfg->nz};
-    e = launch_init(cfg->q, cfg->storage, lat->f, lat->N, n, nullptr, nullptr, 0.0f, u0, lat->stream);
+    e = launch_init(cfg->q, cfg->storage, make_args(lat), nullptr, nullptr, 0.0f, u0, lat->stream);
     if (e != cudaSuccess) { delete lat; return HL_ERR_CUDA; }
     if ((st = reset_outlet_plane(lat, u0)) != HL_OK) { delete lat; return st; }
     double m0 = 0.0;
@@ -306,7 +312,10 @@ hl_status hl_lattice_init(hl_lattice** out, const hl_config* cfg, void* d_worksp
     return HL_OK;
 }
 
-static bool rotor_box(const hl_lattice* lat, const hl_rotor_geometry* g, int lo[3], int nn[3]) {
+// reach of a rotor: every cell from which a blade sample can land inside the
+// blade grid (any angle, any pitch) lies within reach_plane of the axis and
+// reach_axial along it; the hub sphere is included up to eps/2 beyond it
+static void rotor_reach(const hl_lattice* lat, const hl_rotor_geometry* g, double* reach_plane, double* reach_axial) {
     const double h = g->spacing;
     const double R0 = g->origin[0], R1 = g->origin[0] + h * (g->gx - 1);
     const double T0 = g->origin[1], T1 = g->origin[1] + h * (g->gy - 1);
@@ -316,8 +325,14 @@ static bool rotor_box(const hl_lattice* lat, const hl_rotor_geometry* g, int lo[
     const double amax = std::fmax(std::fabs(A0), std::fabs(A1));
     const double w = std::hypot(tmax, amax);     // the pitch rotation mixes T and A
     const double hubr = g->hub_radius > 0 ? g->hub_radius + 0.5 * lat->cfg.eps_h : 0.0;
-    const double reach_plane = std::fmax(g->n_blades > 0 ? std::hypot(rmax, w) : 0.0, hubr) + 2.0;
-    const double reach_axial = std::fmax(g->n_blades > 0 ? w : 0.0, hubr) + 2.0;
+    *reach_plane = std::fmax(g->n_blades > 0 ? std::hypot(rmax, w) : 0.0, hubr);
+    *reach_axial = std::fmax(g->n_blades > 0 ? w : 0.0, hubr);
+}
+
+static bool rotor_box(const hl_lattice* lat, const hl_rotor_geometry* g, int lo[3], int nn[3]) {
+    double rp, ra;
+    rotor_reach(lat, g, &rp, &ra);
+    const double reach_plane = rp + 2.0, reach_axial = ra + 2.0;
     const int dims[3] = {lat->cfg.nx, lat->cfg.ny, lat->cfg.nz};
     for (int k = 0; k < 3; ++k) {
         const double r = (k == g->axis) ? reach_axial : reach_plane;
@@ -396,6 +411,14 @@ hl_status hl_set_rotor(hl_lattice* lat, int* rotor_id, const hl_rotor_geometry* 
     D.hub = (float)geom->hub_radius;
     D.inv_h = (float)(1.0 / geom->spacing);
     D.h = (float)geom->spacing;
+    {
+        double rp, ra;
+        rotor_reach(lat, geom, &rp, &ra);
+        rp += 1.0;   // one cell of margin covers every binary32 rounding of the test
+        ra += 1.0;
+        D.reach_plane2 = (float)(rp * rp);
+        D.reach_axial = (float)ra;
+    }
     D.sdf = reinterpret_cast<const float*>(R.ws + L.sdf);
     D.d = reinterpret_cast<float*>(R.ws + L.d);
     D.flags = reinterpret_cast<uint8_t*>(R.ws + L.flags);
@@ -403,6 +426,9 @@ hl_status hl_set_rotor(hl_lattice* lat, int* rotor_id, const hl_rotor_geometry* 
     D.utau = reinterpret_cast<double*>(R.ws + L.utau);
     D.active = reinterpret_cast<uint8_t*>(R.ws + L.active);
     D.list = reinterpret_cast<int*>(R.ws + L.list);
+    D.wlist = reinterpret_cast<int*>(R.ws + L.wlist);
+    D.wphi = reinterpret_cast<float*>(R.ws + L.wphi);
+    D.wwhich = reinterpret_cast<signed char*>(R.ws + L.wwhich);
     D.count = reinterpret_cast<int*>(R.ws + L.count);
     D.done = reinterpret_cast<unsigned*>(R.ws + L.done);
     D.partial = reinterpret_cast<double*>(R.ws + L.partial);
@@ -437,6 +463,7 @@ hl_status hl_step_async(hl_lattice* lat, int n) {
         if (lat->nrot > 0) {
             HL_CUDA(lat, prof_mark(lat, 0));
             HL_CUDA(lat, launch_band(Q, S, a, lat->stream));
+            HL_CUDA(lat, launch_wall(Q, S, a, lat->stream));
             HL_CUDA(lat, prof_mark(lat, 0));
         }
         HL_CUDA(lat, prof_mark(lat, 1));
@@ -558,8 +585,7 @@ hl_status hl_fields(hl_lattice* lat, float* d_rho, float* d_u) {
 hl_status hl_init_fields(hl_lattice* lat, const float* d_rho, const float* d_u) {
     if (!lat) return HL_ERR_ARG;
     const float u0[3] = {0.f, 0.f, 0.f};
-    const int n[3] = {lat->cfg.nx, lat->cfg.ny, lat->cfg.nz};
-    HL_CUDA(lat, launch_init(lat->cfg.q, lat->cfg.storage, lat->f, lat->N, n, d_rho, d_u, 0.0f, u0,
+    HL_CUDA(lat, launch_init(lat->cfg.q, lat->cfg.storage, make_args(lat), d_rho, d_u, 0.0f, u0,
                              lat->stream));
     lat->t = 0;
     lat->n_avg = 0;
@@ -704,7 +730,7 @@ hl_status hl_velocity_set(int q, int* c, double* w) {
             int v = 0;
             if (s >= 1) {
                 const int p = s <= P ? s - 1 : s - 1 - P;
-                v = q == 19 ? Lat<19>::c[p][a] : Lat<27>::c[p][a];
+                v = cpos(q, p, a);
                 if (s > P) v = -v;
             }
             c[3 * s + a] = v;

@@ -17,58 +17,38 @@ namespace hl {
 
 // ---------------------------------------------------------------------------
 // velocity sets (Sec. 2.2, Fig. "D3Q19"; D3Q27 is its product-lattice sibling)
+//
+// The P = (Q-1)/2 "positive" velocities are encoded as bit masks per axis
+// (bit p set: component non-zero; second mask: component negative), so the
+// components are constant expressions of (Q, p, axis) without any table:
+// inside fully unrolled loops every branch on them folds away.
+//   D3Q19 p = 0..8 : (1,0,0) (0,1,0) (0,0,1) (1,1,0) (1,-1,0) (1,0,1) (1,0,-1) (0,1,1) (0,1,-1)
+//   D3Q27 p = 9..12: (1,1,1) (1,1,-1) (1,-1,1) (1,-1,-1)
 // ---------------------------------------------------------------------------
-template <int Q>
-struct Lat;
+__host__ __device__ constexpr int npos(int Q) { return (Q - 1) / 2; }
 
-template <>
-struct Lat<19> {
-    static constexpr int Q = 19, P = 9;
-    static constexpr int c[P][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {1, 1, 0}, {1, -1, 0},
-                                    {1, 0, 1}, {1, 0, -1}, {0, 1, 1}, {0, 1, -1}};
-    __host__ __device__ static constexpr float w0() { return 1.0f / 3.0f; }
-    __host__ __device__ static constexpr float wp(int p) {
-        return (c[p][0] * c[p][0] + c[p][1] * c[p][1] + c[p][2] * c[p][2]) == 1 ? 1.0f / 18.0f
-                                                                               : 1.0f / 36.0f;
-    }
-};
-
-template <>
-struct Lat<27> {
-    static constexpr int Q = 27, P = 13;
-    static constexpr int c[P][3] = {{1, 0, 0},  {0, 1, 0},  {0, 0, 1},  {1, 1, 0},  {1, -1, 0},
-                                    {1, 0, 1},  {1, 0, -1}, {0, 1, 1},  {0, 1, -1}, {1, 1, 1},
-                                    {1, 1, -1}, {1, -1, 1}, {1, -1, -1}};
-    __host__ __device__ static constexpr float w0() { return 8.0f / 27.0f; }
-    __host__ __device__ static constexpr float wp(int p) {
-        return (c[p][0] * c[p][0] + c[p][1] * c[p][1] + c[p][2] * c[p][2]) == 1   ? 2.0f / 27.0f
-               : (c[p][0] * c[p][0] + c[p][1] * c[p][1] + c[p][2] * c[p][2]) == 2 ? 1.0f / 54.0f
-                                                                                  : 1.0f / 216.0f;
-    }
-};
-
-// slot s -> velocity component a (s = 0 rest, 1..P plus, P+1..2P minus)
-template <int Q>
-__host__ __device__ constexpr int slot_c(int s, int a) {
-    return s == 0 ? 0 : (s <= Lat<Q>::P ? Lat<Q>::c[s - 1][a] : -Lat<Q>::c[s - 1 - Lat<Q>::P][a]);
-}
-template <int Q>
-__host__ __device__ constexpr int slot_opp(int s) {
-    return s == 0 ? 0 : (s <= Lat<Q>::P ? s + Lat<Q>::P : s - Lat<Q>::P);
-}
-template <int Q>
-__host__ __device__ constexpr float slot_w(int s) {
-    return s == 0 ? Lat<Q>::w0() : Lat<Q>::wp(s <= Lat<Q>::P ? s - 1 : s - 1 - Lat<Q>::P);
+__host__ __device__ constexpr int cpos(int Q, int p, int a) {
+    return ((((Q == 19) ? (a == 0 ? 121u : a == 1 ? 410u : 484u)
+                        : (a == 0 ? 7801u : a == 1 ? 8090u : 8164u)) >> p) & 1u)
+               ? (((((Q == 19) ? (a == 0 ? 0u : a == 1 ? 16u : 320u)
+                               : (a == 0 ? 0u : a == 1 ? 6160u : 5440u)) >> p) & 1u) ? -1 : 1)
+               : 0;
 }
 
-// compile-time loop: f(std::integral_constant<int, i>) for i = 0..N-1
-template <class F, int... I>
-__device__ __forceinline__ void sfor_impl(F& f, std::integer_sequence<int, I...>) {
-    (f(std::integral_constant<int, I>{}), ...);
+// slot s: 0 rest, 1..P positive velocities, P+1..2P their opposites
+__host__ __device__ constexpr int cslot(int Q, int s, int a) {
+    return s == 0 ? 0 : (s <= npos(Q) ? cpos(Q, s - 1, a) : -cpos(Q, s - 1 - npos(Q), a));
 }
-template <int N, class F>
-__device__ __forceinline__ void sfor(F&& f) {
-    sfor_impl(f, std::make_integer_sequence<int, N>{});
+__host__ __device__ constexpr int oslot(int Q, int s) {
+    return s == 0 ? 0 : (s <= npos(Q) ? s + npos(Q) : s - npos(Q));
+}
+__host__ __device__ constexpr int shell(int Q, int p) {
+    return cpos(Q, p, 0) * cpos(Q, p, 0) + cpos(Q, p, 1) * cpos(Q, p, 1) + cpos(Q, p, 2) * cpos(Q, p, 2);
+}
+__host__ __device__ constexpr float w0(int Q) { return Q == 19 ? 1.0f / 3.0f : 8.0f / 27.0f; }
+__host__ __device__ constexpr float wpos(int Q, int p) {
+    return Q == 19 ? (shell(Q, p) == 1 ? 1.0f / 18.0f : 1.0f / 36.0f)
+                   : (shell(Q, p) == 1 ? 2.0f / 27.0f : (shell(Q, p) == 2 ? 1.0f / 54.0f : 1.0f / 216.0f));
 }
 
 // ---------------------------------------------------------------------------
@@ -115,55 +95,74 @@ struct Band {
 // A3 = rho u u u + (1-1/tau) sigma a1^(3).  For c in {-1,0,1}^3,
 // H2:A = sum_a c_a^2 A_aa - tr(A)/3 + 2 sum_{a<b} c_a c_b A_ab and
 // H3:A3 = sum_{a!=b} (3 c_a^2 - 1) c_b A3_aab + 6 c_x c_y c_z A3_xyz.
+// Each pair (i, ibar) shares the even part and flips the odd part.
 template <int Q>
 __device__ __forceinline__ void assemble(float (&g)[Q], float drho, float rho, const float (&u)[3],
                                          const float (&A)[6], const float (&M)[6], float Axyz) {
-    using L = Lat<Q>;
-    constexpr int P = L::P;
+    constexpr int P = npos(Q);
     const float trA = A[0] + A[1] + A[2];
-    g[0] = L::w0() * (drho - 1.5f * trA);
+    g[0] = w0(Q) * (drho - 1.5f * trA);
     const float r3 = 3.0f * rho;
-    sfor<P>([&](auto I) {
-        constexpr int p = decltype(I)::value;
-        constexpr int cx = L::c[p][0], cy = L::c[p][1], cz = L::c[p][2];
-        constexpr float w = L::wp(p);
+    const float t3 = trA * (1.0f / 3.0f);
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const int cx = cpos(Q, p, 0), cy = cpos(Q, p, 1), cz = cpos(Q, p, 2);
+        const float w = wpos(Q, p);
         // even part: rho + 9/2 H2:A
-        float h2 = -trA * (1.0f / 3.0f);
-        if constexpr (cx != 0) h2 += A[0];
-        if constexpr (cy != 0) h2 += A[1];
-        if constexpr (cz != 0) h2 += A[2];
-        if constexpr (cx * cy != 0) h2 += float(2 * cx * cy) * A[3];
-        if constexpr (cx * cz != 0) h2 += float(2 * cx * cz) * A[4];
-        if constexpr (cy * cz != 0) h2 += float(2 * cy * cz) * A[5];
+        float h2 = -t3;
+        if (cx != 0) h2 += A[0];
+        if (cy != 0) h2 += A[1];
+        if (cz != 0) h2 += A[2];
+        if (cx * cy != 0) h2 += float(2 * cx * cy) * A[3];
+        if (cx * cz != 0) h2 += float(2 * cx * cz) * A[4];
+        if (cy * cz != 0) h2 += float(2 * cy * cz) * A[5];
         // odd part: 3 rho c.u + 9/2 H3:A3; M = (A3_xxy, A3_yyx, A3_xxz, A3_zzx, A3_yyz, A3_zzy)
         float cu = 0.0f;
-        if constexpr (cx != 0) cu += float(cx) * u[0];
-        if constexpr (cy != 0) cu += float(cy) * u[1];
-        if constexpr (cz != 0) cu += float(cz) * u[2];
+        if (cx != 0) cu += float(cx) * u[0];
+        if (cy != 0) cu += float(cy) * u[1];
+        if (cz != 0) cu += float(cz) * u[2];
         float h3 = 0.0f;
-        if constexpr (cy != 0) h3 += float((3 * cx * cx - 1) * cy) * M[0];
-        if constexpr (cx != 0) h3 += float((3 * cy * cy - 1) * cx) * M[1];
-        if constexpr (cz != 0) h3 += float((3 * cx * cx - 1) * cz) * M[2];
-        if constexpr (cx != 0) h3 += float((3 * cz * cz - 1) * cx) * M[3];
-        if constexpr (cz != 0) h3 += float((3 * cy * cy - 1) * cz) * M[4];
-        if constexpr (cy != 0) h3 += float((3 * cz * cz - 1) * cy) * M[5];
-        if constexpr (Q == 27 && cx * cy * cz != 0) h3 += float(6 * cx * cy * cz) * Axyz;
+        if (cy != 0) h3 += float((3 * cx * cx - 1) * cy) * M[0];
+        if (cx != 0) h3 += float((3 * cy * cy - 1) * cx) * M[1];
+        if (cz != 0) h3 += float((3 * cx * cx - 1) * cz) * M[2];
+        if (cx != 0) h3 += float((3 * cz * cz - 1) * cx) * M[3];
+        if (cz != 0) h3 += float((3 * cy * cy - 1) * cz) * M[4];
+        if (cy != 0) h3 += float((3 * cz * cz - 1) * cy) * M[5];
+        if (Q == 27 && cx * cy * cz != 0) h3 += float(6 * cx * cy * cz) * Axyz;
         const float E = w * (drho + 4.5f * h2);
         const float O = w * (r3 * cu + 4.5f * h3);
         g[1 + p] = E + O;
         g[1 + P + p] = E - O;
-    });
+    }
 }
 
 // Shifted third-order equilibrium g^eq_i = f^eq_i(rho, u) - w_i.
 template <int Q>
 __device__ __forceinline__ void equilibrium(float (&g)[Q], float drho, const float (&u)[3]) {
     const float rho = 1.0f + drho;
-    float A[6] = {rho * u[0] * u[0], rho * u[1] * u[1], rho * u[2] * u[2],
-                  rho * u[0] * u[1], rho * u[0] * u[2], rho * u[1] * u[2]};
-    float M[6] = {A[0] * u[1], A[1] * u[0], A[0] * u[2], A[2] * u[0], A[1] * u[2], A[2] * u[1]};
-    float Axyz = A[3] * u[2];
+    const float A[6] = {rho * u[0] * u[0], rho * u[1] * u[1], rho * u[2] * u[2],
+                        rho * u[0] * u[1], rho * u[0] * u[2], rho * u[1] * u[2]};
+    const float M[6] = {A[0] * u[1], A[1] * u[0], A[0] * u[2], A[2] * u[0], A[1] * u[2], A[2] * u[1]};
+    const float Axyz = A[3] * u[2];
     assemble<Q>(g, drho, rho, u, A, M, Axyz);
+}
+
+// Moments of shifted populations: drho = sum g, j = sum c g.
+template <int Q>
+__device__ __forceinline__ void moments01(const float (&g)[Q], float& drho, float (&j)[3]) {
+    constexpr int P = npos(Q);
+    drho = g[0];
+    j[0] = j[1] = j[2] = 0.0f;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const int cx = cpos(Q, p, 0), cy = cpos(Q, p, 1), cz = cpos(Q, p, 2);
+        const float s = g[1 + p] + g[1 + P + p];
+        const float d = g[1 + p] - g[1 + P + p];
+        drho += s;
+        if (cx != 0) j[0] += float(cx) * d;
+        if (cy != 0) j[1] += float(cy) * d;
+        if (cz != 0) j[2] += float(cz) * d;
+    }
 }
 
 // One collision in place on shifted populations.  BAND selects the
@@ -172,32 +171,31 @@ __device__ __forceinline__ void equilibrium(float (&g)[Q], float drho, const flo
 template <int Q, bool BAND>
 __device__ __forceinline__ float collide(float (&g)[Q], const Band& B, float tau_mo, float Ksmag,
                                          float (&u_out)[3]) {
-    using L = Lat<Q>;
-    constexpr int P = L::P;
+    constexpr int P = npos(Q);
     float drho = g[0];
     float j[3] = {0.f, 0.f, 0.f};
     float pg[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // sum c_a c_b g: xx yy zz xy xz yz
-    sfor<P>([&](auto I) {
-        constexpr int p = decltype(I)::value;
-        constexpr int cx = L::c[p][0], cy = L::c[p][1], cz = L::c[p][2];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const int cx = cpos(Q, p, 0), cy = cpos(Q, p, 1), cz = cpos(Q, p, 2);
         const float s = g[1 + p] + g[1 + P + p];
         const float d = g[1 + p] - g[1 + P + p];
         drho += s;
-        if constexpr (cx != 0) { j[0] += float(cx) * d; pg[0] += s; }
-        if constexpr (cy != 0) { j[1] += float(cy) * d; pg[1] += s; }
-        if constexpr (cz != 0) { j[2] += float(cz) * d; pg[2] += s; }
-        if constexpr (cx * cy != 0) pg[3] += float(cx * cy) * s;
-        if constexpr (cx * cz != 0) pg[4] += float(cx * cz) * s;
-        if constexpr (cy * cz != 0) pg[5] += float(cy * cz) * s;
-    });
+        if (cx != 0) { j[0] += float(cx) * d; pg[0] += s; }
+        if (cy != 0) { j[1] += float(cy) * d; pg[1] += s; }
+        if (cz != 0) { j[2] += float(cz) * d; pg[2] += s; }
+        if (cx * cy != 0) pg[3] += float(cx * cy) * s;
+        if (cx * cz != 0) pg[4] += float(cx * cz) * s;
+        if (cy * cz != 0) pg[5] += float(cy * cz) * s;
+    }
     const float rho = 1.0f + drho;
     const float inv = 1.0f / rho;
-    float u[3] = {j[0] * inv, j[1] * inv, j[2] * inv};
+    const float u[3] = {j[0] * inv, j[1] * inv, j[2] * inv};
     u_out[0] = u[0]; u_out[1] = u[1]; u_out[2] = u[2];
     // non-equilibrium stress Pi_neq = Pi - rho cs2 I - rho u u (fluid velocity)
     const float dr3 = drho * (1.0f / 3.0f);
-    float N[6] = {pg[0] - dr3 - j[0] * u[0], pg[1] - dr3 - j[1] * u[1], pg[2] - dr3 - j[2] * u[2],
-                  pg[3] - j[0] * u[1],       pg[4] - j[0] * u[2],       pg[5] - j[1] * u[2]};
+    const float N[6] = {pg[0] - dr3 - j[0] * u[0], pg[1] - dr3 - j[1] * u[1], pg[2] - dr3 - j[2] * u[2],
+                        pg[3] - j[0] * u[1],       pg[4] - j[0] * u[2],       pg[5] - j[1] * u[2]};
     // Smagorinsky, Eqs. (turbVisc), (tauEff): positive root of
     // tau = tau_mo + 3 C_S^2 |S|, S = -Pi_neq / (2 rho cs2 tau)
     const float Qn = N[0] * N[0] + N[1] * N[1] + N[2] * N[2] +
@@ -231,12 +229,12 @@ __device__ __forceinline__ float collide(float (&g)[Q], const Band& B, float tau
     }
     // third order: A3_aab = rho u_a^2 u_b + om sigma (2 u_a N_ab + u_b N_aa) (recursion with u^)
     const float rxx = rho * uh[0] * uh[0], ryy = rho * uh[1] * uh[1], rzz = rho * uh[2] * uh[2];
-    float M[6] = {rxx * uh[1] + os * (2.0f * uh[0] * N[3] + uh[1] * N[0]),
-                  ryy * uh[0] + os * (2.0f * uh[1] * N[3] + uh[0] * N[1]),
-                  rxx * uh[2] + os * (2.0f * uh[0] * N[4] + uh[2] * N[0]),
-                  rzz * uh[0] + os * (2.0f * uh[2] * N[4] + uh[0] * N[2]),
-                  ryy * uh[2] + os * (2.0f * uh[1] * N[5] + uh[2] * N[1]),
-                  rzz * uh[1] + os * (2.0f * uh[2] * N[5] + uh[1] * N[2])};
+    const float M[6] = {rxx * uh[1] + os * (2.0f * uh[0] * N[3] + uh[1] * N[0]),
+                        ryy * uh[0] + os * (2.0f * uh[1] * N[3] + uh[0] * N[1]),
+                        rxx * uh[2] + os * (2.0f * uh[0] * N[4] + uh[2] * N[0]),
+                        rzz * uh[0] + os * (2.0f * uh[2] * N[4] + uh[0] * N[2]),
+                        ryy * uh[2] + os * (2.0f * uh[1] * N[5] + uh[2] * N[1]),
+                        rzz * uh[1] + os * (2.0f * uh[2] * N[5] + uh[1] * N[2])};
     float Axyz = 0.0f;
     if constexpr (Q == 27)
         Axyz = rho * uh[0] * uh[1] * uh[2] + os * (uh[0] * N[5] + uh[1] * N[4] + uh[2] * N[3]);
@@ -262,6 +260,7 @@ struct RotorDev {
     int g[3];
     float origin[3];
     float inv_h, h;
+    float reach_plane2, reach_axial;   // cells beyond these can be neither force nor wall cells
     float ck[MAXBLADES], sk[MAXBLADES], cp, sp;   // per-step frames
     float* d;                   // [box] porosity
     uint8_t* flags;             // [box] bit0: d<1 (force set), bit1: wall cell
@@ -269,7 +268,10 @@ struct RotorDev {
     double* utau;               // [box] friction velocity (Newton warm start)
     uint8_t* active;            // [box]
     int* list;                  // [box] force cells of this step
-    int* count;                 // [1]
+    int* count;                 // [1] force cells; [1] wall cells at count + 1
+    int* wlist;                 // [box] wall cells of this step (box index)
+    float* wphi;                // [box] their signed distance
+    signed char* wwhich;        // [box] their closest component (blade, or n_blades = hub)
     double* partial;            // [FORCE_BLOCKS][6]
     unsigned* done;             // [1]
     double* acc;                // F(3) M(3) | F_sum(3) M_sum(3)

@@ -8,7 +8,8 @@
 
 namespace hl {
 
-constexpr int FORCE_BLOCKS = 64;     // blocks per rotor in the force reduction
+constexpr int FORCE_BLOCKS = 296;    // blocks per rotor in the force reduction (2 x 148 SMs)
+constexpr int WALL_BLOCKS = 148;     // blocks per rotor in the wall model
 constexpr int MASS_BLOCKS = 592;     // 4 x 148 SMs
 constexpr int BAND_THREADS = 256;
 
@@ -16,8 +17,10 @@ enum ErrBits : unsigned { ERR_NONFINITE = 1u, ERR_MASS = 2u };
 
 struct StepArgs {
     void* f;                 // populations [Q][N], storage type
+    void* slot[27];          // f + s * N: base of slot s
     long long N;
     int n[3];
+    int nxy, nplane;         // nx * ny; cells of an inlet/outlet plane
     int phase;               // t & 1: AA layout of the pre-collision state
     long long t;
     int flow_axis, open;
@@ -52,10 +55,11 @@ struct MassArgs {
 // launchers: return the launch error of the last kernel
 cudaError_t launch_band(int Q, int storage, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_collide(int Q, int storage, const StepArgs& a, cudaStream_t s);
+cudaError_t launch_wall(int Q, int storage, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_force(int Q, int storage, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_mass(int Q, int storage, const MassArgs& m, cudaStream_t s);
-cudaError_t launch_init(int Q, int storage, void* f, long long N, const int n[3], const float* rho,
-                        const float* u, float drho0, const float u0[3], cudaStream_t s);
+cudaError_t launch_init(int Q, int storage, const StepArgs& a, const float* rho, const float* u, float drho0,
+                        const float u0[3], cudaStream_t s);
 cudaError_t launch_fields(int Q, int storage, const StepArgs& a, float* rho, float* u,
                           cudaStream_t s);
 cudaError_t launch_debug_collide(int Q, int n, const float* g_in, const float* d, const float* uB,

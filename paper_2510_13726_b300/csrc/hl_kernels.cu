@@ -1,8 +1,10 @@
 // Kernels of the HHRRLBM-LES rotor step on B300 (sm_103a).
 //
 // Per time step (listing "HHRRLBM-FSI", Sec. 3.2), on one stream:
-//   band_kernel     porosity embedding of the rotor boxes + wall model on the
-//                   wall cells + list of force cells          (Sec. 2.2.1/2.2.2/3.1)
+//   band_kernel     porosity embedding of the rotor boxes (Definition
+//                   "Lattice Porosity", Sec. 3.1): d, force/wall flags, and
+//                   compacted lists of force cells and wall cells
+//   wall_kernel     wall model on the wall-cell list (Sec. 2.2.1, 3.2)
 //   collide_kernel  fused collide-and-stream, single-buffer AA pattern,
 //                   bulk (RRLBM-LES) and band (HHRRLBM-LES) branches,
 //                   equilibrium inlet/outlet planes            (Eq. (hlbm))
@@ -20,99 +22,84 @@
 
 namespace hl {
 
-// index contributions of the three neighbours (-1, 0, +1) along each axis;
-// an open (inlet/outlet) face has no neighbour beyond it
-struct Nbr {
-    long long off[3][3];
-    bool ok[3][3];
+// periodic neighbour index contributions along x, y, z (-1, 0, +1)
+struct Offs {
+    int x[3], y[3], z[3];
 };
 
-__device__ __forceinline__ void make_nbr(const StepArgs& a, int x, int y, int z, Nbr& nb) {
-    const int v[3] = {x, y, z};
-    const long long stride[3] = {1, a.n[0], (long long)a.n[0] * a.n[1]};
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const bool op = a.open && k == a.flow_axis;
-        const int n = a.n[k];
-        int m = v[k] - 1, p = v[k] + 1;
-        nb.ok[k][0] = true;
-        nb.ok[k][2] = true;
-        nb.ok[k][1] = true;
-        if (m < 0) { if (op) { nb.ok[k][0] = false; m = v[k]; } else m = n - 1; }
-        if (p >= n) { if (op) { nb.ok[k][2] = false; p = v[k]; } else p = 0; }
-        nb.off[k][0] = m * stride[k];
-        nb.off[k][1] = (long long)v[k] * stride[k];
-        nb.off[k][2] = p * stride[k];
-    }
+__device__ __forceinline__ void make_offs(const StepArgs& a, int x, int y, int z, Offs& o) {
+    const int nx = a.n[0], ny = a.n[1], nz = a.n[2], nxy = a.nxy;
+    o.x[0] = x == 0 ? nx - 1 : x - 1;
+    o.x[1] = x;
+    o.x[2] = x == nx - 1 ? 0 : x + 1;
+    o.y[0] = (y == 0 ? ny - 1 : y - 1) * nx;
+    o.y[1] = y * nx;
+    o.y[2] = (y == ny - 1 ? 0 : y + 1) * nx;
+    o.z[0] = (z == 0 ? nz - 1 : z - 1) * nxy;
+    o.z[1] = z * nxy;
+    o.z[2] = (z == nz - 1 ? 0 : z + 1) * nxy;
 }
 
-template <int Q, int s, int sign>
-__device__ __forceinline__ long long nbr_index(const Nbr& nb, bool& ok) {
-    constexpr int cx = sign * slot_c<Q>(s, 0), cy = sign * slot_c<Q>(s, 1), cz = sign * slot_c<Q>(s, 2);
-    ok = nb.ok[0][cx + 1] && nb.ok[1][cy + 1] && nb.ok[2][cz + 1];
-    return nb.off[0][cx + 1] + nb.off[1][cy + 1] + nb.off[2][cz + 1];
-}
-
-// pre-collision populations of a cell in the layout of phase p
 template <int Q, int S>
-__device__ __forceinline__ void load_pre(const StepArgs& a, long long cell, const Nbr& nb, float (&g)[Q]) {
-    using T = typename Store<S>::T;
-    const T* f = static_cast<const T*>(a.f);
-    if (a.phase == 0) {
-        sfor<Q>([&](auto I) {
-            constexpr int s = decltype(I)::value;
-            g[s] = Store<S>::ld(f + (long long)s * a.N + cell);
-        });
-    } else {
-        sfor<Q>([&](auto I) {
-            constexpr int s = decltype(I)::value;
-            constexpr int o = slot_opp<Q>(s);
-            bool ok;
-            long long src = nbr_index<Q, s, -1>(nb, ok);
-            if (!ok) src = cell;   // enters through an open face: undefined, keep finite
-            g[s] = Store<S>::ld(f + (long long)o * a.N + src);
-        });
+__device__ __forceinline__ typename Store<S>::T* slot_ptr(const StepArgs& a, int s) {
+    return static_cast<typename Store<S>::T*>(a.slot[s]);
+}
+
+// pre-collision populations of a cell in the layout of phase PH (the
+// neighbour across an open face wraps: that value is undefined by the scheme
+// and only read for cells on an open boundary plane)
+template <int Q, int S, int PH>
+__device__ __forceinline__ void load_pre(const StepArgs& a, int cell, const Offs& o, float (&g)[Q]) {
+#pragma unroll
+    for (int s = 0; s < Q; ++s) {
+        if (PH == 0) {
+            g[s] = Store<S>::ld(slot_ptr<Q, S>(a, s) + cell);
+        } else {
+            const int cx = cslot(Q, s, 0), cy = cslot(Q, s, 1), cz = cslot(Q, s, 2);
+            const int src = o.x[1 - cx] + o.y[1 - cy] + o.z[1 - cz];
+            g[s] = Store<S>::ld(slot_ptr<Q, S>(a, oslot(Q, s)) + src);
+        }
     }
 }
 
 __device__ __forceinline__ void solid_velocity(const RotorDev& R, int x, int y, int z, float us[3]) {
     const float r[3] = {(float)x - R.cf[0], (float)y - R.cf[1], (float)z - R.cf[2]};
-    const int ax = R.axis, b = (ax + 1) % 3, c = (ax + 2) % 3;
-    us[ax] = 0.0f;
-    us[b] = -R.omega * r[c];
-    us[c] = R.omega * r[b];
+    const int ax = R.axis;
+    // u_s = Omega a x r: (a x r)_b = -r_c, (a x r)_c = r_b with (b, c) = (a+1, a+2)
+    if (ax == 0) { us[0] = 0.f; us[1] = -R.omega * r[2]; us[2] = R.omega * r[1]; }
+    else if (ax == 1) { us[1] = 0.f; us[2] = -R.omega * r[0]; us[0] = R.omega * r[2]; }
+    else { us[2] = 0.f; us[0] = -R.omega * r[1]; us[1] = R.omega * r[0]; }
 }
+
+__device__ __forceinline__ int sel3(int ax, int a0, int a1, int a2) { return ax == 0 ? a0 : (ax == 1 ? a1 : a2); }
 
 // ---------------------------------------------------------------------------
 // fused collide and stream
 // ---------------------------------------------------------------------------
-template <int Q, int S>
+template <int Q, int S, int PH>
 __global__ void __launch_bounds__(128) collide_kernel(const StepArgs a) {
-    using T = typename Store<S>::T;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= a.n[0] || y >= a.n[1]) return;
-    const long long cell = ((long long)z * a.n[1] + y) * a.n[0] + x;
-    const int xi[3] = {x, y, z};
-    const int ax = a.flow_axis, bx = (ax + 1) % 3, cxs = (ax + 2) % 3;
-    const int ca = xi[ax];
+    const int cell = (z * a.n[1] + y) * a.n[0] + x;
+    const int ax = a.flow_axis;
+    const int ca = sel3(ax, x, y, z);
+    const int na = sel3(ax, a.n[0], a.n[1], a.n[2]);
     const bool inlet = a.open && ca == 0;
-    const bool outlet = a.open && ca == a.n[ax] - 1;
-    Nbr nb;
-    make_nbr(a, x, y, z, nb);
+    const bool outlet = a.open && ca == na - 1;
+    Offs o;
+    make_offs(a, x, y, z, o);
     float g[Q];
     if (!inlet && !outlet) {
-        load_pre<Q, S>(a, cell, nb, g);
-        int rk = -1;
-        long long bi = 0;
+        load_pre<Q, S, PH>(a, cell, o, g);
+        int rk = -1, bi = 0;
         for (int k = 0; k < a.nrot; ++k) {
-            const RotorDev& R = a.rot[k];
-            const unsigned dx = (unsigned)(x - R.lo[0]), dy = (unsigned)(y - R.lo[1]),
-                           dz = (unsigned)(z - R.lo[2]);
-            if (dx < (unsigned)R.n[0] && dy < (unsigned)R.n[1] && dz < (unsigned)R.n[2]) {
+            const unsigned dx = (unsigned)(x - a.rot[k].lo[0]), dy = (unsigned)(y - a.rot[k].lo[1]),
+                           dz = (unsigned)(z - a.rot[k].lo[2]);
+            if (dx < (unsigned)a.rot[k].n[0] && dy < (unsigned)a.rot[k].n[1] && dz < (unsigned)a.rot[k].n[2]) {
                 rk = k;
-                bi = ((long long)dz * R.n[1] + dy) * R.n[0] + dx;
+                bi = ((int)dz * a.rot[k].n[1] + (int)dy) * a.rot[k].n[0] + (int)dx;
                 break;
             }
         }
@@ -129,11 +116,12 @@ __global__ void __launch_bounds__(128) collide_kernel(const StepArgs a) {
             for (int k = 0; k < 6; ++k) B.S[k] = 0.0f;
             if (a.wall_model && (fl & FL_W)) {
                 const float* wm = R.wm + bi;
+                const long long bc = R.box_cells;
                 B.uB[0] += wm[0];
-                B.uB[1] += wm[R.box_cells];
-                B.uB[2] += wm[2 * R.box_cells];
+                B.uB[1] += wm[bc];
+                B.uB[2] += wm[2 * bc];
 #pragma unroll
-                for (int k = 0; k < 6; ++k) B.S[k] = wm[(3 + k) * R.box_cells];
+                for (int k = 0; k < 6; ++k) B.S[k] = wm[(3 + k) * bc];
                 B.sigma = 0.0f;
             }
             rho = collide<Q, true>(g, B, a.tau_mo, a.Ksmag, u);
@@ -142,14 +130,26 @@ __global__ void __launch_bounds__(128) collide_kernel(const StepArgs a) {
             rho = collide<Q, false>(g, B0, a.tau_mo, a.Ksmag, u);
         }
         if (!(fabsf(rho) < 1e30f)) atomicOr(a.err, ERR_NONFINITE);
-        if (a.open && ca == a.n[ax] - 2) {
-            const long long np = (long long)a.n[bx] * a.n[cxs];
-            const long long pl = (long long)xi[cxs] * a.n[bx] + xi[bx];
+        if (a.open && ca == na - 2) {
+            const int nb = sel3(ax, a.n[1], a.n[2], a.n[0]);
+            const int cb = sel3(ax, y, z, x), cc = sel3(ax, z, x, y);
+            const int pl = cc * nb + cb;
             a.uplane_cur[pl] = u[0];
-            a.uplane_cur[np + pl] = u[1];
-            a.uplane_cur[2 * np + pl] = u[2];
+            a.uplane_cur[a.nplane + pl] = u[1];
+            a.uplane_cur[2 * a.nplane + pl] = u[2];
         }
-    } else if (inlet) {
+#pragma unroll
+        for (int s = 0; s < Q; ++s) {
+            if (PH == 0) {
+                Store<S>::st(slot_ptr<Q, S>(a, oslot(Q, s)) + cell, g[s]);
+            } else {
+                const int cx = cslot(Q, s, 0), cy = cslot(Q, s, 1), cz = cslot(Q, s, 2);
+                Store<S>::st(slot_ptr<Q, S>(a, s) + (o.x[1 + cx] + o.y[1 + cy] + o.z[1 + cz]), g[s]);
+            }
+        }
+        return;
+    }
+    if (inlet) {
         // equilibrium inflow: U a + sum_m a_m cos(k.x') + b_m sin(k.x'), x' = x - U t a
         float u[3] = {0.f, 0.f, 0.f};
         u[ax] = a.u_in;
@@ -167,119 +167,39 @@ __global__ void __launch_bounds__(128) collide_kernel(const StepArgs a) {
         equilibrium<Q>(g, 0.0f, u);
     } else {
         // equilibrium outflow at the velocity of the upstream neighbour, previous step
-        const long long np = (long long)a.n[bx] * a.n[cxs];
-        const long long pl = (long long)xi[cxs] * a.n[bx] + xi[bx];
-        const float u[3] = {a.uplane_prev[pl], a.uplane_prev[np + pl], a.uplane_prev[2 * np + pl]};
+        const int nb = sel3(ax, a.n[1], a.n[2], a.n[0]);
+        const int cb = sel3(ax, y, z, x), cc = sel3(ax, z, x, y);
+        const int pl = cc * nb + cb;
+        const float u[3] = {a.uplane_prev[pl], a.uplane_prev[a.nplane + pl], a.uplane_prev[2 * a.nplane + pl]};
         equilibrium<Q>(g, 0.0f, u);
     }
-    T* f = static_cast<T*>(a.f);
-    if (a.phase == 0) {
-        sfor<Q>([&](auto I) {
-            constexpr int s = decltype(I)::value;
-            Store<S>::st(f + (long long)slot_opp<Q>(s) * a.N + cell, g[s]);
-        });
-    } else {
-        sfor<Q>([&](auto I) {
-            constexpr int s = decltype(I)::value;
-            bool ok;
-            const long long dst = nbr_index<Q, s, +1>(nb, ok);
-            if (ok) Store<S>::st(f + (long long)s * a.N + dst, g[s]);
-        });
-    }
-}
-
-// ---------------------------------------------------------------------------
-// porosity embedding, wall model, force-cell list (rotor boxes)
-// ---------------------------------------------------------------------------
-template <int Q, int S>
-__device__ void cell_velocity(const StepArgs& a, int x, int y, int z, float u[3]) {
-    Nbr nb;
-    make_nbr(a, x, y, z, nb);
-    const long long cell = ((long long)z * a.n[1] + y) * a.n[0] + x;
-    float g[Q];
-    load_pre<Q, S>(a, cell, nb, g);
-    float drho = 0.f, j[3] = {0.f, 0.f, 0.f};
-    sfor<Q>([&](auto I) {
-        constexpr int s = decltype(I)::value;
-        drho += g[s];
-        if constexpr (slot_c<Q>(s, 0) != 0) j[0] += float(slot_c<Q>(s, 0)) * g[s];
-        if constexpr (slot_c<Q>(s, 1) != 0) j[1] += float(slot_c<Q>(s, 1)) * g[s];
-        if constexpr (slot_c<Q>(s, 2) != 0) j[2] += float(slot_c<Q>(s, 2)) * g[s];
-    });
-    const float inv = 1.0f / (1.0f + drho);
-    u[0] = j[0] * inv; u[1] = j[1] * inv; u[2] = j[2] * inv;
-}
-
-template <int Q, int S>
-__device__ void wall_model_cell(const StepArgs& a, const RotorDev& R, long long bi, int x, int y, int z,
-                                float phi, int which) {
-    float n[3];
-    rotor_normal(R, which, x, y, z, n);
-    const float y1 = phi > 0.5f ? phi : 0.5f;
-    // sampling point x_s = x + y_s n and trilinear fluid velocity there
-    const float xs[3] = {x + a.wmYs * n[0], y + a.wmYs * n[1], z + a.wmYs * n[2]};
-    int i0[3];
-    float t[3];
+    // boundary planes: populations that would leave through the open face are dropped
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const float fl = floorf(xs[k]);
-        i0[k] = (int)fl;
-        t[k] = xs[k] - fl;
-        if (a.open && k == a.flow_axis) {
-            if (i0[k] < 0) { i0[k] = 0; t[k] = 0.f; }
-            if (i0[k] > a.n[k] - 2) { i0[k] = a.n[k] - 2; t[k] = 1.f; }
+    for (int s = 0; s < Q; ++s) {
+        if (PH == 0) {
+            Store<S>::st(slot_ptr<Q, S>(a, oslot(Q, s)) + cell, g[s]);
+        } else {
+            const int cx = cslot(Q, s, 0), cy = cslot(Q, s, 1), cz = cslot(Q, s, 2);
+            const int cas = sel3(ax, cx, cy, cz);
+            if ((inlet && cas < 0) || (outlet && cas > 0)) continue;
+            Store<S>::st(slot_ptr<Q, S>(a, s) + (o.x[1 + cx] + o.y[1 + cy] + o.z[1 + cz]), g[s]);
         }
     }
-    float us[3] = {0.f, 0.f, 0.f};
-    for (int cz = 0; cz < 2; ++cz)
-        for (int cy = 0; cy < 2; ++cy)
-            for (int cx = 0; cx < 2; ++cx) {
-                int p[3] = {i0[0] + cx, i0[1] + cy, i0[2] + cz};
-#pragma unroll
-                for (int k = 0; k < 3; ++k)
-                    if (!(a.open && k == a.flow_axis)) p[k] = ((p[k] % a.n[k]) + a.n[k]) % a.n[k];
-                const float wgt = (cx ? t[0] : 1.f - t[0]) * (cy ? t[1] : 1.f - t[1]) * (cz ? t[2] : 1.f - t[2]);
-                float uc[3];
-                cell_velocity<Q, S>(a, p[0], p[1], p[2], uc);
-                us[0] += wgt * uc[0]; us[1] += wgt * uc[1]; us[2] += wgt * uc[2];
-            }
-    float usol[3];
-    solid_velocity(R, x, y, z, usol);
-    const float ur[3] = {us[0] - usol[0], us[1] - usol[1], us[2] - usol[2]};
-    const float un = ur[0] * n[0] + ur[1] * n[1] + ur[2] * n[2];
-    const float ut[3] = {ur[0] - un * n[0], ur[1] - un * n[1], ur[2] - un * n[2]};
-    const float utm = sqrtf(ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2]);
-    const long long B = R.box_cells;
-    float* wm = R.wm + bi;
-    if (!(utm >= 1e-12f)) {
-#pragma unroll
-        for (int k = 0; k < 9; ++k) wm[k * B] = 0.f;
-        R.active[bi] = 0;
-        R.utau[bi] = 0.0;
-        return;
-    }
-    const float th[3] = {ut[0] / utm, ut[1] / utm, ut[2] / utm};
-    const double ysamp = (double)y1 + (double)a.wmYs;
-    // Eq. (guess): previous value if the wall function was active last step
-    const double guess = R.active[bi] ? R.utau[bi] : sqrt(a.nu * (double)utm / (double)a.wmYs);
-    const double utau = wall_newton((double)utm, ysamp, a.nu, guess, a.wmE, a.wmK, a.wmTol, a.wmMaxit);
-    const double up = spalding_uplus((double)y1 * utau / a.nu, a.wmE, a.wmK, a.wmTol, a.wmMaxit);
-    const float uw = (float)(utau * up);
-    const float gs = (float)(0.5 * ((double)utm - utau * up) / (double)a.wmYs);
-    wm[0] = uw * th[0];
-    wm[B] = uw * th[1];
-    wm[2 * B] = uw * th[2];
-    wm[3 * B] = gs * 2.0f * th[0] * n[0];
-    wm[4 * B] = gs * 2.0f * th[1] * n[1];
-    wm[5 * B] = gs * 2.0f * th[2] * n[2];
-    wm[6 * B] = gs * (th[0] * n[1] + n[0] * th[1]);
-    wm[7 * B] = gs * (th[0] * n[2] + n[0] * th[2]);
-    wm[8 * B] = gs * (th[1] * n[2] + n[1] * th[2]);
-    R.active[bi] = 1;
-    R.utau[bi] = utau;
 }
 
-template <int Q, int S>
+// ---------------------------------------------------------------------------
+// porosity embedding of the rotor boxes and the force / wall cell lists
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int append(int* counter, bool take, int lane) {
+    const unsigned mask = __ballot_sync(0xffffffffu, take);
+    int start = 0;
+    if (mask) {
+        if (lane == 0) start = atomicAdd(counter, __popc(mask));
+        start = __shfl_sync(0xffffffffu, start, 0);
+    }
+    return start + __popc(mask & ((1u << lane) - 1u));
+}
+
 __global__ void __launch_bounds__(BAND_THREADS) band_kernel(const StepArgs a) {
     const RotorDev& R = a.rot[blockIdx.y];
     const long long nbox = R.box_cells;
@@ -287,44 +207,146 @@ __global__ void __launch_bounds__(BAND_THREADS) band_kernel(const StepArgs a) {
     for (long long base = (long long)blockIdx.x * blockDim.x; base < nbox;
          base += (long long)gridDim.x * blockDim.x) {
         const long long bi = base + threadIdx.x;
-        bool isB = false;
+        bool isB = false, isW = false;
+        float phi = 0.f;
+        int which = -1;
         if (bi < nbox) {
             const int bx = (int)(bi % R.n[0]);
             const long long r2 = bi / R.n[0];
             const int by = (int)(r2 % R.n[1]);
             const int bz = (int)(r2 / R.n[1]);
             const int x = R.lo[0] + bx, y = R.lo[1] + by, z = R.lo[2] + bz;
-            int which;
-            const float phi = rotor_phi(R, x, y, z, which);
             uint8_t fl = 0;
             float d = 1.0f;
-            if (phi < a.eps_half) {
-                fl |= FL_B;
-                if (phi <= -a.eps_half) {
-                    d = 0.0f;
-                } else {
-                    const float tt = phi * a.inv_eps + 0.5f;
-                    d = a.transition ? tt : tt * tt * (3.0f - 2.0f * tt);
+            // cells beyond the rotor's reach (every blade sample out of its grid,
+            // hub farther than eps/2 + 1) keep d = 1 without evaluating phi
+            const float rx = (float)x - R.cf[0], ry = (float)y - R.cf[1], rz = (float)z - R.cf[2];
+            const float ra = R.axis == 0 ? rx : (R.axis == 1 ? ry : rz);
+            const float rr = rx * rx + ry * ry + rz * rz - ra * ra;
+            if (rr <= R.reach_plane2 && fabsf(ra) <= R.reach_axial) {
+                phi = rotor_phi(R, x, y, z, which);
+                if (phi < a.eps_half) {
+                    fl |= FL_B;
+                    if (phi <= -a.eps_half) {
+                        d = 0.0f;
+                    } else {
+                        const float tt = phi * a.inv_eps + 0.5f;
+                        d = a.transition ? tt : tt * tt * (3.0f - 2.0f * tt);
+                    }
+                    if (phi >= 0.0f) fl |= FL_W;
                 }
-                if (phi >= 0.0f) fl |= FL_W;
             }
             R.d[bi] = d;
             R.flags[bi] = fl;
             isB = (fl & FL_B) != 0;
-            if (a.wall_model && (fl & FL_W))
-                wall_model_cell<Q, S>(a, R, bi, x, y, z, phi, which);
-            else
-                R.active[bi] = 0;
+            isW = a.wall_model && (fl & FL_W);
+            if (!isW) R.active[bi] = 0;
         }
-        // warp-aggregated append to the force-cell list
-        const unsigned mask = __ballot_sync(0xffffffffu, isB);
-        if (mask) {
-            int start = 0;
-            if (lane == 0) start = atomicAdd(R.count, __popc(mask));
-            start = __shfl_sync(0xffffffffu, start, 0);
-            const long long slot = (long long)start + __popc(mask & ((1u << lane) - 1u));
-            if (isB && slot < nbox) R.list[slot] = (int)bi;
+        const int fslot = append(R.count, isB, lane);
+        if (isB && fslot < nbox) R.list[fslot] = (int)bi;
+        const int wslot = append(R.count + 1, isW, lane);
+        if (isW && wslot < nbox) {
+            R.wlist[wslot] = (int)bi;
+            R.wphi[wslot] = phi;
+            R.wwhich[wslot] = (signed char)which;
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// wall model on the wall-cell list (Sec. 2.2.1): sample, Newton in FP64
+// ---------------------------------------------------------------------------
+template <int Q, int S, int PH>
+__device__ void cell_velocity(const StepArgs& a, int x, int y, int z, float u[3]) {
+    Offs o;
+    make_offs(a, x, y, z, o);
+    const int cell = (z * a.n[1] + y) * a.n[0] + x;
+    float g[Q];
+    load_pre<Q, S, PH>(a, cell, o, g);
+    float drho, j[3];
+    moments01<Q>(g, drho, j);
+    const float inv = 1.0f / (1.0f + drho);
+    u[0] = j[0] * inv; u[1] = j[1] * inv; u[2] = j[2] * inv;
+}
+
+template <int Q, int S, int PH>
+__global__ void __launch_bounds__(128) wall_kernel(const StepArgs a) {
+    const RotorDev& R = a.rot[blockIdx.y];
+    int count = *((volatile int*)(R.count + 1));
+    if ((long long)count > R.box_cells) count = (int)R.box_cells;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < count; idx += gridDim.x * blockDim.x) {
+        const long long bi = R.wlist[idx];
+        const float phi = R.wphi[idx];
+        const int which = R.wwhich[idx];
+        const int bx = (int)(bi % R.n[0]);
+        const long long r2 = bi / R.n[0];
+        const int by = (int)(r2 % R.n[1]);
+        const int bz = (int)(r2 / R.n[1]);
+        const int x = R.lo[0] + bx, y = R.lo[1] + by, z = R.lo[2] + bz;
+        float n[3];
+        rotor_normal(R, which, x, y, z, n);
+        const float y1 = phi > 0.5f ? phi : 0.5f;
+        // sampling point x_s = x + y_s n and trilinear fluid velocity there
+        const float xs[3] = {x + a.wmYs * n[0], y + a.wmYs * n[1], z + a.wmYs * n[2]};
+        int i0[3];
+        float t[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float fl = floorf(xs[k]);
+            i0[k] = (int)fl;
+            t[k] = xs[k] - fl;
+            if (a.open && k == a.flow_axis) {
+                if (i0[k] < 0) { i0[k] = 0; t[k] = 0.f; }
+                if (i0[k] > a.n[k] - 2) { i0[k] = a.n[k] - 2; t[k] = 1.f; }
+            }
+        }
+        float us[3] = {0.f, 0.f, 0.f};
+        for (int cz = 0; cz < 2; ++cz)
+            for (int cy = 0; cy < 2; ++cy)
+                for (int cx = 0; cx < 2; ++cx) {
+                    int p[3] = {i0[0] + cx, i0[1] + cy, i0[2] + cz};
+#pragma unroll
+                    for (int k = 0; k < 3; ++k)
+                        if (!(a.open && k == a.flow_axis)) p[k] = ((p[k] % a.n[k]) + a.n[k]) % a.n[k];
+                    const float wgt = (cx ? t[0] : 1.f - t[0]) * (cy ? t[1] : 1.f - t[1]) * (cz ? t[2] : 1.f - t[2]);
+                    float uc[3];
+                    cell_velocity<Q, S, PH>(a, p[0], p[1], p[2], uc);
+                    us[0] += wgt * uc[0]; us[1] += wgt * uc[1]; us[2] += wgt * uc[2];
+                }
+        float usol[3];
+        solid_velocity(R, x, y, z, usol);
+        const float ur[3] = {us[0] - usol[0], us[1] - usol[1], us[2] - usol[2]};
+        const float un = ur[0] * n[0] + ur[1] * n[1] + ur[2] * n[2];
+        const float ut[3] = {ur[0] - un * n[0], ur[1] - un * n[1], ur[2] - un * n[2]};
+        const float utm = sqrtf(ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2]);
+        const long long B = R.box_cells;
+        float* wm = R.wm + bi;
+        if (!(utm >= 1e-12f)) {
+#pragma unroll
+            for (int k = 0; k < 9; ++k) wm[k * B] = 0.f;
+            R.active[bi] = 0;
+            R.utau[bi] = 0.0;
+            continue;
+        }
+        const float th[3] = {ut[0] / utm, ut[1] / utm, ut[2] / utm};
+        const double ysamp = (double)y1 + (double)a.wmYs;
+        // Eq. (guess): previous value if the wall function was active last step
+        const double guess = R.active[bi] ? R.utau[bi] : sqrt(a.nu * (double)utm / (double)a.wmYs);
+        const double utau = wall_newton((double)utm, ysamp, a.nu, guess, a.wmE, a.wmK, a.wmTol, a.wmMaxit);
+        const double up = spalding_uplus((double)y1 * utau / a.nu, a.wmE, a.wmK, a.wmTol, a.wmMaxit);
+        const float uw = (float)(utau * up);
+        const float gs = (float)(0.5 * ((double)utm - utau * up) / (double)a.wmYs);
+        wm[0] = uw * th[0];
+        wm[B] = uw * th[1];
+        wm[2 * B] = uw * th[2];
+        wm[3 * B] = gs * 2.0f * th[0] * n[0];
+        wm[4 * B] = gs * 2.0f * th[1] * n[1];
+        wm[5 * B] = gs * 2.0f * th[2] * n[2];
+        wm[6 * B] = gs * (th[0] * n[1] + n[0] * th[1]);
+        wm[7 * B] = gs * (th[0] * n[2] + n[0] * th[2]);
+        wm[8 * B] = gs * (th[1] * n[2] + n[1] * th[2]);
+        R.active[bi] = 1;
+        R.utau[bi] = utau;
     }
 }
 
@@ -337,13 +359,11 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-template <int Q, int S>
+template <int Q, int S, int PH>
 __global__ void __launch_bounds__(256) force_kernel(const StepArgs a) {
-    using T = typename Store<S>::T;
     const RotorDev& R = a.rot[blockIdx.y];
-    const T* f = static_cast<const T*>(a.f);
     int count = *((volatile int*)R.count);
-    if ((long long)count > R.box_cells) count = (int)R.box_cells;   // never read past the list
+    if ((long long)count > R.box_cells) count = (int)R.box_cells;
     double acc[6] = {0, 0, 0, 0, 0, 0};
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < count; idx += gridDim.x * blockDim.x) {
         const long long bi = R.list[idx];
@@ -352,45 +372,41 @@ __global__ void __launch_bounds__(256) force_kernel(const StepArgs a) {
         const int by = (int)(r2 % R.n[1]);
         const int bz = (int)(r2 / R.n[1]);
         const int x = R.lo[0] + bx, y = R.lo[1] + by, z = R.lo[2] + bz;
-        const long long cell = ((long long)z * a.n[1] + y) * a.n[0] + x;
-        Nbr nb;
-        make_nbr(a, x, y, z, nb);
+        const int cell = (z * a.n[1] + y) * a.n[0] + x;
+        Offs o;
+        make_offs(a, x, y, z, o);
+        float us[3];
+        solid_velocity(R, x, y, z, us);
+        // per-cell link sum in FP32 on the shifted populations (the rest-weight
+        // parts of the link terms cancel); cells are combined in FP64
+        float Fc[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int s = 1; s < Q; ++s) {
+            const int c0 = cslot(Q, s, 0), c1 = cslot(Q, s, 1), c2 = cslot(Q, s, 2);
+            const int o_s = oslot(Q, s);
+            const int nbx = o.x[1 + c0] + o.y[1 + c1] + o.z[1 + c2];
+            float out_s, in_o;   // f*_s(x) and f*_o(x + c_s)
+            if (PH == 0) {
+                out_s = Store<S>::ld(slot_ptr<Q, S>(a, o_s) + cell);
+                in_o = Store<S>::ld(slot_ptr<Q, S>(a, s) + nbx);
+            } else {
+                out_s = Store<S>::ld(slot_ptr<Q, S>(a, s) + nbx);
+                in_o = Store<S>::ld(slot_ptr<Q, S>(a, o_s) + cell);
+            }
+            Fc[0] += (float(-c0) - us[0]) * in_o - (float(c0) - us[0]) * out_s;
+            Fc[1] += (float(-c1) - us[1]) * in_o - (float(c1) - us[1]) * out_s;
+            Fc[2] += (float(-c2) - us[2]) * in_o - (float(c2) - us[2]) * out_s;
+        }
         const double r[3] = {(double)((float)x - R.cf[0]), (double)((float)y - R.cf[1]),
                              (double)((float)z - R.cf[2])};
-        double us[3];
-        {
-            const int ax = R.axis, b = (ax + 1) % 3, c = (ax + 2) % 3;
-            us[ax] = 0.0;
-            us[b] = -(double)R.omega * r[c];
-            us[c] = (double)R.omega * r[b];
-        }
-        double Fc[3] = {0.0, 0.0, 0.0};
-        // shifted populations: the rest-weight parts of the link terms cancel
-        sfor<Q - 1>([&](auto I) {
-            constexpr int s = decltype(I)::value + 1;
-            constexpr int o = slot_opp<Q>(s);
-            bool ok;
-            const long long nbx = nbr_index<Q, s, +1>(nb, ok);
-            if (!ok) return;
-            double out_s, in_o;   // f*_s(x) and f*_o(x + c_s)
-            if (a.phase == 0) {
-                out_s = Store<S>::ld(f + (long long)o * a.N + cell);
-                in_o = Store<S>::ld(f + (long long)s * a.N + nbx);
-            } else {
-                out_s = Store<S>::ld(f + (long long)s * a.N + nbx);
-                in_o = Store<S>::ld(f + (long long)o * a.N + cell);
-            }
-            constexpr double c0 = slot_c<Q>(s, 0), c1 = slot_c<Q>(s, 1), c2 = slot_c<Q>(s, 2);
-            Fc[0] += (-c0 - us[0]) * in_o - (c0 - us[0]) * out_s;
-            Fc[1] += (-c1 - us[1]) * in_o - (c1 - us[1]) * out_s;
-            Fc[2] += (-c2 - us[2]) * in_o - (c2 - us[2]) * out_s;
-        });
-        acc[0] += Fc[0]; acc[1] += Fc[1]; acc[2] += Fc[2];
-        acc[3] += r[1] * Fc[2] - r[2] * Fc[1];
-        acc[4] += r[2] * Fc[0] - r[0] * Fc[2];
-        acc[5] += r[0] * Fc[1] - r[1] * Fc[0];
+        const double F0 = Fc[0], F1 = Fc[1], F2 = Fc[2];
+        acc[0] += F0; acc[1] += F1; acc[2] += F2;
+        acc[3] += r[1] * F2 - r[2] * F1;
+        acc[4] += r[2] * F0 - r[0] * F2;
+        acc[5] += r[0] * F1 - r[1] * F0;
     }
     __shared__ double sh[8][6];
+    __shared__ bool last;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
@@ -398,7 +414,6 @@ __global__ void __launch_bounds__(256) force_kernel(const StepArgs a) {
         if (lane == 0) sh[warp][k] = v;
     }
     __syncthreads();
-    __shared__ bool last;
     if (threadIdx.x < 6) {
         double v = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += sh[w][threadIdx.x];
@@ -418,28 +433,49 @@ __global__ void __launch_bounds__(256) force_kernel(const StepArgs a) {
         }
         if (threadIdx.x == 0) {
             *R.done = 0u;
-            *R.count = 0;
+            R.count[0] = 0;   // force cells
+            R.count[1] = 0;   // wall cells
         }
     }
 }
 
 // ---------------------------------------------------------------------------
-// FP64 mass total (deterministic two-stage reduction) and drift check
+// FP64 mass total (deterministic two-stage reduction) and drift check;
+// groups of 8 stored values are summed in FP32 first (16-byte loads)
 // ---------------------------------------------------------------------------
+template <int S>
+__device__ __forceinline__ float sum8(const typename Store<S>::T* p) {
+    if constexpr (S == ST_F32) {
+        const float4 a = reinterpret_cast<const float4*>(p)[0];
+        const float4 b = reinterpret_cast<const float4*>(p)[1];
+        return ((a.x + a.y) + (a.z + a.w)) + ((b.x + b.y) + (b.z + b.w));
+    } else {
+        const uint4 v = *reinterpret_cast<const uint4*>(p);
+        const typename Store<S>::T* h = reinterpret_cast<const typename Store<S>::T*>(&v);
+        float s = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) s += Store<S>::ld(h + k);
+        return s;
+    }
+}
+
 template <int S>
 __global__ void __launch_bounds__(256) mass_kernel(const MassArgs m) {
     using T = typename Store<S>::T;
     const T* f = static_cast<const T*>(m.f);
+    const long long groups = m.count / 8;
     double v = 0.0;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m.count;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < groups;
          i += (long long)gridDim.x * blockDim.x)
-        v += (double)Store<S>::ld(f + i);
+        v += (double)sum8<S>(f + 8 * i);
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        for (long long i = 8 * groups; i < m.count; ++i) v += (double)Store<S>::ld(f + i);
     __shared__ double sh[8];
+    __shared__ bool last;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     v = warp_sum(v);
     if (lane == 0) sh[warp] = v;
     __syncthreads();
-    __shared__ bool last;
     if (threadIdx.x == 0) {
         double s = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
@@ -464,46 +500,36 @@ __global__ void __launch_bounds__(256) mass_kernel(const MassArgs m) {
 // initial state, macroscopic fields, single-cell collisions (unit checks)
 // ---------------------------------------------------------------------------
 template <int Q, int S>
-__global__ void init_kernel(void* fv, long long N, int nx, int ny, int nz, const float* rho, const float* u,
-                            float drho0, float u0x, float u0y, float u0z) {
-    using T = typename Store<S>::T;
+__global__ void init_kernel(const StepArgs a, const float* rho, const float* u, float drho0, float u0x, float u0y,
+                            float u0z) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     const int z = blockIdx.z;
-    if (x >= nx) return;
-    const long long cell = ((long long)z * ny + y) * nx + x;
+    if (x >= a.n[0]) return;
+    const int cell = (z * a.n[1] + y) * a.n[0] + x;
     float uu[3] = {u0x, u0y, u0z};
     float drho = drho0;
     if (rho) drho = rho[cell] - 1.0f;
-    if (u) { uu[0] = u[cell]; uu[1] = u[N + cell]; uu[2] = u[2 * N + cell]; }
+    if (u) { uu[0] = u[cell]; uu[1] = u[a.N + cell]; uu[2] = u[2 * a.N + cell]; }
     float g[Q];
     equilibrium<Q>(g, drho, uu);
-    T* f = static_cast<T*>(fv);
-    sfor<Q>([&](auto I) {
-        constexpr int s = decltype(I)::value;
-        Store<S>::st(f + (long long)s * N + cell, g[s]);
-    });
+#pragma unroll
+    for (int s = 0; s < Q; ++s) Store<S>::st(slot_ptr<Q, S>(a, s) + cell, g[s]);
 }
 
-template <int Q, int S>
+template <int Q, int S, int PH>
 __global__ void fields_kernel(const StepArgs a, float* rho, float* u) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     const int z = blockIdx.z;
     if (x >= a.n[0]) return;
-    const long long cell = ((long long)z * a.n[1] + y) * a.n[0] + x;
-    Nbr nb;
-    make_nbr(a, x, y, z, nb);
+    const int cell = (z * a.n[1] + y) * a.n[0] + x;
+    Offs o;
+    make_offs(a, x, y, z, o);
     float g[Q];
-    load_pre<Q, S>(a, cell, nb, g);
-    float drho = 0.f, j[3] = {0.f, 0.f, 0.f};
-    sfor<Q>([&](auto I) {
-        constexpr int s = decltype(I)::value;
-        drho += g[s];
-        if constexpr (slot_c<Q>(s, 0) != 0) j[0] += float(slot_c<Q>(s, 0)) * g[s];
-        if constexpr (slot_c<Q>(s, 1) != 0) j[1] += float(slot_c<Q>(s, 1)) * g[s];
-        if constexpr (slot_c<Q>(s, 2) != 0) j[2] += float(slot_c<Q>(s, 2)) * g[s];
-    });
+    load_pre<Q, S, PH>(a, cell, o, g);
+    float drho, j[3];
+    moments01<Q>(g, drho, j);
     const float r = 1.0f + drho;
     rho[cell] = r;
     u[cell] = j[0] / r;
@@ -549,7 +575,8 @@ template <int Q, int S>
 static cudaError_t launch_collide_t(const StepArgs& a, cudaStream_t s) {
     const dim3 blk = cell_block(a.n[0]);
     const dim3 grd((a.n[0] + blk.x - 1) / blk.x, (a.n[1] + blk.y - 1) / blk.y, a.n[2]);
-    collide_kernel<Q, S><<<grd, blk, 0, s>>>(a);
+    if (a.phase == 0) collide_kernel<Q, S, 0><<<grd, blk, 0, s>>>(a);
+    else collide_kernel<Q, S, 1><<<grd, blk, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -561,14 +588,25 @@ static cudaError_t launch_band_t(const StepArgs& a, cudaStream_t s) {
     long long blocks = (maxbox + BAND_THREADS - 1) / BAND_THREADS;
     if (blocks > 148 * 16) blocks = 148 * 16;
     if (blocks < 1) blocks = 1;
-    band_kernel<Q, S><<<dim3((unsigned)blocks, a.nrot), BAND_THREADS, 0, s>>>(a);
+    band_kernel<<<dim3((unsigned)blocks, a.nrot), BAND_THREADS, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int Q, int S>
+static cudaError_t launch_wall_t(const StepArgs& a, cudaStream_t s) {
+    if (a.nrot == 0 || !a.wall_model) return cudaSuccess;
+    const dim3 grd(WALL_BLOCKS, a.nrot);
+    if (a.phase == 0) wall_kernel<Q, S, 0><<<grd, 128, 0, s>>>(a);
+    else wall_kernel<Q, S, 1><<<grd, 128, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 template <int Q, int S>
 static cudaError_t launch_force_t(const StepArgs& a, cudaStream_t s) {
     if (a.nrot == 0) return cudaSuccess;
-    force_kernel<Q, S><<<dim3(FORCE_BLOCKS, a.nrot), 256, 0, s>>>(a);
+    const dim3 grd(FORCE_BLOCKS, a.nrot);
+    if (a.phase == 0) force_kernel<Q, S, 0><<<grd, 256, 0, s>>>(a);
+    else force_kernel<Q, S, 1><<<grd, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -589,6 +627,9 @@ cudaError_t launch_collide(int Q, int S, const StepArgs& a, cudaStream_t s) {
 cudaError_t launch_band(int Q, int S, const StepArgs& a, cudaStream_t s) {
     HL_DISPATCH(Q, S, launch_band_t, a, s);
 }
+cudaError_t launch_wall(int Q, int S, const StepArgs& a, cudaStream_t s) {
+    HL_DISPATCH(Q, S, launch_wall_t, a, s);
+}
 cudaError_t launch_force(int Q, int S, const StepArgs& a, cudaStream_t s) {
     HL_DISPATCH(Q, S, launch_force_t, a, s);
 }
@@ -605,21 +646,22 @@ cudaError_t launch_mass(int Q, int S, const MassArgs& m, cudaStream_t s) {
 }
 
 template <int Q, int S>
-static cudaError_t launch_init_t(void* f, long long N, const int n[3], const float* rho, const float* u,
-                                 float drho0, const float u0[3], cudaStream_t s) {
-    const dim3 grd((n[0] + 127) / 128, n[1], n[2]);
-    init_kernel<Q, S><<<grd, 128, 0, s>>>(f, N, n[0], n[1], n[2], rho, u, drho0, u0[0], u0[1], u0[2]);
+static cudaError_t launch_init_t(const StepArgs& a, const float* rho, const float* u, float drho0,
+                                 const float u0[3], cudaStream_t s) {
+    const dim3 grd((a.n[0] + 127) / 128, a.n[1], a.n[2]);
+    init_kernel<Q, S><<<grd, 128, 0, s>>>(a, rho, u, drho0, u0[0], u0[1], u0[2]);
     return cudaGetLastError();
 }
-cudaError_t launch_init(int Q, int S, void* f, long long N, const int n[3], const float* rho, const float* u,
-                        float drho0, const float u0[3], cudaStream_t s) {
-    HL_DISPATCH(Q, S, launch_init_t, f, N, n, rho, u, drho0, u0, s);
+cudaError_t launch_init(int Q, int S, const StepArgs& a, const float* rho, const float* u, float drho0,
+                        const float u0[3], cudaStream_t s) {
+    HL_DISPATCH(Q, S, launch_init_t, a, rho, u, drho0, u0, s);
 }
 
 template <int Q, int S>
 static cudaError_t launch_fields_t(const StepArgs& a, float* rho, float* u, cudaStream_t s) {
     const dim3 grd((a.n[0] + 127) / 128, a.n[1], a.n[2]);
-    fields_kernel<Q, S><<<grd, 128, 0, s>>>(a, rho, u);
+    if (a.phase == 0) fields_kernel<Q, S, 0><<<grd, 128, 0, s>>>(a, rho, u);
+    else fields_kernel<Q, S, 1><<<grd, 128, 0, s>>>(a, rho, u);
     return cudaGetLastError();
 }
 cudaError_t launch_fields(int Q, int S, const StepArgs& a, float* rho, float* u, cudaStream_t s) {
