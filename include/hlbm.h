@@ -71,6 +71,11 @@ typedef int hl_status;
  *                  x' = x - U t a
  *  mass_check_every  every K steps an FP64 mass total is taken (0 = never)
  *  mass_tol        relative drift of the total mass that fails the check
+ *  overlap         1: with rotors, the cells outside every rotor box are
+ *                  collided on the lattice's stream while the embedding,
+ *                  wall model, box collision and force reduction run on an
+ *                  internal high-priority stream (ordered by events; same
+ *                  results bit for bit); 0: everything on one stream
  */
 typedef struct hl_config {
     int nx, ny, nz;
@@ -88,6 +93,7 @@ typedef struct hl_config {
     const double* modes;
     int mass_check_every;
     double mass_tol;
+    int overlap;
 } hl_config;
 
 /* A rotor: n_blades copies of one blade grid plus a hub sphere (Sec. 3.1).
@@ -116,7 +122,7 @@ typedef struct hl_rotor_geometry {
 /* Default parameters (D3Q19, FP32 storage, z streamwise, open boundaries,
  * tau_mo 0.5005, C_S 0.1, u_in 0.05, smoothstep over eps_h = 2, wall model on
  * with E 9.8, kappa 0.41, y_s 2, tol 1e-4, 10 iterations; mass check every 100
- * steps with 5 % tolerance).  The grid size is left at 0 and must be set. */
+ * steps with 5 % tolerance; overlap on).  The grid size is left at 0 and must be set. */
 void hl_config_defaults(hl_config* cfg);
 
 /* Bytes of device workspace hl_lattice_init needs for cfg.  Host only. */
@@ -212,9 +218,11 @@ hl_status hl_debug_collide(int q, int n, const float* d_g_in, const float* d_d, 
  * each launch of the time loop.  hl_profile_begin(lat, capacity) starts
  * recording (at most `capacity` launches per kernel kind; it creates CUDA
  * events, it allocates no device memory); hl_profile_end synchronises,
- * returns for each kind (0 band: embedding + wall model, 1 collide-and-stream,
- * 2 force reduction, 3 mass check) the summed duration in ms and the number of
- * launches, and releases the events.  Either output may be NULL. */
+ * returns for each kind (0 porosity embedding, 1 collide-and-stream of all
+ * cells, or of the cells outside every rotor box when overlap is on, 2 force
+ * reduction, 3 mass check, 4 wall model, 5 collide-and-stream of rotor boxes
+ * when overlap is on) the summed duration in ms and the number of launches
+ * ([6] each), and releases the events.  Either output may be NULL. */
 hl_status hl_profile_begin(hl_lattice* lat, int capacity);
 hl_status hl_profile_end(hl_lattice* lat, double* ms, long long* launches);
 

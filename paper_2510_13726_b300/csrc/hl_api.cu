@@ -94,10 +94,14 @@ struct hl_lattice {
     int nrot;
     RotorHost rot[MAXROT];
     char msg[256];
+    // second stream for the rotor-box chain, and the events that order it
+    cudaStream_t aux;
+    cudaEvent_t ev_bulk[2], ev_box[2], ev_fork, ev_join;
+    bool have_aux;
     // per-kernel event timing (hl_profile_begin / hl_profile_end)
     bool prof_on;
     int prof_cap;
-    std::vector<cudaEvent_t> prof_ev[4];   // start/stop pairs per kernel kind
+    std::vector<cudaEvent_t> prof_ev[6];   // start/stop pairs per kernel kind
 };
 
 namespace {
@@ -261,6 +265,7 @@ void hl_config_defaults(hl_config* c) {
     c->wm_maxit = 10;
     c->mass_check_every = 100;
     c->mass_tol = 0.05;
+    c->overlap = 1;
 }
 
 hl_status hl_workspace_size(const hl_config* cfg, size_t* bytes) {
@@ -308,6 +313,18 @@ hl_status hl_lattice_init(hl_lattice** out, const hl_config* cfg, void* d_worksp
     double m0 = 0.0;
     if ((st = compute_mass(lat, -1.0, &m0)) != HL_OK) { delete lat; return st; }
     lat->mass_ref = m0;
+    if (cfg->overlap) {
+        int lo = 0, hi = 0;
+        bool ok = cudaDeviceGetStreamPriorityRange(&lo, &hi) == cudaSuccess &&
+                  cudaStreamCreateWithPriority(&lat->aux, cudaStreamNonBlocking, hi) == cudaSuccess;
+        for (int k = 0; ok && k < 2; ++k)
+            ok = cudaEventCreateWithFlags(&lat->ev_bulk[k], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&lat->ev_box[k], cudaEventDisableTiming) == cudaSuccess;
+        ok = ok && cudaEventCreateWithFlags(&lat->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&lat->ev_join, cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) { hl_destroy(lat); return HL_ERR_CUDA; }
+        lat->have_aux = true;
+    }
     *out = lat;
     return HL_OK;
 }
@@ -444,7 +461,7 @@ hl_status hl_set_rotor(hl_lattice* lat, int* rotor_id, const hl_rotor_geometry* 
 }
 
 // records one event of kind k when profiling (start: even index, stop: odd)
-static cudaError_t prof_mark(hl_lattice* lat, int k) {
+static cudaError_t prof_mark(hl_lattice* lat, int k, cudaStream_t st) {
     if (!lat->prof_on) return cudaSuccess;
     std::vector<cudaEvent_t>& v = lat->prof_ev[k];
     if ((int)v.size() >= 2 * lat->prof_cap) return cudaSuccess;
@@ -452,37 +469,109 @@ static cudaError_t prof_mark(hl_lattice* lat, int k) {
     cudaError_t err = cudaEventCreate(&e);
     if (err != cudaSuccess) return err;
     v.push_back(e);
-    return cudaEventRecord(e, lat->stream);
+    return cudaEventRecord(e, st);
+}
+
+// one step on a single stream
+static hl_status step_serial(hl_lattice* lat) {
+    const int Q = lat->cfg.q, S = lat->cfg.storage;
+    cudaStream_t st = lat->stream;
+    StepArgs a = make_args(lat);
+    a.part = 0;
+    if (lat->nrot > 0) {
+        HL_CUDA(lat, prof_mark(lat, 0, st));
+        HL_CUDA(lat, launch_band(Q, S, a, st));
+        HL_CUDA(lat, prof_mark(lat, 0, st));
+        if (lat->cfg.wall_model) {
+            HL_CUDA(lat, prof_mark(lat, 4, st));
+            HL_CUDA(lat, launch_wall(Q, S, a, st));
+            HL_CUDA(lat, prof_mark(lat, 4, st));
+        }
+    }
+    HL_CUDA(lat, prof_mark(lat, 1, st));
+    HL_CUDA(lat, launch_collide(Q, S, a, st));
+    HL_CUDA(lat, prof_mark(lat, 1, st));
+    if (lat->nrot > 0) {
+        HL_CUDA(lat, prof_mark(lat, 2, st));
+        HL_CUDA(lat, launch_force(Q, S, a, st));
+        HL_CUDA(lat, prof_mark(lat, 2, st));
+    }
+    return HL_OK;
+}
+
+// One step on two streams.  The AA pattern gives every memory location to
+// exactly one cell's thread, and the wall model and force only read cells
+// deep inside a rotor box, so within a step the bulk launch (cells outside
+// every box, lattice stream) and the box chain (embedding, wall model, box
+// collision, force; aux stream) touch disjoint memory.  Across steps:
+// box(t) waits for bulk(t-1), bulk(t) waits for box(t-1).
+static hl_status step_overlap(hl_lattice* lat) {
+    const int Q = lat->cfg.q, S = lat->cfg.storage;
+    const int p = (int)(lat->t & 1), q = p ^ 1;
+    cudaStream_t us = lat->stream, ax = lat->aux;
+    StepArgs a = make_args(lat);
+    // lattice stream: cells outside every rotor box
+    HL_CUDA(lat, cudaStreamWaitEvent(us, lat->ev_box[q], 0));
+    a.part = 1;
+    HL_CUDA(lat, prof_mark(lat, 1, us));
+    HL_CUDA(lat, launch_collide(Q, S, a, us));
+    HL_CUDA(lat, prof_mark(lat, 1, us));
+    HL_CUDA(lat, cudaEventRecord(lat->ev_bulk[p], us));
+    // aux stream: embedding, wall model, box collision, force
+    HL_CUDA(lat, prof_mark(lat, 0, ax));
+    HL_CUDA(lat, launch_band(Q, S, a, ax));
+    HL_CUDA(lat, prof_mark(lat, 0, ax));
+    if (lat->cfg.wall_model) {
+        HL_CUDA(lat, prof_mark(lat, 4, ax));
+        HL_CUDA(lat, launch_wall(Q, S, a, ax));
+        HL_CUDA(lat, prof_mark(lat, 4, ax));
+    }
+    HL_CUDA(lat, cudaStreamWaitEvent(ax, lat->ev_bulk[q], 0));
+    a.part = 2;
+    for (int k = 0; k < lat->nrot; ++k) {
+        a.part_rotor = k;
+        HL_CUDA(lat, prof_mark(lat, 5, ax));
+        HL_CUDA(lat, launch_collide(Q, S, a, ax));
+        HL_CUDA(lat, prof_mark(lat, 5, ax));
+    }
+    HL_CUDA(lat, cudaEventRecord(lat->ev_box[p], ax));
+    a.part = 0;
+    HL_CUDA(lat, prof_mark(lat, 2, ax));
+    HL_CUDA(lat, launch_force(Q, S, a, ax));
+    HL_CUDA(lat, prof_mark(lat, 2, ax));
+    return HL_OK;
 }
 
 hl_status hl_step_async(hl_lattice* lat, int n) {
     if (!lat || n < 0) return HL_ERR_ARG;
-    const int Q = lat->cfg.q, S = lat->cfg.storage;
+    const bool two = lat->have_aux && lat->nrot > 0;
+    if (two && n > 0) {
+        // everything issued on the lattice stream so far precedes the aux work
+        HL_CUDA(lat, cudaEventRecord(lat->ev_fork, lat->stream));
+        HL_CUDA(lat, cudaStreamWaitEvent(lat->aux, lat->ev_fork, 0));
+    }
     for (int s = 0; s < n; ++s) {
-        const StepArgs a = make_args(lat);
-        if (lat->nrot > 0) {
-            HL_CUDA(lat, prof_mark(lat, 0));
-            HL_CUDA(lat, launch_band(Q, S, a, lat->stream));
-            HL_CUDA(lat, launch_wall(Q, S, a, lat->stream));
-            HL_CUDA(lat, prof_mark(lat, 0));
-        }
-        HL_CUDA(lat, prof_mark(lat, 1));
-        HL_CUDA(lat, launch_collide(Q, S, a, lat->stream));
-        HL_CUDA(lat, prof_mark(lat, 1));
-        if (lat->nrot > 0) {
-            HL_CUDA(lat, prof_mark(lat, 2));
-            HL_CUDA(lat, launch_force(Q, S, a, lat->stream));
-            HL_CUDA(lat, prof_mark(lat, 2));
-        }
+        hl_status st = two ? step_overlap(lat) : step_serial(lat);
+        if (st != HL_OK) return st;
+        const long long t_done = lat->t;
         lat->t += 1;
         lat->n_avg += 1;
         const int K = lat->cfg.mass_check_every;
         if (K > 0 && lat->t % K == 0) {
-            HL_CUDA(lat, prof_mark(lat, 3));
-            hl_status st = compute_mass(lat, lat->cfg.mass_tol, nullptr);
+            const int p = (int)(t_done & 1);
+            if (two) HL_CUDA(lat, cudaStreamWaitEvent(lat->stream, lat->ev_box[p], 0));
+            HL_CUDA(lat, prof_mark(lat, 3, lat->stream));
+            st = compute_mass(lat, lat->cfg.mass_tol, nullptr);
             if (st != HL_OK) return st;
-            HL_CUDA(lat, prof_mark(lat, 3));
+            HL_CUDA(lat, prof_mark(lat, 3, lat->stream));
+            // the next box collision must also wait for the mass total
+            if (two) HL_CUDA(lat, cudaEventRecord(lat->ev_bulk[p], lat->stream));
         }
+    }
+    if (two && n > 0) {
+        // the lattice stream sees the completed aux work
+        HL_CUDA(lat, cudaEventRecord(lat->ev_join, lat->aux));
+        HL_CUDA(lat, cudaStreamWaitEvent(lat->stream, lat->ev_join, 0));
     }
     return HL_OK;
 }
@@ -503,7 +592,7 @@ hl_status hl_profile_end(hl_lattice* lat, double* ms, long long* launches) {
     lat->prof_on = false;
     HL_CUDA(lat, cudaStreamSynchronize(lat->stream));
     hl_status st = HL_OK;
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 6; ++k) {
         std::vector<cudaEvent_t>& v = lat->prof_ev[k];
         double sum = 0.0;
         const size_t pairs = v.size() / 2;
@@ -763,6 +852,14 @@ void hl_destroy(hl_lattice* lat) {
     if (!lat) return;
     for (auto& v : lat->prof_ev)
         for (cudaEvent_t e : v) cudaEventDestroy(e);
+    if (lat->aux) cudaStreamSynchronize(lat->aux);
+    for (int k = 0; k < 2; ++k) {
+        if (lat->ev_bulk[k]) cudaEventDestroy(lat->ev_bulk[k]);
+        if (lat->ev_box[k]) cudaEventDestroy(lat->ev_box[k]);
+    }
+    if (lat->ev_fork) cudaEventDestroy(lat->ev_fork);
+    if (lat->ev_join) cudaEventDestroy(lat->ev_join);
+    if (lat->aux) cudaStreamDestroy(lat->aux);
     delete lat;
 }
 

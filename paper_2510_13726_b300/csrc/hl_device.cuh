@@ -390,27 +390,36 @@ __device__ inline void rotor_normal(const RotorDev& R, int which, int x, int y, 
 // u+ ~ 216, which the iterates of a cold start do reach).  Only the few
 // wall cells run this code.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double spalding_yplus(double up, double E, double kappa) {
+// y+(u+) of Eq. (spalding) and its derivative, given e = exp(kappa u+)
+__device__ __forceinline__ double spalding_yplus_e(double up, double e, double E, double kappa) {
     const double k = kappa * up;
-    return up + (exp(k) - 1.0 - k - 0.5 * k * k - k * k * k / 6.0) / E;
+    return up + (e - 1.0 - k - 0.5 * k * k - k * k * k / 6.0) / E;
 }
-__device__ __forceinline__ double spalding_dyplus(double up, double E, double kappa) {
+__device__ __forceinline__ double spalding_dyplus_e(double up, double e, double E, double kappa) {
     const double k = kappa * up;
-    return 1.0 + kappa / E * (exp(k) - 1.0 - k - 0.5 * k * k);
+    return 1.0 + kappa / E * (e - 1.0 - k - 0.5 * k * k);
 }
 
 // Newton-Raphson on Eq. (implicitWF): stop when the residual changes by less
-// than tol, at most maxit iterations; a non-positive iterate is halved.
+// than tol, at most maxit iterations; a non-positive iterate is halved.  The
+// exponential of each iterate is evaluated once and serves both the residual
+// and the derivative.
 __device__ inline double wall_newton(double u, double y, double nu, double guess, double E, double kappa,
                                      double tol, int maxit) {
     double ut = guess;
-    double fv = spalding_yplus(u / ut, E, kappa) - y * ut / nu;
+    double up = u / ut;
+    double e = exp(kappa * up);
+    double fv = spalding_yplus_e(up, e, E, kappa) - y * ut / nu;
     for (int it = 0; it < maxit; ++it) {
-        const double fp = -spalding_dyplus(u / ut, E, kappa) * u / (ut * ut) - y / nu;
+        const double fp = -spalding_dyplus_e(up, e, E, kappa) * u / (ut * ut) - y / nu;
         double un = ut - fv / fp;
         if (!(un > 0.0)) un = 0.5 * ut;
-        const double fn = spalding_yplus(u / un, E, kappa) - y * un / nu;
+        const double upn = u / un;
+        const double en = exp(kappa * upn);
+        const double fn = spalding_yplus_e(upn, en, E, kappa) - y * un / nu;
         ut = un;
+        up = upn;
+        e = en;
         if (fabs(fn - fv) < tol) break;
         fv = fn;
     }
@@ -421,12 +430,15 @@ __device__ inline double wall_newton(double u, double y, double nu, double guess
 __device__ inline double spalding_uplus(double yp, double E, double kappa, double tol, int maxit) {
     const double lg = log(1.0 + E * yp) / kappa;
     double up = yp < lg ? yp : lg;
-    double g = spalding_yplus(up, E, kappa) - yp;
+    double e = exp(kappa * up);
+    double g = spalding_yplus_e(up, e, E, kappa) - yp;
     for (int it = 0; it < maxit; ++it) {
-        double un = up - g / spalding_dyplus(up, E, kappa);
+        double un = up - g / spalding_dyplus_e(up, e, E, kappa);
         if (!(un > 0.0)) un = 0.5 * up;
-        const double gn = spalding_yplus(un, E, kappa) - yp;
+        const double en = exp(kappa * un);
+        const double gn = spalding_yplus_e(un, en, E, kappa) - yp;
         up = un;
+        e = en;
         if (fabs(gn - g) < tol) break;
         g = gn;
     }

@@ -37,6 +37,8 @@ struct StepArgs {
     const float* uplane_prev;  // [3][plane]
     float* uplane_cur;
     unsigned* err;
+    int part;                // collide cells: 0 all, 1 outside every rotor box, 2 the box of part_rotor
+    int part_rotor;
     int nrot;
     RotorDev rot[MAXROT];
 };

@@ -78,10 +78,19 @@ __device__ __forceinline__ int sel3(int ax, int a0, int a1, int a2) { return ax 
 // ---------------------------------------------------------------------------
 template <int Q, int S, int PH>
 __global__ void __launch_bounds__(128) collide_kernel(const StepArgs a) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
-    if (x >= a.n[0] || y >= a.n[1]) return;
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    int z = blockIdx.z;
+    if (a.part == 2) {
+        // the box of one rotor: launch grid spans the box
+        const RotorDev& R = a.rot[a.part_rotor];
+        if (x >= R.n[0] || y >= R.n[1]) return;
+        x += R.lo[0];
+        y += R.lo[1];
+        z += R.lo[2];
+    } else if (x >= a.n[0] || y >= a.n[1]) {
+        return;
+    }
     const int cell = (z * a.n[1] + y) * a.n[0] + x;
     const int ax = a.flow_axis;
     const int ca = sel3(ax, x, y, z);
@@ -92,7 +101,6 @@ __global__ void __launch_bounds__(128) collide_kernel(const StepArgs a) {
     make_offs(a, x, y, z, o);
     float g[Q];
     if (!inlet && !outlet) {
-        load_pre<Q, S, PH>(a, cell, o, g);
         int rk = -1, bi = 0;
         for (int k = 0; k < a.nrot; ++k) {
             const unsigned dx = (unsigned)(x - a.rot[k].lo[0]), dy = (unsigned)(y - a.rot[k].lo[1]),
@@ -103,6 +111,8 @@ __global__ void __launch_bounds__(128) collide_kernel(const StepArgs a) {
                 break;
             }
         }
+        if (a.part == 1 && rk >= 0) return;   // box cells belong to the box launch
+        load_pre<Q, S, PH>(a, cell, o, g);
         float u[3];
         float rho;
         if (rk >= 0) {
@@ -425,11 +435,21 @@ __global__ void __launch_bounds__(256) force_kernel(const StepArgs a) {
     __syncthreads();
     if (last) {
         __threadfence();
-        if (threadIdx.x < 6) {
+        // combine the block partials in a fixed order: strided per thread, then a tree
+        for (int k = 0; k < 6; ++k) {
             double v = 0.0;
-            for (int b = 0; b < (int)gridDim.x; ++b) v += ((volatile double*)R.partial)[b * 6 + threadIdx.x];
-            R.acc[threadIdx.x] = v;
-            R.acc[6 + threadIdx.x] += v;
+            for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+                v += ((volatile double*)R.partial)[b * 6 + k];
+            v = warp_sum(v);
+            __syncthreads();
+            if (lane == 0) sh[warp][0] = v;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double t = 0.0;
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w][0];
+                R.acc[k] = t;
+                R.acc[6 + k] += t;
+            }
         }
         if (threadIdx.x == 0) {
             *R.done = 0u;
@@ -484,15 +504,23 @@ __global__ void __launch_bounds__(256) mass_kernel(const MassArgs m) {
         last = atomicAdd(m.done, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (last && threadIdx.x == 0) {
+    if (last) {
         __threadfence();
-        double s = 0.0;
-        for (int b = 0; b < (int)gridDim.x; ++b) s += ((volatile double*)m.partial)[b];
-        s += m.shift_mass;
-        *m.out = s;
-        if (!(fabs(s) < 1e300)) atomicOr(m.err, ERR_NONFINITE);
-        else if (m.tol >= 0.0 && fabs(s - m.ref) > m.tol * fabs(m.ref)) atomicOr(m.err, ERR_MASS);
-        *m.done = 0u;
+        double t = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += ((volatile double*)m.partial)[b];
+        t = warp_sum(t);
+        __syncthreads();
+        if (lane == 0) sh[warp] = t;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
+            s += m.shift_mass;
+            *m.out = s;
+            if (!(fabs(s) < 1e300)) atomicOr(m.err, ERR_NONFINITE);
+            else if (m.tol >= 0.0 && fabs(s - m.ref) > m.tol * fabs(m.ref)) atomicOr(m.err, ERR_MASS);
+            *m.done = 0u;
+        }
     }
 }
 
@@ -573,8 +601,9 @@ static dim3 cell_block(int nx) {
 
 template <int Q, int S>
 static cudaError_t launch_collide_t(const StepArgs& a, cudaStream_t s) {
-    const dim3 blk = cell_block(a.n[0]);
-    const dim3 grd((a.n[0] + blk.x - 1) / blk.x, (a.n[1] + blk.y - 1) / blk.y, a.n[2]);
+    const int* n = a.part == 2 ? a.rot[a.part_rotor].n : a.n;
+    const dim3 blk = cell_block(n[0]);
+    const dim3 grd((n[0] + blk.x - 1) / blk.x, (n[1] + blk.y - 1) / blk.y, n[2]);
     if (a.phase == 0) collide_kernel<Q, S, 0><<<grd, blk, 0, s>>>(a);
     else collide_kernel<Q, S, 1><<<grd, blk, 0, s>>>(a);
     return cudaGetLastError();

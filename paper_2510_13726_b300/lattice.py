@@ -30,7 +30,7 @@ class Lattice:
     def __init__(self, nx, ny, nz, q=19, storage="f32", flow_axis=2, open_boundaries=True,
                  tau_mo=0.5005, c_smag=0.1, u_in=0.05, eps_h=2.0, transition="smoothstep",
                  wall_model=True, wm_E=9.8, wm_kappa=0.41, wm_ysample=2.0, wm_tol=1e-4,
-                 wm_maxit=10, modes=None, mass_check_every=100, mass_tol=0.05,
+                 wm_maxit=10, modes=None, mass_check_every=100, mass_tol=0.05, overlap=True,
                  device=None, stream=None):
         import torch
         self.device = torch.device(device if device is not None else "cuda")
@@ -49,6 +49,7 @@ class Lattice:
         cfg.wm_E, cfg.wm_kappa, cfg.wm_ysample = float(wm_E), float(wm_kappa), float(wm_ysample)
         cfg.wm_tol, cfg.wm_maxit = float(wm_tol), int(wm_maxit)
         cfg.mass_check_every, cfg.mass_tol = int(mass_check_every), float(mass_tol)
+        cfg.overlap = int(bool(overlap))
         self._modes = None
         if modes is not None and len(modes):
             self._modes = np.ascontiguousarray(modes, dtype=np.float64).reshape(-1, 9)
@@ -195,15 +196,15 @@ class Lattice:
         return m.value
 
     # -- per-kernel timing ----------------------------------------------------
-    KERNELS = ("band", "collide", "force", "mass")
+    KERNELS = ("band", "collide", "force", "mass", "wall", "collide_box")
 
     def profile_begin(self, capacity: int = 100000):
         self._check(lib().hl_profile_begin(self._h, int(capacity)))
 
     def profile_end(self):
         """{kernel: (total ms, launches)} of the launches since profile_begin."""
-        ms = np.zeros(4)
-        n = (C.c_longlong * 4)()
+        ms = np.zeros(6)
+        n = (C.c_longlong * 6)()
         self._check(lib().hl_profile_end(self._h, ms.ctypes.data_as(C.POINTER(C.c_double)), n))
         return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(self.KERNELS)}
 
