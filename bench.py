@@ -254,6 +254,8 @@ def run_cuda(args):
     else:
         alg_bytes = collide_bytes(wl.q, args.storage, wl.cells, box_cells, wall_cells)
         roof_cells = wl.cells
+    # algorithmic bytes of all collide-and-stream work of one step (every cell)
+    step_bytes = collide_bytes(wl.q, args.storage, wl.cells, box_cells, wall_cells)
     c_ms, c_n = prof["collide"]
     per_launch_s = c_ms / c_n / 1e3
     achieved = alg_bytes / per_launch_s / 1e9
@@ -301,6 +303,8 @@ def run_cuda(args):
                          "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
                          else "fallback", "traffic": traffic,
                          "alg_bytes_per_launch": alg_bytes, "cells_per_launch": roof_cells,
+                         "step_effective_gbs": round(step_bytes / (t_max / K) / 1e9, 1),
+                         "step_effective_frac": round(step_bytes / (t_max / K) / 1e9 / peak, 4),
                          "frac_of_8TBps_nominal": round(achieved / 8000.0, 4)},
             "kernels": kernels,
             "gpu_launches": launches,
