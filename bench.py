@@ -315,9 +315,67 @@ def run_cuda(args):
             "thrust_last": float(F[0, wl.flow_axis]) if lat.nrot else None,
             "cpu_baseline": cpu,
         }
+        if world == 1 and not args.no_extra:
+            lat.close()
+            torch.cuda.empty_cache()
+            line["storage_study"] = storage_study(dev, args.extra_steps)
+            line["farm"] = farm_run(dev, args.extra_steps)
         print(json.dumps(line), flush=True)
     lat.close()
     return 0
+
+
+def timed_run(wl, storage, steps, warmup, dev):
+    """MLUPS of `steps` steps of a workload (CUDA events on the lattice stream)
+    and the per-launch roofline of its collide-and-stream launch."""
+    import torch
+    from paper_2510_13726_b300 import Lattice
+    from paper_2510_13726_b300.perf import collide_bytes
+    lat = Lattice.from_workload(wl, storage=storage, device=dev)
+    lat.step(warmup)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    lat.profile_begin(4 * steps + 16)
+    e0.record(lat.stream)
+    lat.step_async(steps)
+    e1.record(lat.stream)
+    e1.synchronize()
+    prof = lat.profile_end()
+    lat.check()
+    ms = e0.elapsed_time(e1) / steps
+    box = sum(lat.rotor_box(k)[1][0] * lat.rotor_box(k)[1][1] * lat.rotor_box(k)[1][2] for k in range(lat.nrot))
+    cells = wl.cells - box if prof["collide_box"][1] else wl.cells
+    c_ms, c_n = prof["collide"]
+    peak, _ = measured_peaks()
+    gbs = collide_bytes(wl.q, storage, cells) / (c_ms / c_n / 1e3) / 1e9
+    F, _ = lat.forces()
+    lat.close()
+    del lat
+    torch.cuda.empty_cache()
+    return {"MLUPS": round(wl.cells / ms / 1e3, 1), "ms_per_step": round(ms, 4),
+            "collide_gbs": round(gbs, 1), "collide_frac": round(gbs / peak, 4),
+            "thrust_last": [round(float(f[wl.flow_axis]), 6) for f in F]}
+
+
+def storage_study(dev, steps):
+    """D3Q27 512x512x1024 rotor (R = 128, TSR 7): FP32 vs FP16 / BF16 storage."""
+    import workloads as W
+    wl = W.workload("rotor1024_q27")
+    out = {"workload": "rotor1024_q27: 512x512x1024 D3Q27, R=128 NACA4412 rotor, TSR 7", "steps": steps}
+    for st in ("f32", "f16s", "bf16s"):
+        out[st] = timed_run(wl, st, steps, 5, dev)
+    for st in ("f16s", "bf16s"):
+        out[f"ratio_{st}_over_f32"] = round(out[st]["MLUPS"] / out["f32"]["MLUPS"], 3)
+    return out
+
+
+def farm_run(dev, steps):
+    """Wind-farm scale on one GPU: 1536x512x1024 D3Q19 FP32, 3x2 rotors R=64."""
+    import workloads as W
+    wl = W.workload("farm")
+    r = timed_run(wl, "f32", steps, 5, dev)
+    r["workload"] = "farm: 1536x512x1024 (805M cells) D3Q19 FP32, 6 rotors R=64, flow along x, 5% turbulence"
+    return r
 
 
 def main(argv=None):
@@ -330,6 +388,8 @@ def main(argv=None):
     ap.add_argument("--storage", default="f32", choices=["f32", "f16s", "bf16s"])
     ap.add_argument("--cpu-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the 16-bit storage study and the farm run")
+    ap.add_argument("--extra-steps", type=int, default=40)
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "cuda":
         args.warmup = 3

@@ -73,9 +73,12 @@ class Lattice:
 
     # -- lifetime -----------------------------------------------------------
     def close(self):
+        """Release the handle and drop the device buffers it used."""
         if getattr(self, "_h", None):
             lib().hl_destroy(self._h)
             self._h = None
+            self._ws = None
+            self._rotor_ws = []
 
     def __del__(self):
         self.close()

@@ -277,3 +277,71 @@ def test_overlap_schedule_is_bit_identical(P):
     a.step(1)
     b.step(1)
     assert torch.equal(a.fields()[1], b.fields()[1])
+
+
+def test_d3q27_whole_step_parity(P):
+    """D3Q27 (adds the H_xyz third-order term) on the 48x48x96 rotor, FP32
+    storage: fields after 200 steps within the FP32 tolerance."""
+    wl = _wl48()
+    wl.q = 27
+    lat = P.Lattice.from_workload(wl)
+    o = O.from_workload(wl)
+    for t_target in (1, 50, 200):
+        lat.step(t_target - lat.t)
+        o.step(t_target - o.t)
+        rg, ug = (a.cpu().numpy().astype(np.float64) for a in lat.fields())
+        ro, uo = o.fields()
+        e_rho = np.linalg.norm((rg - ro)[1:-1]) / np.linalg.norm(ro[1:-1])
+        e_u = _rel_l2(ug[:, 1:-1], uo[:, 1:-1])
+        assert e_rho <= 1e-5 and e_u <= 1e-5, (t_target, e_rho, e_u)
+    Fg, _ = lat.forces()
+    Fo, _, _, _ = o.forces()
+    assert np.abs(Fg - Fo).max() <= 1e-3 * np.abs(Fo).max()
+
+
+@pytest.mark.parametrize("storage", ["f16s", "bf16s"])
+def test_16bit_storage_rotor48(P, storage):
+    """16-bit population storage (f_i - w_i in FP16 / BF16, FP32 arithmetic) on
+    the 48x48x96 rotor: time-averaged thrust and torque over steps 101-200
+    within 1 % of the FP64 oracle (the 16-bit accuracy target)."""
+    wl = _wl48()
+    lat = P.Lattice.from_workload(wl, storage=storage)
+    o = O.from_workload(wl)
+    lat.step(100)
+    o.step(100)
+    lat.forces(reset_avg=True)
+    o.reset_average()
+    lat.step(100)
+    o.step(100)
+    _, Fa = lat.forces()
+    _, Ma = lat.moments()
+    _, _, Fo, Mo = o.forces()
+    a = wl.flow_axis
+    assert abs(Fa[0, a] - Fo[0, a]) <= 0.01 * abs(Fo[0, a]), (Fa, Fo)
+    assert abs(Ma[0, a] - Mo[0, a]) <= 0.01 * abs(Mo[0, a]), (Ma, Mo)
+
+
+def test_16bit_precision_study_rotor256_q27(P):
+    """The precision study: D3Q27 128x128x256 rotor (R = 32, TSR 7), 1000 steps,
+    thrust and torque averaged over the last 500 steps, FP32 / FP16 / BF16
+    storage against the stored FP64 oracle run (tests/golden)."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "precision_rotor256_q27.json")
+    ref = json.load(open(path))
+    wl = W.workload("rotor256_q27")
+    a = wl.flow_axis
+    out = {}
+    for storage in ("f32", "f16s", "bf16s"):
+        lat = P.Lattice.from_workload(wl, storage=storage)
+        lat.step(ref["average_from_step"])
+        lat.forces(reset_avg=True)
+        lat.step(ref["steps"] - ref["average_from_step"])
+        _, Fa = lat.forces()
+        _, Ma = lat.moments()
+        out[storage] = (abs(Fa[0, a] / ref["thrust_mean"] - 1), abs(Ma[0, a] / ref["torque_mean"] - 1))
+        lat.close()
+    print("relative error of mean thrust, torque:", out)
+    assert out["f32"][0] < 1e-3 and out["f32"][1] < 1e-3
+    for s in ("f16s", "bf16s"):
+        assert out[s][0] <= 0.01 and out[s][1] <= 0.01, (s, out[s])
