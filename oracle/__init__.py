@@ -100,6 +100,20 @@ def lib():
         L.or_rotor_phi.argtypes = [C.POINTER(Rotor), C.c_long, C.c_int, _ip, _fp, _ip]
         L.or_rotor_normal.argtypes = [C.POINTER(Rotor), C.c_long, C.c_int, C.c_int, C.c_int,
                                       C.c_int, _dp]
+        L.or_collide_vjp_cells.restype = C.c_int
+        L.or_collide_vjp_cells.argtypes = [C.c_int, C.c_int, _dp, _dp, _dp, _dp, _dp, C.c_double,
+                                           C.c_double, _dp, _dp, _dp, _dp, _dp]
+        L.or_set_d0.restype = C.c_int
+        L.or_set_d0.argtypes = [C.c_void_p, _dp]
+        L.or_set_pitch.restype = C.c_int
+        L.or_set_pitch.argtypes = [C.c_void_p, C.c_int, C.c_double]
+        L.or_freeze_sets.argtypes = [C.c_void_p, C.c_int]
+        L.or_adjoint.restype = C.c_int
+        L.or_adjoint.argtypes = [C.c_void_p, C.c_int, C.c_int, _dp, _dp, _dp, _dp, _dp]
+        L.or_porosity_tangent.argtypes = [C.c_void_p, _dp]
+        L.or_wall_tangent.argtypes = [C.c_void_p, _dp, _dp]
+        L.or_rotor_normal_tangent.argtypes = [C.POINTER(Rotor), C.c_long, C.c_int, C.c_int, C.c_int,
+                                              C.c_int, _dp]
         L.or_sizeof_params.restype = C.c_size_t
         L.or_sizeof_rotor.restype = C.c_size_t
         assert L.or_sizeof_params() == C.sizeof(Params)
@@ -212,10 +226,45 @@ def rotor_phi(rotor, t, xyz):
     return phi, which
 
 
+def rotor_normal_tangent(rotor, t, which, x, y, z):
+    """d n / d pitch of component `which` at cell (x, y, z), time t (complex step)."""
+    dn = np.zeros(3)
+    lib().or_rotor_normal_tangent(C.byref(rotor), int(t), int(which), int(x), int(y), int(z), _ptr(dn))
+    return dn
+
+
 def rotor_normal(rotor, t, which, x, y, z):
     n = np.zeros(3)
     lib().or_rotor_normal(C.byref(rotor), int(t), int(which), int(x), int(y), int(z), _ptr(n))
     return n
+
+
+def collide_vjp_cells(q, f, lam_star, d=None, uB=None, sigma=None, Sfd=None, tau_mo=0.5005, c_smag=0.1):
+    """Vector-Jacobian product of the collision of n independent cells, by
+    complex-step differentiation: lam_star[n][q] (adjoint of f*) ->
+    (lam_f[n][q], g_d[n], g_uB[n][3], g_S[n][3][3])."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    lam_star = np.ascontiguousarray(lam_star, dtype=np.float64).reshape(f.shape)
+    n = f.shape[0]
+
+    def conv(a, s):
+        if a is None:
+            return None
+        return np.ascontiguousarray(np.broadcast_to(np.asarray(a, dtype=np.float64), s))
+
+    d = conv(d, (n,))
+    uB = conv(uB, (n, 3))
+    sigma = conv(sigma, (n,))
+    Sfd = conv(Sfd, (n, 3, 3))
+    lam_f = np.zeros_like(f)
+    g_d = np.zeros(n)
+    g_uB = np.zeros((n, 3))
+    g_S = np.zeros((n, 3, 3))
+    rc = lib().or_collide_vjp_cells(q, n, _ptr(f), _ptr(d), _ptr(uB), _ptr(sigma), _ptr(Sfd), tau_mo, c_smag,
+                                    _ptr(lam_star), _ptr(lam_f), _ptr(g_d), _ptr(g_uB), _ptr(g_S))
+    if rc:
+        raise ValueError("oracle: bad lattice")
+    return lam_f, g_d, g_uB, g_S
 
 
 class Oracle:
@@ -327,6 +376,53 @@ class Oracle:
         out = np.empty((nc, nb, 3))
         lib().or_inflow_plane(self._h, int(t), _ptr(out))
         return out
+
+    def set_d0(self, d0):
+        """Static porosity multiplier d0 (shape (nz, ny, nx)); None restores d0 = 1."""
+        if d0 is None:
+            lib().or_set_d0(self._h, None)
+            return
+        self._d0 = np.ascontiguousarray(np.broadcast_to(d0, self.shape), dtype=np.float64)
+        lib().or_set_d0(self._h, _ptr(self._d0))
+
+    def set_pitch(self, k: int, pitch: float):
+        if lib().or_set_pitch(self._h, int(k), float(pitch)):
+            raise IndexError("rotor index")
+
+    def freeze_sets(self, on: bool = True):
+        """Hold the cell sets at the current pitches; porosity, normals and wall
+        distances keep following set_pitch."""
+        lib().or_freeze_sets(self._h, int(bool(on)))
+
+    def adjoint(self, steps: int, avg_last: int, w_thrust, w_torque):
+        """Run `steps` steps; return (J, dJ/dpitch[n_rotors], dJ/dd0 (nz, ny, nx)) for
+        J = mean over the last avg_last steps of sum_k wT_k F_k.a_k + wQ_k M_k.a_k."""
+        n = max(1, self.nrot)
+        wT = np.zeros(n)
+        wQ = np.zeros(n)
+        wT[:self.nrot] = w_thrust
+        wQ[:self.nrot] = w_torque
+        J = np.zeros(1)
+        gp = np.zeros(n)
+        gd0 = np.zeros(self.shape)
+        rc = lib().or_adjoint(self._h, int(steps), int(avg_last), _ptr(wT), _ptr(wQ), _ptr(J), _ptr(gp), _ptr(gd0))
+        if rc:
+            raise ValueError(f"oracle adjoint failed ({rc})")
+        return float(J[0]), gp[:self.nrot], gd0
+
+    def porosity_tangent(self):
+        """d(d_rotor)/d(pitch) of the last porosity update, shape (nz, ny, nx)."""
+        out = np.zeros(self.shape)
+        lib().or_porosity_tangent(self._h, _ptr(out))
+        return out
+
+    def wall_tangent(self):
+        """Run the porosity update and wall model of the current step (state not
+        advanced) and return (d du/d pitch (nz,ny,nx,3), d S/d pitch (nz,ny,nx,3,3))."""
+        ddu = np.zeros(self.shape + (3,))
+        dS = np.zeros(self.shape + (3, 3))
+        lib().or_wall_tangent(self._h, _ptr(ddu), _ptr(dS))
+        return ddu, dS
 
     def newton_stats(self):
         it, ev = C.c_long(0), C.c_long(0)

@@ -50,6 +50,7 @@
  *    operation order (the kernel's precision), because it decides discrete
  *    cell sets (solid, wall, force cells); everything downstream is FP64.
  */
+#include <complex.h>
 #include <math.h>
 #ifndef M_PI
 #define M_PI 3.14159265358979323846
@@ -411,6 +412,29 @@ static float rotor_phi_f32(const or_rotor* R, const blade_frames* B, int ix, int
     return best;
 }
 
+/* Signed distance of one component (blade `which`, or the hub when which =
+   n_blades) at the frames B, with the same binary32 operations as
+   rotor_phi_f32: for the component that attains the minimum the two agree
+   bit for bit. */
+static float component_phi_f32(const or_rotor* R, const blade_frames* B, int which, int ix, int iy, int iz)
+{
+    int a = R->axis, b = (a + 1) % 3, c = (a + 2) % 3;
+    int ii[3] = {ix, iy, iz};
+    float rl[3];
+    for (int k = 0; k < 3; ++k) rl[k] = (float)ii[k] - (float)R->center[k];
+    float rb = rl[b], rc = rl[c], ra = rl[a];
+    if (which >= R->n_blades) {
+        float r2 = fmaf(rb, rb, fmaf(rc, rc, ra * ra));
+        return sqrtf(r2) - (float)R->hub_radius;
+    }
+    int k = which;
+    float pR = fmaf(B->ck[k], rb, B->sk[k] * rc);
+    float pT = fmaf(B->ck[k], rc, -(B->sk[k] * rb));
+    float qT = fmaf(B->cp, pT, -(B->sp * ra));
+    float qA = fmaf(B->cp, ra, B->sp * pT);
+    return blade_sample_f32(R, pR, qT, qA);
+}
+
 /* Outward unit normal (lab frame, FP64) of the component `which` of rotor R
    at cell (ix, iy, iz): trilinear interpolation of the central-difference
    gradient of the blade grid, rotated back through pitch and azimuth; the
@@ -525,6 +549,7 @@ typedef struct {
     float* phi;      /* [N] binary32 decision value */
     double* d;       /* [N] porosity */
     signed char* tag;
+    signed char* which; /* [N] component (blade k, n_blades = hub) of force-set cells */
     unsigned char* flags;
     double* nrm;     /* [N][3] */
     double* y1;      /* [N][3] */
@@ -534,6 +559,9 @@ typedef struct {
     unsigned char* wm_active;
     double* uplane[2];
     long step;
+    double* d0;      /* [N] static porosity multiplier, NULL = 1 */
+    int frozen;      /* 1: cell sets from decision_pitch, porosity and normals from pitch */
+    double decision_pitch[OR_MAXROT];
     double F[OR_MAXROT][3], M[OR_MAXROT][3];
     double Fsum[OR_MAXROT][3], Msum[OR_MAXROT][3];
     long navg;
@@ -598,8 +626,15 @@ static void cell_velocity(const or_state* S, size_t x, double u[3], double* rho_
 static void update_porosity(or_state* S)
 {
     const or_params* P = &S->P;
-    blade_frames BF[OR_MAXROT];
-    for (int k = 0; k < S->nrot; ++k) blade_frames_at(&S->rot[k].r, S->step, &BF[k]);
+    /* BF: frames of the rotor's pitch; BD: frames that decide the cell sets
+       (the same unless the sets are frozen for a finite-difference check) */
+    blade_frames BF[OR_MAXROT], BD[OR_MAXROT];
+    for (int k = 0; k < S->nrot; ++k) {
+        blade_frames_at(&S->rot[k].r, S->step, &BF[k]);
+        or_rotor rd = S->rot[k].r;
+        if (S->frozen) rd.pitch = S->decision_pitch[k];
+        blade_frames_at(&rd, S->step, &BD[k]);
+    }
     #pragma omp parallel for schedule(static)
     for (int z = 0; z < P->nz; ++z)
         for (int y = 0; y < P->ny; ++y)
@@ -609,7 +644,7 @@ static void update_porosity(or_state* S)
                 int tag = -1, which = -1;
                 for (int k = 0; k < S->nrot; ++k) {
                     int w;
-                    float v = rotor_phi_f32(&S->rot[k].r, &BF[k], x, y, z, &w);
+                    float v = rotor_phi_f32(&S->rot[k].r, &BD[k], x, y, z, &w);
                     if (v < best) { best = v; tag = k; which = w; }
                 }
                 S->phi[o] = best;
@@ -619,11 +654,14 @@ static void update_porosity(or_state* S)
                 if (best >= 0.0f && best < half) fl |= FL_W;
                 S->flags[o] = fl;
                 S->tag[o] = (fl & FL_B) ? (signed char)tag : -1;
-                S->d[o] = (fl & FL_B) ? porosity_of_phi((double)best, P->eps_h, P->transition) : 1.0;
+                S->which[o] = (fl & FL_B) ? (signed char)which : -1;
+                float val = best;
+                if (S->frozen && (fl & FL_B)) val = component_phi_f32(&S->rot[tag].r, &BF[tag], which, x, y, z);
+                S->d[o] = (fl & FL_B) ? porosity_of_phi((double)val, P->eps_h, P->transition) : 1.0;
                 if (fl & FL_W) {
                     double n[3];
                     rotor_normal(&S->rot[tag].r, &BF[tag], which, x, y, z, n);
-                    double y1 = (double)best > 0.5 ? (double)best : 0.5;
+                    double y1 = (double)val > 0.5 ? (double)val : 0.5;
                     for (int k = 0; k < 3; ++k) { S->nrm[3 * o + k] = n[k]; S->y1[3 * o + k] = y1 * n[k]; }
                 }
             }
@@ -713,6 +751,30 @@ static void wall_model(or_state* S)
     S->wm_evals += evals;
 }
 
+/* Band parameters of interior cell o at (x, y, z) for this step's collision:
+   d = d0 d_rotor (d0 = static multiplier, 1 unless set), u^B = u_s + du_WM,
+   sigma, S^FD (Sec. 2.2, 2.2.1; d_rotor = 1 and u^B = 0 outside the force set). */
+static void band_of_cell(const or_state* S, size_t o, int x, int y, int z, cell_band* B)
+{
+    const or_params* P = &S->P;
+    memset(B, 0, sizeof *B);
+    const double d0 = S->d0 ? S->d0[o] : 1.0;
+    B->d = d0;
+    B->sigma = 1.0;
+    if (S->flags[o] & FL_B) {
+        const or_rotor* R = &S->rot[S->tag[o]].r;
+        B->d = d0 * S->d[o];
+        solid_velocity(R, x, y, z, B->uB);
+        B->sigma = P->sigma_band;
+        if (P->wall_model && (S->flags[o] & FL_W)) {
+            for (int k = 0; k < 3; ++k) B->uB[k] += S->wm_du[3 * o + k];
+            for (int p = 0; p < 3; ++p)
+                for (int q = 0; q < 3; ++q) B->Sfd[p][q] = S->wm_S[9 * o + 3 * p + q];
+            B->sigma = 0.0;
+        }
+    }
+}
+
 static void collide_all(or_state* S)
 {
     const or_params* P = &S->P;
@@ -738,21 +800,7 @@ static void collide_all(or_state* S)
                 } else {
                     for (int i = 0; i < L->q; ++i) fin[i] = S->f[(size_t)i * S->N + o];
                     cell_band B;
-                    memset(&B, 0, sizeof B);
-                    B.d = 1.0;
-                    B.sigma = 1.0;
-                    if (S->flags[o] & FL_B) {
-                        const or_rotor* R = &S->rot[S->tag[o]].r;
-                        B.d = S->d[o];
-                        solid_velocity(R, x, y, z, B.uB);
-                        B.sigma = P->sigma_band;
-                        if (P->wall_model && (S->flags[o] & FL_W)) {
-                            for (int k = 0; k < 3; ++k) B.uB[k] += S->wm_du[3 * o + k];
-                            for (int p = 0; p < 3; ++p)
-                                for (int q = 0; q < 3; ++q) B.Sfd[p][q] = S->wm_S[9 * o + 3 * p + q];
-                            B.sigma = 0.0;
-                        }
-                    }
+                    band_of_cell(S, o, x, y, z, &B);
                     double u[3];
                     collide(L, fin, &B, P->tau_mo, P->c_smag, fout, u);
                     if (P->open_boundaries && xi[a] == dims[a] - 2)
@@ -863,6 +911,7 @@ or_state* or_create(const or_params* P, const or_rotor* rotors, int nrot)
     S->phi = (float*)malloc(sizeof(float) * N);
     S->d = (double*)malloc(sizeof(double) * N);
     S->tag = (signed char*)malloc(N);
+    S->which = (signed char*)malloc(N);
     S->flags = (unsigned char*)calloc(N, 1);
     S->nrm = (double*)calloc(3 * N, sizeof(double));
     S->y1 = (double*)calloc(3 * N, sizeof(double));
@@ -875,7 +924,7 @@ or_state* or_create(const or_params* P, const or_rotor* rotors, int nrot)
     size_t npl = (size_t)dims[(a + 1) % 3] * dims[(a + 2) % 3];
     S->uplane[0] = (double*)malloc(sizeof(double) * 3 * npl);
     S->uplane[1] = (double*)malloc(sizeof(double) * 3 * npl);
-    if (!S->f || !S->fpost || !S->phi || !S->d || !S->tag || !S->flags || !S->nrm || !S->y1 ||
+    if (!S->f || !S->fpost || !S->phi || !S->d || !S->tag || !S->which || !S->flags || !S->nrm || !S->y1 ||
         !S->wm_du || !S->wm_S || !S->wm_ut || !S->wm_active || !S->uplane[0] || !S->uplane[1]) {
         or_destroy(S);
         return NULL;
@@ -896,9 +945,10 @@ void or_destroy(or_state* S)
 {
     if (!S) return;
     for (int k = 0; k < S->nrot; ++k) free(S->rot[k].sdf);
-    free(S->modes); free(S->f); free(S->fpost); free(S->phi); free(S->d); free(S->tag); free(S->flags);
+    free(S->modes); free(S->f); free(S->fpost); free(S->phi); free(S->d); free(S->tag); free(S->which); free(S->flags);
     free(S->nrm); free(S->y1); free(S->wm_du); free(S->wm_S); free(S->wm_ut); free(S->wm_active);
     free(S->uplane[0]); free(S->uplane[1]);
+    free(S->d0);
     free(S);
 }
 
@@ -1120,3 +1170,840 @@ void or_rotor_normal(const or_rotor* R, long t, int which, int x, int y, int z, 
 
 size_t or_sizeof_params(void) { return sizeof(or_params); }
 size_t or_sizeof_rotor(void) { return sizeof(or_rotor); }
+
+/* ================================================================== */
+/* Discrete adjoint of the time step (FP64).                          */
+/*                                                                    */
+/* J = (1/n_avg) sum over the last n_avg steps of                     */
+/*     sum_k [ wT_k F_k(t).a_k + wQ_k M_k(t).a_k ]                    */
+/* differentiated with respect to each rotor's pitch and the static    */
+/* porosity multiplier d0 (d_eff = d0 d, d0 = 1 by default), with the  */
+/* cell sets (force cells, wall cells) frozen at their forward values. */
+/* Every local Jacobian is taken by complex-step differentiation       */
+/* (f(x + i h) = f(x) + i h f'(x) + O(h^2), h = 1e-30): derivatives to */
+/* rounding, with no hand-derived formula; the wall-model Newton roots */
+/* are differentiated by the implicit function theorem at the root,    */
+/* with complex-step partials of the residuals.                        */
+/* ================================================================== */
+
+typedef double complex cplx;
+static const double CSTEP = 1e-30;
+
+static void equilibrium_c(const or_lattice* L, cplx rho, const cplx u[3], cplx* feq)
+{
+    cplx A2[3][3], A3[3][3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            A2[a][b] = rho * u[a] * u[b];
+            for (int g = 0; g < 3; ++g) A3[a][b][g] = rho * u[a] * u[b] * u[g];
+        }
+    for (int i = 0; i < L->q; ++i) {
+        cplx cu = L->c[i][0] * u[0] + L->c[i][1] * u[1] + L->c[i][2] * u[2];
+        cplx c2 = 0, c3 = 0;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                c2 += L->H2[i][a][b] * A2[a][b];
+                for (int g = 0; g < 3; ++g) c3 += L->H3[i][a][b][g] * A3[a][b][g];
+            }
+        feq[i] = L->w[i] * (rho + rho * cu / CS2 + c2 / (2.0 * CS2 * CS2) + c3 / (6.0 * CS2 * CS2 * CS2));
+    }
+}
+
+/* complex twin of collide(): same formulas, complex band parameters */
+typedef struct { cplx d, uB[3], sigma, Sfd[3][3]; } cell_band_c;
+
+static void collide_c(const or_lattice* L, const cplx* f, const cell_band_c* B, double tau_mo, double c_smag,
+                      cplx* fout)
+{
+    cplx rho = 0, j[3] = {0, 0, 0}, Pi[3][3] = {{0}};
+    for (int i = 0; i < L->q; ++i) {
+        rho += f[i];
+        for (int a = 0; a < 3; ++a) {
+            j[a] += L->c[i][a] * f[i];
+            for (int b = 0; b < 3; ++b) Pi[a][b] += L->c[i][a] * L->c[i][b] * f[i];
+        }
+    }
+    cplx u[3] = {j[0] / rho, j[1] / rho, j[2] / rho};
+    cplx Pneq[3][3], Q = 0;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            Pneq[a][b] = Pi[a][b] - rho * CS2 * delta(a, b) - rho * u[a] * u[b];
+            Q += Pneq[a][b] * Pneq[a][b];
+        }
+    cplx tau = 0.5 * (tau_mo + csqrt(tau_mo * tau_mo + 18.0 * sqrt(2.0) * c_smag * c_smag * csqrt(Q) / rho));
+    cplx uh[3];
+    for (int a = 0; a < 3; ++a) uh[a] = B->d * u[a] + (1.0 - B->d) * B->uB[a];
+    cplx feq[OR_MAXQ];
+    equilibrium_c(L, rho, uh, feq);
+    cplx a3[3][3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            for (int g = 0; g < 3; ++g) a3[a][b][g] = uh[a] * Pneq[b][g] + uh[b] * Pneq[a][g] + uh[g] * Pneq[a][b];
+    for (int i = 0; i < L->q; ++i) {
+        cplx h2 = 0, h3 = 0, hs = 0;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                h2 += L->H2[i][a][b] * Pneq[a][b];
+                hs += L->H2[i][a][b] * B->Sfd[a][b];
+                for (int g = 0; g < 3; ++g) h3 += L->H3[i][a][b][g] * a3[a][b][g];
+            }
+        cplx f1 = L->w[i] * (h2 / (2.0 * CS2 * CS2) + h3 / (6.0 * CS2 * CS2 * CS2));
+        cplx f1fd = L->w[i] * rho * tau / CS2 * hs;
+        fout[i] = feq[i] + (1.0 - 1.0 / tau) * (B->sigma * f1 - (1.0 - B->sigma) * f1fd);
+    }
+}
+
+/* Vector-Jacobian product of one collision: given the adjoint lam_star of
+   the post-collision populations, the adjoint of the pre-collision
+   populations and of the band parameters d, u^B, S (S as a full 3x3). */
+static void collide_vjp(const or_lattice* L, const double* f, const cell_band* B, double tau_mo, double c_smag,
+                        const double* lam_star, double* lam_f, double* g_d, double g_uB[3], double g_S[3][3])
+{
+    cplx fc[OR_MAXQ] = {0}, out[OR_MAXQ];
+    cell_band_c Bc;
+    Bc.d = B->d;
+    Bc.sigma = B->sigma;
+    for (int a = 0; a < 3; ++a) {
+        Bc.uB[a] = B->uB[a];
+        for (int b = 0; b < 3; ++b) Bc.Sfd[a][b] = B->Sfd[a][b];
+    }
+    for (int i = 0; i < L->q; ++i) fc[i] = f[i];
+    for (int jdir = 0; jdir < L->q; ++jdir) {
+        fc[jdir] += I * CSTEP;
+        collide_c(L, fc, &Bc, tau_mo, c_smag, out);
+        fc[jdir] = f[jdir];
+        double s = 0.0;
+        for (int i = 0; i < L->q; ++i) s += lam_star[i] * cimag(out[i]) / CSTEP;
+        lam_f[jdir] = s;
+    }
+    if (g_d) {
+        Bc.d += I * CSTEP;
+        collide_c(L, fc, &Bc, tau_mo, c_smag, out);
+        Bc.d = B->d;
+        double s = 0.0;
+        for (int i = 0; i < L->q; ++i) s += lam_star[i] * cimag(out[i]) / CSTEP;
+        *g_d = s;
+    }
+    if (g_uB)
+        for (int a = 0; a < 3; ++a) {
+            Bc.uB[a] += I * CSTEP;
+            collide_c(L, fc, &Bc, tau_mo, c_smag, out);
+            Bc.uB[a] = B->uB[a];
+            double s = 0.0;
+            for (int i = 0; i < L->q; ++i) s += lam_star[i] * cimag(out[i]) / CSTEP;
+            g_uB[a] = s;
+        }
+    if (g_S)
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                Bc.Sfd[a][b] += I * CSTEP;
+                collide_c(L, fc, &Bc, tau_mo, c_smag, out);
+                Bc.Sfd[a][b] = B->Sfd[a][b];
+                double s = 0.0;
+                for (int i = 0; i < L->q; ++i) s += lam_star[i] * cimag(out[i]) / CSTEP;
+                g_S[a][b] = s;
+            }
+}
+
+/* n cells: as or_collide_cells, plus the adjoint lam_star[n][q] ->
+   lam_f[n][q], g_d[n], g_uB[n][3], g_S[n][9] (any output may be NULL) */
+int or_collide_vjp_cells(int q, int n, const double* f, const double* d, const double* uB, const double* sigma,
+                         const double* Sfd, double tau_mo, double c_smag, const double* lam_star, double* lam_f,
+                         double* g_d, double* g_uB, double* g_S)
+{
+    or_lattice L;
+    if (lattice_init(&L, q)) return -1;
+    #pragma omp parallel for schedule(static)
+    for (int c = 0; c < n; ++c) {
+        cell_band B;
+        B.d = d ? d[c] : 1.0;
+        for (int k = 0; k < 3; ++k) B.uB[k] = uB ? uB[3 * c + k] : 0.0;
+        B.sigma = sigma ? sigma[c] : 1.0;
+        for (int p = 0; p < 3; ++p)
+            for (int r = 0; r < 3; ++r) B.Sfd[p][r] = Sfd ? Sfd[9 * c + 3 * p + r] : 0.0;
+        double gd, gu[3], gS[3][3];
+        collide_vjp(&L, f + (size_t)q * c, &B, tau_mo, c_smag, lam_star + (size_t)q * c, lam_f + (size_t)q * c,
+                    &gd, gu, gS);
+        if (g_d) g_d[c] = gd;
+        for (int k = 0; k < 3; ++k)
+            if (g_uB) g_uB[3 * c + k] = gu[k];
+        for (int p = 0; p < 3; ++p)
+            for (int r = 0; r < 3; ++r)
+                if (g_S) g_S[9 * c + 3 * p + r] = gS[p][r];
+    }
+    return 0;
+}
+
+/* ---- setters used by gradient checks ---- */
+
+/* Static porosity multiplier d0 [N] (copied; NULL restores d0 = 1). */
+int or_set_d0(or_state* S, const double* d0)
+{
+    if (!d0) { free(S->d0); S->d0 = NULL; return 0; }
+    if (!S->d0) S->d0 = (double*)malloc(sizeof(double) * S->N);
+    if (!S->d0) return -1;
+    memcpy(S->d0, d0, sizeof(double) * S->N);
+    return 0;
+}
+
+int or_set_pitch(or_state* S, int k, double pitch)
+{
+    if (k < 0 || k >= S->nrot) return -1;
+    S->rot[k].r.pitch = pitch;
+    return 0;
+}
+
+/* on = 1: from now on the cell sets (force set, wall set, tag, component)
+   follow the pitch each rotor has at this call, while porosity, normal and
+   wall distance follow the current pitch (Sec. 3.1 quantities with the set
+   memberships held fixed); on = 0: both follow the current pitch. */
+void or_freeze_sets(or_state* S, int on)
+{
+    S->frozen = on ? 1 : 0;
+    for (int k = 0; k < S->nrot; ++k) S->decision_pitch[k] = S->rot[k].r.pitch;
+}
+
+/* ---- complex twins of the geometry (pitch enters through cp, sp) ---- */
+
+static cplx blade_sample_c(const or_rotor* R, cplx p0, cplx p1, cplx p2)
+{
+    double h = R->spacing;
+    cplx g[3] = {(p0 - R->origin[0]) / h, (p1 - R->origin[1]) / h, (p2 - R->origin[2]) / h};
+    double fl[3] = {floor(creal(g[0])), floor(creal(g[1])), floor(creal(g[2]))};
+    if (!(fl[0] >= 0.0 && fl[0] <= R->gx - 2 && fl[1] >= 0.0 && fl[1] <= R->gy - 2 && fl[2] >= 0.0 &&
+          fl[2] <= R->gz - 2))
+        return INFINITY;
+    int i0 = (int)fl[0], j0 = (int)fl[1], k0 = (int)fl[2];
+    cplx t[3] = {g[0] - fl[0], g[1] - fl[1], g[2] - fl[2]};
+    cplx v = 0.0;
+    for (int cz = 0; cz < 2; ++cz)
+        for (int cy = 0; cy < 2; ++cy)
+            for (int cx = 0; cx < 2; ++cx) {
+                cplx wgt = (cx ? t[0] : 1.0 - t[0]) * (cy ? t[1] : 1.0 - t[1]) * (cz ? t[2] : 1.0 - t[2]);
+                size_t o = ((size_t)(k0 + cz) * R->gy + (size_t)(j0 + cy)) * R->gx + (size_t)(i0 + cx);
+                v += wgt * (double)R->sdf[o];
+            }
+    return v;
+}
+
+/* phi of one component in FP64 with pitch frames (cp, sp) */
+static cplx component_phi_c(const or_rotor* R, const blade_frames* B, int which, int ix, int iy, int iz,
+                            cplx cp, cplx sp)
+{
+    int a = R->axis, b = (a + 1) % 3, c = (a + 2) % 3;
+    double rl[3] = {ix - R->center[0], iy - R->center[1], iz - R->center[2]};
+    double rb = rl[b], rc = rl[c], ra = rl[a];
+    if (which >= R->n_blades) return sqrt(rb * rb + rc * rc + ra * ra) - R->hub_radius;
+    double ck = B->ckd[which], sk = B->skd[which];
+    double pR = ck * rb + sk * rc, pT = ck * rc - sk * rb;
+    cplx qT = cp * pT - sp * ra, qA = cp * ra + sp * pT;
+    return blade_sample_c(R, pR, qT, qA);
+}
+
+static cplx porosity_c(cplx phi, double eps, int linear)
+{
+    double pr = creal(phi);
+    if (pr <= -0.5 * eps) return 0.0;
+    if (pr >= 0.5 * eps) return 1.0;
+    cplx t = phi / eps + 0.5;
+    return linear ? t : t * t * (3.0 - 2.0 * t);
+}
+
+/* complex twin of rotor_normal */
+static void rotor_normal_c(const or_rotor* R, const blade_frames* B, int which, int ix, int iy, int iz, cplx cp,
+                           cplx sp, cplx n_out[3])
+{
+    int a = R->axis, b = (a + 1) % 3, c = (a + 2) % 3;
+    double rl[3] = {ix - R->center[0], iy - R->center[1], iz - R->center[2]};
+    cplx v[3];
+    if (which >= R->n_blades) {
+        v[0] = rl[0]; v[1] = rl[1]; v[2] = rl[2];
+    } else {
+        double rb = rl[b], rc = rl[c], ra = rl[a];
+        double ck = B->ckd[which], sk = B->skd[which];
+        double pR = ck * rb + sk * rc, pT = ck * rc - sk * rb;
+        cplx qT = cp * pT - sp * ra, qA = cp * ra + sp * pT;
+        double h = R->spacing;
+        cplx g[3] = {(pR - R->origin[0]) / h, (qT - R->origin[1]) / h, (qA - R->origin[2]) / h};
+        int i0 = (int)floor(creal(g[0])), j0 = (int)floor(creal(g[1])), k0 = (int)floor(creal(g[2]));
+        if (i0 < 0) i0 = 0;
+        if (i0 > R->gx - 2) i0 = R->gx - 2;
+        if (j0 < 0) j0 = 0;
+        if (j0 > R->gy - 2) j0 = R->gy - 2;
+        if (k0 < 0) k0 = 0;
+        if (k0 > R->gz - 2) k0 = R->gz - 2;
+        cplx t[3] = {g[0] - i0, g[1] - j0, g[2] - k0};
+        cplx gb[3] = {0, 0, 0};
+        int dims[3] = {R->gx, R->gy, R->gz};
+        for (int cz = 0; cz < 2; ++cz)
+            for (int cy = 0; cy < 2; ++cy)
+                for (int cx = 0; cx < 2; ++cx) {
+                    int node[3] = {i0 + cx, j0 + cy, k0 + cz};
+                    cplx wgt = (cx ? t[0] : 1.0 - t[0]) * (cy ? t[1] : 1.0 - t[1]) * (cz ? t[2] : 1.0 - t[2]);
+                    for (int d = 0; d < 3; ++d) {
+                        int lo[3] = {node[0], node[1], node[2]}, hi[3] = {node[0], node[1], node[2]};
+                        lo[d] = node[d] > 0 ? node[d] - 1 : node[d];
+                        hi[d] = node[d] < dims[d] - 1 ? node[d] + 1 : node[d];
+                        size_t olo = ((size_t)lo[2] * R->gy + lo[1]) * R->gx + lo[0];
+                        size_t ohi = ((size_t)hi[2] * R->gy + hi[1]) * R->gx + hi[0];
+                        double der = ((double)R->sdf[ohi] - (double)R->sdf[olo]) / ((hi[d] - lo[d]) * h);
+                        gb[d] += wgt * der;
+                    }
+                }
+        cplx vT = cp * gb[1] + sp * gb[2];
+        cplx vA = -sp * gb[1] + cp * gb[2];
+        cplx vR = gb[0];
+        cplx lab[3];
+        lab[b] = ck * vR - sk * vT;
+        lab[c] = sk * vR + ck * vT;
+        lab[a] = vA;
+        v[0] = lab[0]; v[1] = lab[1]; v[2] = lab[2];
+    }
+    cplx nrm = csqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    if (creal(nrm) > 0.0) { n_out[0] = v[0] / nrm; n_out[1] = v[1] / nrm; n_out[2] = v[2] / nrm; }
+    else { n_out[0] = n_out[1] = n_out[2] = 0.0; }
+}
+
+/* ---- complex twin of one wall-model cell ---- */
+
+static cplx spalding_yplus_c(cplx up, double E, double kappa)
+{
+    cplx k = kappa * up;
+    return up + (cexp(k) - 1.0 - k - 0.5 * k * k - k * k * k / 6.0) / E;
+}
+
+/* complex twins of the two Newton solves: the same iterations as
+   wf_newton / spalding_uplus, every branch taken on the real part, so that
+   the imaginary part carries the derivative of the iterate actually
+   returned (a capped, unconverged solve included) */
+static cplx wf_newton_c(cplx u, cplx y, double nu, cplx guess, double E, double kappa, double tol, int maxit)
+{
+    cplx ut = guess;
+    cplx fv = spalding_yplus_c(u / ut, E, kappa) - y * ut / nu;
+    int it = 0;
+    while (it < maxit) {
+        cplx r = u / ut;
+        cplx k = kappa * r;
+        cplx dyp = 1.0 + kappa / E * (cexp(k) - 1.0 - k - 0.5 * k * k);
+        cplx fp = -dyp * u / (ut * ut) - y / nu;
+        cplx un = ut - fv / fp;
+        if (!(creal(un) > 0.0)) un = 0.5 * ut;
+        cplx fn = spalding_yplus_c(u / un, E, kappa) - y * un / nu;
+        ut = un;
+        ++it;
+        if (fabs(creal(fn) - creal(fv)) < tol) break;
+        fv = fn;
+    }
+    return ut;
+}
+
+static cplx spalding_uplus_c(cplx yp, double E, double kappa, double tol, int maxit)
+{
+    cplx lg = clog(1.0 + E * yp) / kappa;
+    cplx up = creal(yp) < creal(lg) ? yp : lg;
+    cplx g = spalding_yplus_c(up, E, kappa) - yp;
+    for (int it = 0; it < maxit; ++it) {
+        cplx k = kappa * up;
+        cplx dyp = 1.0 + kappa / E * (cexp(k) - 1.0 - k - 0.5 * k * k);
+        cplx un = up - g / dyp;
+        if (!(creal(un) > 0.0)) un = 0.5 * up;
+        cplx gn = spalding_yplus_c(un, E, kappa) - yp;
+        up = un;
+        if (fabs(creal(gn) - creal(g)) < tol) break;
+        g = gn;
+    }
+    return up;
+}
+
+/* Outputs du[3], Sm[9] and u_tau of wall cell o at (x, y, z) as functions of
+   the eight trilinear corner velocities uc[8][3], the geometry (n, y1) and
+   the Newton start value (the previous step's u_tau when warm, else the
+   estimate of Eq. (guess)).  Returns 0 for a cell the forward left inactive. */
+static int wall_cell_c(const or_state* S, size_t o, int x, int y, int z, const cplx uc[8][3], const cplx n[3],
+                       cplx y1, int warm, cplx guess_prev, cplx du[3], cplx Sm[9], cplx* utau_out)
+{
+    const or_params* P = &S->P;
+    double nu = (P->tau_mo - 0.5) * CS2;
+    int dims[3] = {P->nx, P->ny, P->nz};
+    for (int k = 0; k < 3; ++k) du[k] = 0.0;
+    for (int k = 0; k < 9; ++k) Sm[k] = 0.0;
+    *utau_out = 0.0;
+    if (!S->wm_active[o]) return 0;
+    int xi[3] = {x, y, z};
+    cplx t[3];
+    for (int k = 0; k < 3; ++k) {
+        cplx xs = xi[k] + P->wm_ysample * n[k];
+        double fl = floor(creal(xs));
+        int i0 = (int)fl;
+        t[k] = xs - fl;
+        if (P->open_boundaries && k == P->flow_axis) {
+            if (i0 < 0) t[k] = 0.0;
+            if (i0 > dims[k] - 2) t[k] = 1.0;
+        }
+    }
+    cplx us_[3] = {0, 0, 0};
+    for (int cz = 0; cz < 2; ++cz)
+        for (int cy = 0; cy < 2; ++cy)
+            for (int cx = 0; cx < 2; ++cx) {
+                cplx wgt = (cx ? t[0] : 1.0 - t[0]) * (cy ? t[1] : 1.0 - t[1]) * (cz ? t[2] : 1.0 - t[2]);
+                int m = (cz * 2 + cy) * 2 + cx;
+                for (int k = 0; k < 3; ++k) us_[k] += wgt * uc[m][k];
+            }
+    double usol[3];
+    solid_velocity(&S->rot[S->tag[o]].r, x, y, z, usol);
+    cplx ur[3] = {us_[0] - usol[0], us_[1] - usol[1], us_[2] - usol[2]};
+    cplx un = ur[0] * n[0] + ur[1] * n[1] + ur[2] * n[2];
+    cplx ut[3] = {ur[0] - un * n[0], ur[1] - un * n[1], ur[2] - un * n[2]};
+    cplx utm = csqrt(ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2]);
+    cplx th[3] = {ut[0] / utm, ut[1] / utm, ut[2] / utm};
+    cplx ysamp = y1 + P->wm_ysample;
+    cplx guess = warm ? guess_prev : csqrt(nu * utm / P->wm_ysample);
+    cplx utau = wf_newton_c(utm, ysamp, nu, guess, P->wm_E, P->wm_kappa, P->wm_tol, P->wm_maxit);
+    cplx y1p = y1 * utau / nu;
+    cplx up = spalding_uplus_c(y1p, P->wm_E, P->wm_kappa, P->wm_tol, P->wm_maxit);
+    cplx uwall = utau * up;
+    for (int k = 0; k < 3; ++k) du[k] = uwall * th[k];
+    cplx g = (utm - uwall) / P->wm_ysample;
+    for (int p = 0; p < 3; ++p)
+        for (int q = 0; q < 3; ++q) Sm[3 * p + q] = 0.5 * g * (th[p] * n[q] + n[p] * th[q]);
+    *utau_out = utau;
+    return 1;
+}
+
+/* corner cells of the wall-model sample of cell o (same clamping and
+   wrapping as wall_model); returns the real trilinear setup in idx[8] */
+static void wall_corners(const or_state* S, size_t o, int x, int y, int z, size_t idx[8])
+{
+    const or_params* P = &S->P;
+    int dims[3] = {P->nx, P->ny, P->nz};
+    const double* n = S->nrm + 3 * o;
+    double xs[3] = {x + P->wm_ysample * n[0], y + P->wm_ysample * n[1], z + P->wm_ysample * n[2]};
+    int i0[3];
+    for (int k = 0; k < 3; ++k) {
+        i0[k] = (int)floor(xs[k]);
+        if (P->open_boundaries && k == P->flow_axis) {
+            if (i0[k] < 0) i0[k] = 0;
+            if (i0[k] > dims[k] - 2) i0[k] = dims[k] - 2;
+        }
+    }
+    for (int cz = 0; cz < 2; ++cz)
+        for (int cy = 0; cy < 2; ++cy)
+            for (int cx = 0; cx < 2; ++cx) {
+                int p[3] = {i0[0] + cx, i0[1] + cy, i0[2] + cz};
+                for (int k = 0; k < 3; ++k)
+                    if (!(P->open_boundaries && k == P->flow_axis)) p[k] = wrap(p[k], dims[k]);
+                idx[(cz * 2 + cy) * 2 + cx] = cidx(S, p[0], p[1], p[2]);
+            }
+}
+
+/* ---- the reverse sweep ---- */
+
+typedef struct {
+    double* f;          /* [T][q][N] pre-collision populations at the start of each step */
+    double* wm_ut;      /* [T][N] */
+    unsigned char* wm_active; /* [T][N] */
+    double* uplane;     /* [T][2][3 npl] */
+} or_tape;
+
+/* J = (1/n_avg) sum_{t = T - n_avg}^{T-1} sum_k [ wT_k F_k(t).a_k + wQ_k M_k(t).a_k ]
+   over the next T steps from the current state, and its gradient with
+   respect to every rotor's pitch (dJdp[nrot]) and the static porosity
+   multiplier (dJdd0[N]), cell sets frozen at their forward values (the
+   reading for the non-smooth points of the step).  On return the state has
+   advanced T steps, exactly as or_step(S, T).  The trajectory is kept in
+   host memory: T (q + 1) N doubles. */
+int or_adjoint(or_state* S, int T, int n_avg, const double* wT, const double* wQ, double* J_out, double* dJdp,
+               double* dJdd0)
+{
+    const or_params* P = &S->P;
+    const or_lattice* L = &S->L;
+    const int q = L->q;
+    const size_t N = S->N;
+    int dims[3] = {P->nx, P->ny, P->nz};
+    const int ax = P->flow_axis, bx = (ax + 1) % 3, cxx = (ax + 2) % 3;
+    const size_t npl = (size_t)dims[bx] * dims[cxx];
+    if (T < 1 || n_avg < 1 || n_avg > T) return -1;
+    or_tape tp;
+    tp.f = (double*)malloc(sizeof(double) * (size_t)T * q * N);
+    tp.wm_ut = (double*)malloc(sizeof(double) * (size_t)T * N);
+    tp.wm_active = (unsigned char*)malloc((size_t)T * N);
+    tp.uplane = (double*)malloc(sizeof(double) * (size_t)T * 6 * npl);
+    double* lam = (double*)calloc((size_t)q * N, sizeof(double));
+    double* lam_star = (double*)malloc(sizeof(double) * (size_t)q * N);
+    double* lam_new = (double*)malloc(sizeof(double) * (size_t)q * N);
+    double* g_up_cur = (double*)calloc(3 * npl, sizeof(double));   /* dJ/d uplane written in this step */
+    double* g_up_prev = (double*)calloc(3 * npl, sizeof(double));  /* dJ/d uplane read in this step */
+    double* g_uB = (double*)malloc(sizeof(double) * 3 * N);
+    double* g_S = (double*)malloc(sizeof(double) * 9 * N);
+    double* gp_cell = (double*)malloc(sizeof(double) * N);
+    double* wm_ubar = (double*)malloc(sizeof(double) * 24 * N);
+    double* wm_pbar = (double*)malloc(sizeof(double) * N);
+    double* g_ut_cur = (double*)calloc(N, sizeof(double));   /* dJ/d u_tau of this step (next step's start) */
+    double* g_ut_prev = (double*)calloc(N, sizeof(double));  /* dJ/d u_tau of the previous step */
+    if (!tp.f || !tp.wm_ut || !tp.wm_active || !tp.uplane || !lam || !lam_star || !lam_new || !g_up_cur ||
+        !g_up_prev || !g_uB || !g_S || !gp_cell || !wm_ubar || !wm_pbar || !g_ut_cur || !g_ut_prev) {
+        free(tp.f); free(tp.wm_ut); free(tp.wm_active); free(tp.uplane); free(lam); free(lam_star);
+        free(lam_new); free(g_up_cur); free(g_up_prev); free(g_uB); free(g_S); free(gp_cell); free(wm_ubar);
+        free(wm_pbar); free(g_ut_cur); free(g_ut_prev);
+        return -2;
+    }
+    const long t0 = S->step;
+    /* forward, recording the state each step starts from */
+    double J = 0.0;
+    for (int s = 0; s < T; ++s) {
+        memcpy(tp.f + (size_t)s * q * N, S->f, sizeof(double) * q * N);
+        memcpy(tp.wm_ut + (size_t)s * N, S->wm_ut, sizeof(double) * N);
+        memcpy(tp.wm_active + (size_t)s * N, S->wm_active, N);
+        memcpy(tp.uplane + (size_t)s * 6 * npl, S->uplane[0], sizeof(double) * 3 * npl);
+        memcpy(tp.uplane + (size_t)s * 6 * npl + 3 * npl, S->uplane[1], sizeof(double) * 3 * npl);
+        or_step(S, 1);
+        if (s >= T - n_avg)
+            for (int k = 0; k < S->nrot; ++k) {
+                int a = S->rot[k].r.axis;
+                J += (wT[k] * S->F[k][a] + wQ[k] * S->M[k][a]) / n_avg;
+            }
+    }
+    /* keep the final forward state to put back at the end */
+    double* f_end = (double*)malloc(sizeof(double) * q * N);
+    double* ut_end = (double*)malloc(sizeof(double) * N);
+    unsigned char* act_end = (unsigned char*)malloc(N);
+    double* up_end = (double*)malloc(sizeof(double) * 6 * npl);
+    memcpy(f_end, S->f, sizeof(double) * q * N);
+    memcpy(ut_end, S->wm_ut, sizeof(double) * N);
+    memcpy(act_end, S->wm_active, N);
+    memcpy(up_end, S->uplane[0], sizeof(double) * 3 * npl);
+    memcpy(up_end + 3 * npl, S->uplane[1], sizeof(double) * 3 * npl);
+    double Fk[OR_MAXROT][3], Mk[OR_MAXROT][3];
+    memcpy(Fk, S->F, sizeof Fk);
+    memcpy(Mk, S->M, sizeof Mk);
+    long it_end = S->wm_newton_iters, ev_end = S->wm_evals, step_end = S->step;
+
+    for (int k = 0; k < S->nrot; ++k) dJdp[k] = 0.0;
+    for (size_t x = 0; x < N; ++x) dJdd0[x] = 0.0;
+
+    for (int s = T - 1; s >= 0; --s) {
+        /* recompute the forward quantities of step s */
+        memcpy(S->f, tp.f + (size_t)s * q * N, sizeof(double) * q * N);
+        memcpy(S->wm_ut, tp.wm_ut + (size_t)s * N, sizeof(double) * N);
+        memcpy(S->wm_active, tp.wm_active + (size_t)s * N, N);
+        memcpy(S->uplane[0], tp.uplane + (size_t)s * 6 * npl, sizeof(double) * 3 * npl);
+        memcpy(S->uplane[1], tp.uplane + (size_t)s * 6 * npl + 3 * npl, sizeof(double) * 3 * npl);
+        S->step = t0 + s;
+        update_porosity(S);
+        wall_model(S);
+
+        /* adjoint of streaming: transpose of stream_all */
+        for (size_t m = 0; m < (size_t)q * N; ++m) lam_star[m] = 0.0;
+        for (int z = 0; z < P->nz; ++z)
+            for (int y = 0; y < P->ny; ++y)
+                for (int x = 0; x < P->nx; ++x) {
+                    size_t o = cidx(S, x, y, z);
+                    int xi[3] = {x, y, z};
+                    for (int i = 0; i < q; ++i) {
+                        int nb[3];
+                        size_t src = o;
+                        if (neighbour(S, xi, L->c[i], -1, nb)) src = cidx(S, nb[0], nb[1], nb[2]);
+                        lam_star[(size_t)i * N + src] += lam[(size_t)i * N + o];
+                    }
+                }
+        /* adjoint of the force: transpose of boundary_force, weighted */
+        if (s >= T - n_avg)
+            for (int z = 0; z < P->nz; ++z)
+                for (int y = 0; y < P->ny; ++y)
+                    for (int x = 0; x < P->nx; ++x) {
+                        size_t o = cidx(S, x, y, z);
+                        if (!(S->flags[o] & FL_B)) continue;
+                        const or_rotor* R = &S->rot[S->tag[o]].r;
+                        int k = S->tag[o], a = R->axis;
+                        double us[3];
+                        solid_velocity(R, x, y, z, us);
+                        double r[3] = {x - R->center[0], y - R->center[1], z - R->center[2]};
+                        /* J per step = wT F_a + wQ (r x F)_a = F . v,  v = wT e_a + wQ (e_a x r) */
+                        double ea[3] = {0, 0, 0};
+                        ea[a] = 1.0;
+                        double v[3] = {wT[k] * ea[0] + wQ[k] * (ea[1] * r[2] - ea[2] * r[1]),
+                                       wT[k] * ea[1] + wQ[k] * (ea[2] * r[0] - ea[0] * r[2]),
+                                       wT[k] * ea[2] + wQ[k] * (ea[0] * r[1] - ea[1] * r[0])};
+                        for (int m = 0; m < 3; ++m) v[m] /= n_avg;
+                        int xi[3] = {x, y, z};
+                        for (int i = 1; i < q; ++i) {
+                            int nb[3];
+                            if (!neighbour(S, xi, L->c[i], +1, nb)) continue;
+                            size_t on = cidx(S, nb[0], nb[1], nb[2]);
+                            int ib = L->opp[i];
+                            double cib = 0.0, ci = 0.0, cip = 0.0;
+                            for (int m = 0; m < 3; ++m) {
+                                cib += (L->c[ib][m] - us[m]) * v[m];
+                                ci += (L->c[i][m] - us[m]) * v[m];
+                                cip += (L->c[i][m] + us[m]) * v[m];
+                            }
+                            if (P->force_form == 0) {
+                                lam_star[(size_t)ib * N + on] += cib;
+                                lam_star[(size_t)i * N + o] -= ci;
+                            } else {
+                                lam_star[(size_t)i * N + on] += ci;
+                                lam_star[(size_t)i * N + o] += cip;
+                            }
+                        }
+                    }
+
+        /* adjoint of the collision, cell by cell */
+        for (size_t m = 0; m < 3 * npl; ++m) g_up_prev[m] = 0.0;
+        #pragma omp parallel for schedule(static)
+        for (int z = 0; z < P->nz; ++z)
+            for (int y = 0; y < P->ny; ++y)
+                for (int x = 0; x < P->nx; ++x) {
+                    size_t o = cidx(S, x, y, z);
+                    int xi[3] = {x, y, z};
+                    size_t pl = (size_t)xi[cxx] * dims[bx] + xi[bx];
+                    double ls[OR_MAXQ], lf[OR_MAXQ];
+                    for (int i = 0; i < q; ++i) ls[i] = lam_star[(size_t)i * N + o];
+                    gp_cell[o] = 0.0;
+                    for (int k = 0; k < 3; ++k) g_uB[3 * o + k] = 0.0;
+                    for (int k = 0; k < 9; ++k) g_S[9 * o + k] = 0.0;
+                    for (int i = 0; i < q; ++i) lf[i] = 0.0;
+                    if (P->open_boundaries && xi[ax] == 0) {
+                        /* inlet: f* = f^eq(1, u_in(t)) does not depend on the state */
+                    } else if (P->open_boundaries && xi[ax] == dims[ax] - 1) {
+                        /* outlet: f* = f^eq(1, u_plane), u_plane from the previous step */
+                        int prev = (int)((S->step & 1) ^ 1);
+                        const double* u0 = S->uplane[prev] + 3 * pl;
+                        for (int k = 0; k < 3; ++k) {
+                            cplx uc[3] = {u0[0], u0[1], u0[2]}, fe[OR_MAXQ];
+                            uc[k] += I * CSTEP;
+                            equilibrium_c(L, 1.0, uc, fe);
+                            double sacc = 0.0;
+                            for (int i = 0; i < q; ++i) sacc += ls[i] * cimag(fe[i]) / CSTEP;
+                            g_up_prev[3 * pl + k] = sacc;
+                        }
+                    } else {
+                        double fin[OR_MAXQ];
+                        for (int i = 0; i < q; ++i) fin[i] = S->f[(size_t)i * N + o];
+                        cell_band B;
+                        band_of_cell(S, o, x, y, z, &B);
+                        double gd, gu[3], gS[3][3];
+                        collide_vjp(L, fin, &B, P->tau_mo, P->c_smag, ls, lf, &gd, gu, gS);
+                        const double d0 = S->d0 ? S->d0[o] : 1.0;
+                        if (S->flags[o] & FL_B) {
+                            /* d = d0 d_rotor(pitch); u^B = u_s + du_WM */
+                            dJdd0[o] += gd * S->d[o];
+                            const or_rotor* R = &S->rot[S->tag[o]].r;
+                            blade_frames BF;
+                            blade_frames_at(R, S->step, &BF);
+                            cplx pc = R->pitch + I * CSTEP;
+                            cplx val = component_phi_c(R, &BF, S->which[o], x, y, z, ccos(pc), csin(pc));
+                            double ddp = cimag(porosity_c(val, P->eps_h, P->transition)) / CSTEP;
+                            gp_cell[o] = gd * d0 * ddp;
+                            for (int k = 0; k < 3; ++k) g_uB[3 * o + k] = gu[k];
+                            for (int p = 0; p < 3; ++p)
+                                for (int r = 0; r < 3; ++r) g_S[9 * o + 3 * p + r] = gS[p][r];
+                        } else {
+                            dJdd0[o] += gd;
+                        }
+                        if (P->open_boundaries && xi[ax] == dims[ax] - 2) {
+                            /* u of this cell became the outlet's u_plane for the next step */
+                            double rho = 0.0, jm[3] = {0, 0, 0};
+                            for (int i = 0; i < q; ++i) {
+                                rho += fin[i];
+                                for (int k = 0; k < 3; ++k) jm[k] += L->c[i][k] * fin[i];
+                            }
+                            const double* gu_pl = g_up_cur + 3 * pl;
+                            for (int i = 0; i < q; ++i)
+                                for (int k = 0; k < 3; ++k)
+                                    lf[i] += gu_pl[k] * (L->c[i][k] - jm[k] / rho) / rho;
+                        }
+                    }
+                    for (int i = 0; i < q; ++i) lam_new[(size_t)i * N + o] = lf[i];
+                }
+
+        /* adjoint of the wall model: corner velocities and pitch */
+        if (P->wall_model) {
+            #pragma omp parallel for schedule(dynamic, 64)
+            for (int z = 0; z < P->nz; ++z)
+                for (int y = 0; y < P->ny; ++y)
+                    for (int x = 0; x < P->nx; ++x) {
+                        size_t o = cidx(S, x, y, z);
+                        for (int m = 0; m < 24; ++m) wm_ubar[24 * o + m] = 0.0;
+                        wm_pbar[o] = 0.0;
+                        g_ut_prev[o] = 0.0;
+                        if (!((S->flags[o] & FL_W) && S->wm_active[o])) continue;
+                        size_t idx[8];
+                        wall_corners(S, o, x, y, z, idx);
+                        double ucr[8][3];
+                        for (int m = 0; m < 8; ++m) cell_velocity(S, idx[m], ucr[m], NULL);
+                        const or_rotor* R = &S->rot[S->tag[o]].r;
+                        blade_frames BF;
+                        blade_frames_at(R, S->step, &BF);
+                        const double* nr = S->nrm + 3 * o;
+                        const double* y1v = S->y1 + 3 * o;
+                        double y1r = sqrt(y1v[0] * y1v[0] + y1v[1] * y1v[1] + y1v[2] * y1v[2]);
+                        double gout[13];
+                        for (int k = 0; k < 3; ++k) gout[k] = g_uB[3 * o + k];
+                        for (int k = 0; k < 9; ++k) gout[3 + k] = g_S[9 * o + k];
+                        gout[12] = g_ut_cur[o];     /* u_tau is the next step's Newton start */
+                        const int warm = tp.wm_active[(size_t)s * N + o];
+                        const double guess_prev = tp.wm_ut[(size_t)s * N + o];
+                        /* 24 corner-velocity directions, the pitch, the Newton start */
+                        for (int dir = 0; dir < 26; ++dir) {
+                            if (dir == 25 && !warm) break;
+                            cplx uc[8][3], n[3], y1 = y1r, du[3], Sm[9], ut_out, gs = guess_prev;
+                            for (int m = 0; m < 8; ++m)
+                                for (int k = 0; k < 3; ++k) uc[m][k] = ucr[m][k];
+                            for (int k = 0; k < 3; ++k) n[k] = nr[k];
+                            if (dir < 24) {
+                                uc[dir / 3][dir % 3] += I * CSTEP;
+                            } else if (dir == 25) {
+                                gs += I * CSTEP;
+                            } else {
+                                cplx pc = R->pitch + I * CSTEP, cp = ccos(pc), sp = csin(pc);
+                                cplx nc[3];
+                                rotor_normal_c(R, &BF, S->which[o], x, y, z, cp, sp, nc);
+                                for (int k = 0; k < 3; ++k) n[k] = nr[k] + I * cimag(nc[k]);
+                                cplx val = component_phi_c(R, &BF, S->which[o], x, y, z, cp, sp);
+                                /* y1 = max(phi, 1/2): the forward's branch, on its binary32 phi */
+                                float vf = component_phi_f32(R, &BF, S->which[o], x, y, z);
+                                if ((double)vf > 0.5) y1 = y1r + I * cimag(val);
+                            }
+                            wall_cell_c(S, o, x, y, z, (const cplx(*)[3])uc, n, y1, warm, gs, du, Sm, &ut_out);
+                            double acc = 0.0;
+                            for (int k = 0; k < 3; ++k) acc += gout[k] * cimag(du[k]) / CSTEP;
+                            for (int k = 0; k < 9; ++k) acc += gout[3 + k] * cimag(Sm[k]) / CSTEP;
+                            acc += gout[12] * cimag(ut_out) / CSTEP;
+                            if (dir < 24) wm_ubar[24 * o + dir] = acc;
+                            else if (dir == 24) wm_pbar[o] = acc;
+                            else g_ut_prev[o] = acc;
+                        }
+                    }
+            /* scatter into the corner cells' populations: du/df_i = (c_i - u) / rho */
+            for (int z = 0; z < P->nz; ++z)
+                for (int y = 0; y < P->ny; ++y)
+                    for (int x = 0; x < P->nx; ++x) {
+                        size_t o = cidx(S, x, y, z);
+                        if (!((S->flags[o] & FL_W) && S->wm_active[o])) continue;
+                        size_t idx[8];
+                        wall_corners(S, o, x, y, z, idx);
+                        for (int m = 0; m < 8; ++m) {
+                            double u[3], rho;
+                            cell_velocity(S, idx[m], u, &rho);
+                            for (int i = 0; i < q; ++i) {
+                                double acc = 0.0;
+                                for (int k = 0; k < 3; ++k) acc += wm_ubar[24 * o + 3 * m + k] * (L->c[i][k] - u[k]);
+                                lam_new[(size_t)i * N + idx[m]] += acc / rho;
+                            }
+                        }
+                        dJdp[S->tag[o]] += wm_pbar[o];
+                    }
+        }
+        for (int z = 0; z < P->nz; ++z)
+            for (int y = 0; y < P->ny; ++y)
+                for (int x = 0; x < P->nx; ++x) {
+                    size_t o = cidx(S, x, y, z);
+                    if (S->flags[o] & FL_B) dJdp[S->tag[o]] += gp_cell[o];
+                }
+        double* tswap = lam; lam = lam_new; lam_new = tswap;
+        tswap = g_up_cur; g_up_cur = g_up_prev; g_up_prev = tswap;
+        tswap = g_ut_cur; g_ut_cur = g_ut_prev; g_ut_prev = tswap;
+        if (!P->wall_model)
+            for (size_t m = 0; m < N; ++m) g_ut_cur[m] = 0.0;
+    }
+
+    /* put back the final forward state */
+    memcpy(S->f, f_end, sizeof(double) * q * N);
+    memcpy(S->wm_ut, ut_end, sizeof(double) * N);
+    memcpy(S->wm_active, act_end, N);
+    memcpy(S->uplane[0], up_end, sizeof(double) * 3 * npl);
+    memcpy(S->uplane[1], up_end + 3 * npl, sizeof(double) * 3 * npl);
+    memcpy(S->F, Fk, sizeof Fk);
+    memcpy(S->M, Mk, sizeof Mk);
+    S->wm_newton_iters = it_end;
+    S->wm_evals = ev_end;
+    /* geometry arrays as or_step leaves them: those of the last step taken */
+    S->step = step_end - 1;
+    update_porosity(S);
+    S->step = step_end;
+    *J_out = J;
+    free(f_end); free(ut_end); free(act_end); free(up_end);
+    free(tp.f); free(tp.wm_ut); free(tp.wm_active); free(tp.uplane); free(lam); free(lam_star); free(lam_new);
+    free(g_up_cur); free(g_up_prev); free(g_uB); free(g_S); free(gp_cell); free(wm_ubar); free(wm_pbar);
+    free(g_ut_cur); free(g_ut_prev);
+    return 0;
+}
+
+/* d(d_rotor)/d(pitch) of every force-set cell for the geometry of the last
+   porosity update (complex step, component and sets frozen), 0 elsewhere. */
+void or_porosity_tangent(const or_state* S, double* dd)
+{
+    const or_params* P = &S->P;
+    long t = S->step > 0 ? S->step - 1 : 0;
+    for (int z = 0; z < P->nz; ++z)
+        for (int y = 0; y < P->ny; ++y)
+            for (int x = 0; x < P->nx; ++x) {
+                size_t o = cidx(S, x, y, z);
+                dd[o] = 0.0;
+                if (!(S->flags[o] & FL_B)) continue;
+                const or_rotor* R = &S->rot[S->tag[o]].r;
+                blade_frames BF;
+                blade_frames_at(R, t, &BF);
+                cplx pc = R->pitch + I * CSTEP;
+                cplx val = component_phi_c(R, &BF, S->which[o], x, y, z, ccos(pc), csin(pc));
+                dd[o] = cimag(porosity_c(val, P->eps_h, P->transition)) / CSTEP;
+            }
+}
+
+/* Tangents d(du_WM)/d(pitch) [N][3] and d(S_WM)/d(pitch) [N][9] of the wall
+   model at the current step (porosity update and wall model are run first,
+   as at the start of or_step, without advancing the state). */
+void or_wall_tangent(or_state* S, double* ddu, double* dSm)
+{
+    const or_params* P = &S->P;
+    double* guess = (double*)malloc(sizeof(double) * S->N);
+    unsigned char* warm = (unsigned char*)malloc(S->N);
+    memcpy(guess, S->wm_ut, sizeof(double) * S->N);
+    memcpy(warm, S->wm_active, S->N);
+    update_porosity(S);
+    wall_model(S);
+    for (int z = 0; z < P->nz; ++z)
+        for (int y = 0; y < P->ny; ++y)
+            for (int x = 0; x < P->nx; ++x) {
+                size_t o = cidx(S, x, y, z);
+                for (int k = 0; k < 3; ++k) ddu[3 * o + k] = 0.0;
+                for (int k = 0; k < 9; ++k) dSm[9 * o + k] = 0.0;
+                if (!(P->wall_model && (S->flags[o] & FL_W) && S->wm_active[o])) continue;
+                size_t idx[8];
+                wall_corners(S, o, x, y, z, idx);
+                cplx uc[8][3];
+                for (int m = 0; m < 8; ++m) {
+                    double u[3];
+                    cell_velocity(S, idx[m], u, NULL);
+                    for (int k = 0; k < 3; ++k) uc[m][k] = u[k];
+                }
+                const or_rotor* R = &S->rot[S->tag[o]].r;
+                blade_frames BF;
+                blade_frames_at(R, S->step, &BF);
+                const double* y1v = S->y1 + 3 * o;
+                double y1r = sqrt(y1v[0] * y1v[0] + y1v[1] * y1v[1] + y1v[2] * y1v[2]);
+                cplx pc = R->pitch + I * CSTEP, cp = ccos(pc), sp = csin(pc);
+                cplx nc[3], n[3], y1 = y1r, du[3], Sm[9];
+                rotor_normal_c(R, &BF, S->which[o], x, y, z, cp, sp, nc);
+                for (int k = 0; k < 3; ++k) n[k] = S->nrm[3 * o + k] + I * cimag(nc[k]);
+                cplx val = component_phi_c(R, &BF, S->which[o], x, y, z, cp, sp);
+                float vf = component_phi_f32(R, &BF, S->which[o], x, y, z);
+                if ((double)vf > 0.5) y1 = y1r + I * cimag(val);
+                cplx ut_out;
+                wall_cell_c(S, o, x, y, z, (const cplx(*)[3])uc, n, y1, warm[o], guess[o], du, Sm, &ut_out);
+                for (int k = 0; k < 3; ++k) ddu[3 * o + k] = cimag(du[k]) / CSTEP;
+                for (int k = 0; k < 9; ++k) dSm[9 * o + k] = cimag(Sm[k]) / CSTEP;
+            }
+    free(guess);
+    free(warm);
+}
+
+/* d n / d(pitch) of component `which` of rotor R at cell (x, y, z), time t */
+void or_rotor_normal_tangent(const or_rotor* R, long t, int which, int x, int y, int z, double* dn)
+{
+    blade_frames BF;
+    blade_frames_at(R, t, &BF);
+    cplx pc = R->pitch + I * CSTEP, nc[3];
+    rotor_normal_c(R, &BF, which, x, y, z, ccos(pc), csin(pc), nc);
+    for (int k = 0; k < 3; ++k) dn[k] = cimag(nc[k]) / CSTEP;
+}
