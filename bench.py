@@ -183,7 +183,10 @@ def run_reference(args):
 # --------------------------------------------------------------------------
 # DRAM traffic of one collide-and-stream launch of this workload from an ncu
 # capture, valid for the kernel source of the given hash (else reported null)
-NCU_TRAFFIC = {"source_sha": None, "bytes_per_launch": None}
+# DRAM bytes (read + write) of one bulk collide launch of the rotor256 step, from
+# one ncu capture (profiles/collide_kernel_rotor256_traffic.md); reported only
+# while the kernel sources hash to the value they had at the capture
+NCU_TRAFFIC = {"source_sha": "7f793fe47aee770f", "bytes_per_launch": 4853713408}
 
 
 def kernel_source_sha():
