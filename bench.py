@@ -264,7 +264,9 @@ def run_cuda(args):
     achieved = alg_bytes / per_launch_s / 1e9
     peak, peak_src = measured_peaks()
     sha = kernel_source_sha()
-    traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["source_sha"] == sha else None
+    traffic = (NCU_TRAFFIC["bytes_per_launch"]
+               if NCU_TRAFFIC["source_sha"] == sha and args.workload == "rotor256" and args.storage == "f32"
+               else None)
     total_kernel_ms = sum(v[0] for v in prof.values())
     kernels = {k: {"launches": n, "ms_per_launch": round(ms / n, 4) if n else None,
                    "share": round(ms / total_kernel_ms, 4) if total_kernel_ms else None}
