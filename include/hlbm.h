@@ -214,6 +214,61 @@ hl_status hl_debug_collide(int q, int n, const float* d_g_in, const float* d_d, 
                            const float* d_sigma, const float* d_S, double tau_mo, double c_smag,
                            float* d_g_out, void* stream);
 
+/* ---- gradients (discrete adjoint of the step) ----
+ *
+ * Objective over the next `steps` steps from the current state:
+ *   J = (1/avg_last) sum over the last avg_last steps of
+ *       sum_k [ w_thrust[k] F_k . a_k + w_torque[k] M_k . a_k ]
+ * (F, M: the momentum-exchange force and torque of Sec. 2.2.2, a_k the rotor
+ * axis).  Its gradient is taken with respect to each rotor's pitch and to a
+ * static porosity multiplier d0 (d = d0 d_rotor in Eq. (convexVelocity),
+ * d0 = 1 unless set by hl_set_d0), with the step's cell sets (force cells,
+ * wall cells, closest blade) held at their forward values; the wall-model
+ * Newton solves are differentiated through the iterations they took. */
+
+/* Static porosity multiplier d0[N] (device FP32, caller-owned, read by every
+ * later step while set; NULL restores d0 = 1).  Cells outside the rotors'
+ * force sets then relax towards rest with weight 1 - d0. */
+hl_status hl_set_d0(hl_lattice* lat, const float* d_d0);
+
+/* Change the pitch of rotor `rotor` (rad) for the following steps. */
+hl_status hl_set_pitch(hl_lattice* lat, int rotor, double pitch);
+
+/* on != 0: from now on the cell sets follow the pitches the rotors have at
+ * this call while porosity, normals and wall distances follow later
+ * hl_set_pitch calls (finite-difference checks of the pitch gradient with
+ * the sets frozen, as the gradient has them); on = 0: both follow the pitch. */
+hl_status hl_freeze_sets(hl_lattice* lat, int on);
+
+/* Bytes of device workspace hl_grad needs: (ceil(steps / ckpt_every) + 1)
+ * state checkpoints, ckpt_every - 1 population buffers of a recomputed
+ * segment, two adjoint population arrays and small per-rotor arrays. */
+hl_status hl_grad_workspace_size(const hl_lattice* lat, int steps, int ckpt_every, size_t* bytes);
+
+/* Run `steps` steps (the lattice ends exactly where hl_step(lat, steps)
+ * leaves it, force averages included) and return J (host double, may be
+ * NULL), dJ/dpitch[n_rotors] (host double, may be NULL) and dJ/dd0 (device
+ * float [N], overwritten; may be NULL).  w_thrust, w_torque: host
+ * [n_rotors]; 1 <= avg_last <= steps; ckpt_every >= 1 sets the checkpoint
+ * spacing (memory vs. one recomputed forward step per step).  d_work:
+ * caller's device workspace of hl_grad_workspace_size bytes, 256-byte
+ * aligned, overwritten.  Synchronises; HL_ERR_NONFINITE / HL_ERR_MASS as
+ * hl_step. */
+hl_status hl_grad(hl_lattice* lat, int steps, int avg_last, int ckpt_every, const double* w_thrust,
+                  const double* w_torque, double* J, double* dJ_dpitch, float* d_dJ_dd0, void* d_work,
+                  size_t bytes);
+
+/* Vector-Jacobian product of the collision of n independent cells (unit
+ * checks): arguments as hl_debug_collide, plus d_lam_star[n][q] (adjoint of
+ * the post-collision populations) -> d_lam[n][q] (adjoint of the
+ * pre-collision populations) and, for the homogenized branch, the adjoint
+ * of the band data d_gd[n], d_guB[n][3], d_gS[n][6] (each may be NULL).
+ * Runs on `stream`; does not synchronise. */
+hl_status hl_debug_collide_vjp(int q, int n, const float* d_g_in, const float* d_d, const float* d_uB,
+                               const float* d_sigma, const float* d_S, double tau_mo, double c_smag,
+                               const float* d_lam_star, float* d_lam, float* d_gd, float* d_guB, float* d_gS,
+                               void* stream);
+
 /* Per-kernel timing with CUDA events recorded on the lattice's stream around
  * each launch of the time loop.  hl_profile_begin(lat, capacity) starts
  * recording (at most `capacity` launches per kernel kind; it creates CUDA

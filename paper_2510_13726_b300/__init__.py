@@ -8,5 +8,6 @@ no CPU fallback: loading fails loudly when the CUDA library is missing.
 
 from ._lib import HlConfig, HlRotorGeometry, HlError, lib, velocity_set
 from .lattice import Lattice
+from .objective import rotor_objective
 
-__all__ = ["HlConfig", "HlRotorGeometry", "HlError", "lib", "velocity_set", "Lattice"]
+__all__ = ["HlConfig", "HlRotorGeometry", "HlError", "lib", "velocity_set", "Lattice", "rotor_objective"]

@@ -74,6 +74,13 @@ SIGNATURES = {
     "hl_velocity_set": (C.c_int, [C.c_int, _ip, _dp]),
     "hl_debug_collide": (C.c_int, [C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, C.c_double, C.c_double,
                                    _vp, _vp]),
+    "hl_set_d0": (C.c_int, [_vp, _vp]),
+    "hl_set_pitch": (C.c_int, [_vp, C.c_int, C.c_double]),
+    "hl_freeze_sets": (C.c_int, [_vp, C.c_int]),
+    "hl_grad_workspace_size": (C.c_int, [_vp, C.c_int, C.c_int, C.POINTER(C.c_size_t)]),
+    "hl_grad": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, _dp, _dp, _dp, _dp, _vp, _vp, C.c_size_t]),
+    "hl_debug_collide_vjp": (C.c_int, [C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, C.c_double, C.c_double,
+                                       _vp, _vp, _vp, _vp, _vp, _vp]),
     "hl_profile_begin": (C.c_int, [_vp, C.c_int]),
     "hl_profile_end": (C.c_int, [_vp, _dp, C.POINTER(C.c_longlong)]),
     "hl_mass_noalloc": (C.c_int, [C.c_int, C.c_int, _vp, C.c_longlong, _vp, _vp]),

@@ -5,106 +5,13 @@
 #include <new>
 #include <vector>
 
-#include "hl_internal.h"
-#include "hlbm.h"
+#include "hl_host.h"
 
 using namespace hl;
+using namespace hl::host;
 
-namespace {
-
-constexpr size_t ALIGN = 256;
-
-size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
-
-struct Layout {
-    size_t f, uplane0, uplane1, modes, err, mpartial, mdone, mout, total;
-};
-
-int store_bytes(int storage) { return storage == HL_STORE_F32 ? 4 : 2; }
-
-long long plane_cells(const hl_config& c) {
-    const int n[3] = {c.nx, c.ny, c.nz};
-    return (long long)n[(c.flow_axis + 1) % 3] * n[(c.flow_axis + 2) % 3];
-}
-
-Layout lattice_layout(const hl_config& c) {
-    Layout L{};
-    const long long N = (long long)c.nx * c.ny * c.nz;
-    size_t o = 0;
-    L.f = o; o = align_up(o + (size_t)c.q * N * store_bytes(c.storage));
-    L.uplane0 = o; o = align_up(o + sizeof(float) * 3 * plane_cells(c));
-    L.uplane1 = o; o = align_up(o + sizeof(float) * 3 * plane_cells(c));
-    L.modes = o; o = align_up(o + sizeof(float) * 9 * (c.n_modes > 0 ? c.n_modes : 1));
-    L.err = o; o = align_up(o + sizeof(unsigned));
-    L.mpartial = o; o = align_up(o + sizeof(double) * MASS_BLOCKS);
-    L.mdone = o; o = align_up(o + sizeof(unsigned));
-    L.mout = o; o = align_up(o + sizeof(double));
-    L.total = o;
-    return L;
-}
-
-struct RotorLayout {
-    size_t sdf, d, flags, wm, utau, active, list, wlist, wphi, wwhich, count, done, partial, acc, total;
-};
-
-RotorLayout rotor_layout(long long ngrid, long long box) {
-    RotorLayout L{};
-    size_t o = 0;
-    L.sdf = o; o = align_up(o + sizeof(float) * ngrid);
-    L.d = o; o = align_up(o + sizeof(float) * box);
-    L.flags = o; o = align_up(o + box);
-    L.wm = o; o = align_up(o + sizeof(float) * 9 * box);
-    L.utau = o; o = align_up(o + sizeof(double) * box);
-    L.active = o; o = align_up(o + box);
-    L.list = o; o = align_up(o + sizeof(int) * box);
-    L.wlist = o; o = align_up(o + sizeof(int) * box);
-    L.wphi = o; o = align_up(o + sizeof(float) * box);
-    L.wwhich = o; o = align_up(o + box);
-    L.count = o; o = align_up(o + 2 * sizeof(int));
-    L.done = o; o = align_up(o + sizeof(unsigned));
-    L.partial = o; o = align_up(o + sizeof(double) * 6 * FORCE_BLOCKS);
-    L.acc = o; o = align_up(o + sizeof(double) * 12);
-    L.total = o;
-    return L;
-}
-
-struct RotorHost {
-    hl_rotor_geometry geom;
-    double omega, pitch;
-    RotorDev dev;
-    char* ws;
-    RotorLayout L;
-};
-
-}  // namespace
-
-struct hl_lattice {
-    hl_config cfg;
-    long long N;
-    cudaStream_t stream;
-    char* ws;
-    Layout L;
-    void* f;
-    float* uplane[2];
-    float* modes;
-    unsigned* err;
-    double mass_ref;
-    long long t;
-    long long n_avg;
-    int nrot;
-    RotorHost rot[MAXROT];
-    char msg[256];
-    // second stream for the rotor-box chain, and the events that order it
-    cudaStream_t aux;
-    cudaEvent_t ev_bulk[2], ev_box[2], ev_fork, ev_join;
-    bool have_aux;
-    // per-kernel event timing (hl_profile_begin / hl_profile_end)
-    bool prof_on;
-    int prof_cap;
-    std::vector<cudaEvent_t> prof_ev[6];   // start/stop pairs per kernel kind
-};
-
-namespace {
+namespace hl {
+namespace host {
 
 hl_status fail(hl_lattice* lat, hl_status code, const char* what) {
     if (lat) std::snprintf(lat->msg, sizeof lat->msg, "%s", what);
@@ -116,11 +23,10 @@ hl_status cuda_fail(hl_lattice* lat, cudaError_t e, const char* where) {
     return HL_ERR_CUDA;
 }
 
-#define HL_CUDA(lat, call)                                       \
-    do {                                                         \
-        cudaError_t e_ = (call);                                 \
-        if (e_ != cudaSuccess) return cuda_fail(lat, e_, #call); \
-    } while (0)
+}  // namespace host
+}  // namespace hl
+
+namespace {
 
 bool valid_config(const hl_config* c) {
     if (!c) return false;
@@ -138,14 +44,22 @@ bool valid_config(const hl_config* c) {
     return true;
 }
 
+}  // namespace
+
+namespace hl {
+namespace host {
+
 StepArgs make_args(const hl_lattice* lat) {
     const hl_config& c = lat->cfg;
     StepArgs a;
     std::memset(&a, 0, sizeof a);
     a.f = lat->f;
     a.N = lat->N;
-    for (int q = 0; q < c.q; ++q)
+    for (int q = 0; q < c.q; ++q) {
         a.slot[q] = static_cast<char*>(lat->f) + (size_t)q * lat->N * store_bytes(c.storage);
+        a.wslot[q] = a.slot[q];
+    }
+    a.d0 = lat->d0;
     a.n[0] = c.nx; a.n[1] = c.ny; a.n[2] = c.nz;
     a.nxy = c.nx * c.ny;
     a.nplane = (int)plane_cells(c);
@@ -187,9 +101,27 @@ StepArgs make_args(const hl_lattice* lat) {
         }
         a.rot[k].cp = (float)std::cos(R.pitch);
         a.rot[k].sp = (float)std::sin(R.pitch);
+        const double ps = lat->frozen ? R.pitch_sets : R.pitch;
+        a.rot[k].cpD = (float)std::cos(ps);
+        a.rot[k].spD = (float)std::sin(ps);
+        a.rot[k].frozen = lat->frozen ? 1 : 0;
     }
     return a;
 }
+
+hl_status read_error_word(hl_lattice* lat) {
+    unsigned e = 0;
+    HL_CUDA(lat, cudaMemcpyAsync(&e, lat->err, sizeof e, cudaMemcpyDeviceToHost, lat->stream));
+    HL_CUDA(lat, cudaStreamSynchronize(lat->stream));
+    if (e & ERR_NONFINITE) return fail(lat, HL_ERR_NONFINITE, "non-finite density on the device");
+    if (e & ERR_MASS) return fail(lat, HL_ERR_MASS, "total mass drifted beyond mass_tol");
+    return HL_OK;
+}
+
+}  // namespace host
+}  // namespace hl
+
+namespace {
 
 double shift_mass(const hl_lattice* lat) {
     std::vector<int> c(3 * lat->cfg.q);
@@ -228,15 +160,6 @@ hl_status reset_outlet_plane(hl_lattice* lat, const float u0[3]) {
         HL_CUDA(lat, cudaMemcpyAsync(lat->uplane[b], h.data(), sizeof(float) * h.size(),
                                      cudaMemcpyHostToDevice, lat->stream));
     HL_CUDA(lat, cudaStreamSynchronize(lat->stream));
-    return HL_OK;
-}
-
-hl_status read_error_word(hl_lattice* lat) {
-    unsigned e = 0;
-    HL_CUDA(lat, cudaMemcpyAsync(&e, lat->err, sizeof e, cudaMemcpyDeviceToHost, lat->stream));
-    HL_CUDA(lat, cudaStreamSynchronize(lat->stream));
-    if (e & ERR_NONFINITE) return fail(lat, HL_ERR_NONFINITE, "non-finite density on the device");
-    if (e & ERR_MASS) return fail(lat, HL_ERR_MASS, "total mass drifted beyond mass_tol");
     return HL_OK;
 }
 
@@ -410,6 +333,7 @@ hl_status hl_set_rotor(hl_lattice* lat, int* rotor_id, const hl_rotor_geometry* 
     R.geom.sdf = nullptr;
     R.omega = omega;
     R.pitch = pitch;
+    R.pitch_sets = pitch;
     R.ws = static_cast<char*>(d_workspace);
     R.L = L;
     RotorDev& D = R.dev;
@@ -472,11 +396,13 @@ static cudaError_t prof_mark(hl_lattice* lat, int k, cudaStream_t st) {
     return cudaEventRecord(e, st);
 }
 
+}  // extern "C"
+
 // one step on a single stream
-static hl_status step_serial(hl_lattice* lat) {
+static hl_status step_serial(hl_lattice* lat, const StepArgs& a0, bool with_force) {
     const int Q = lat->cfg.q, S = lat->cfg.storage;
     cudaStream_t st = lat->stream;
-    StepArgs a = make_args(lat);
+    StepArgs a = a0;
     a.part = 0;
     if (lat->nrot > 0) {
         HL_CUDA(lat, prof_mark(lat, 0, st));
@@ -492,9 +418,14 @@ static hl_status step_serial(hl_lattice* lat) {
     HL_CUDA(lat, launch_collide(Q, S, a, st));
     HL_CUDA(lat, prof_mark(lat, 1, st));
     if (lat->nrot > 0) {
-        HL_CUDA(lat, prof_mark(lat, 2, st));
-        HL_CUDA(lat, launch_force(Q, S, a, st));
-        HL_CUDA(lat, prof_mark(lat, 2, st));
+        if (with_force) {
+            HL_CUDA(lat, prof_mark(lat, 2, st));
+            HL_CUDA(lat, launch_force(Q, S, a, st));
+            HL_CUDA(lat, prof_mark(lat, 2, st));
+        } else {
+            for (int k = 0; k < lat->nrot; ++k)
+                HL_CUDA(lat, cudaMemsetAsync(lat->rot[k].dev.count, 0, 2 * sizeof(int), st));
+        }
     }
     return HL_OK;
 }
@@ -505,11 +436,11 @@ static hl_status step_serial(hl_lattice* lat) {
 // every box, lattice stream) and the box chain (embedding, wall model, box
 // collision, force; aux stream) touch disjoint memory.  Across steps:
 // box(t) waits for bulk(t-1), bulk(t) waits for box(t-1).
-static hl_status step_overlap(hl_lattice* lat) {
+static hl_status step_overlap(hl_lattice* lat, const StepArgs& a0, bool with_force) {
     const int Q = lat->cfg.q, S = lat->cfg.storage;
-    const int p = (int)(lat->t & 1), q = p ^ 1;
+    const int p = (int)(a0.t & 1), q = p ^ 1;
     cudaStream_t us = lat->stream, ax = lat->aux;
-    StepArgs a = make_args(lat);
+    StepArgs a = a0;
     // lattice stream: cells outside every rotor box
     HL_CUDA(lat, cudaStreamWaitEvent(us, lat->ev_box[q], 0));
     a.part = 1;
@@ -536,11 +467,29 @@ static hl_status step_overlap(hl_lattice* lat) {
     }
     HL_CUDA(lat, cudaEventRecord(lat->ev_box[p], ax));
     a.part = 0;
-    HL_CUDA(lat, prof_mark(lat, 2, ax));
-    HL_CUDA(lat, launch_force(Q, S, a, ax));
-    HL_CUDA(lat, prof_mark(lat, 2, ax));
+    if (with_force) {
+        HL_CUDA(lat, prof_mark(lat, 2, ax));
+        HL_CUDA(lat, launch_force(Q, S, a, ax));
+        HL_CUDA(lat, prof_mark(lat, 2, ax));
+    } else {
+        for (int k = 0; k < lat->nrot; ++k)
+            HL_CUDA(lat, cudaMemsetAsync(lat->rot[k].dev.count, 0, 2 * sizeof(int), ax));
+    }
     return HL_OK;
 }
+
+namespace hl {
+namespace host {
+
+hl_status issue_step(hl_lattice* lat, const StepArgs& a, bool with_force) {
+    const bool two = lat->have_aux && lat->nrot > 0;
+    return two ? step_overlap(lat, a, with_force) : step_serial(lat, a, with_force);
+}
+
+}  // namespace host
+}  // namespace hl
+
+extern "C" {
 
 hl_status hl_step_async(hl_lattice* lat, int n) {
     if (!lat || n < 0) return HL_ERR_ARG;
@@ -551,7 +500,7 @@ hl_status hl_step_async(hl_lattice* lat, int n) {
         HL_CUDA(lat, cudaStreamWaitEvent(lat->aux, lat->ev_fork, 0));
     }
     for (int s = 0; s < n; ++s) {
-        hl_status st = two ? step_overlap(lat) : step_serial(lat);
+        hl_status st = issue_step(lat, make_args(lat), true);
         if (st != HL_OK) return st;
         const long long t_done = lat->t;
         lat->t += 1;

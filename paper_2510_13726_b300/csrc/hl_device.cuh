@@ -262,6 +262,8 @@ struct RotorDev {
     float inv_h, h;
     float reach_plane2, reach_axial;   // cells beyond these can be neither force nor wall cells
     float ck[MAXBLADES], sk[MAXBLADES], cp, sp;   // per-step frames
+    float cpD, spD;             // pitch frames that decide the cell sets (cp, sp unless frozen)
+    int frozen;                 // 1: sets from (cpD, spD), porosity / normal / distance from (cp, sp)
     float* d;                   // [box] porosity
     uint8_t* flags;             // [box] bit0: d<1 (force set), bit1: wall cell
     float* wm;                  // [9][box]: du_x du_y du_z S_xx S_yy S_zz S_xy S_xz S_yz
@@ -275,7 +277,19 @@ struct RotorDev {
     double* partial;            // [FORCE_BLOCKS][6]
     unsigned* done;             // [1]
     double* acc;                // F(3) M(3) | F_sum(3) M_sum(3)
+    // reverse sweep only (null in forward steps)
+    float* ddp;                 // [box] d(porosity)/d(pitch) of force cells
+    float* gub;                 // [3][box] adjoint of u^B at wall cells
+    float* gS;                  // [6][box] adjoint of S^FD at wall cells
+    const double* tape_utau;    // [box] friction velocity at the start of the step (Newton start)
+    const uint8_t* tape_active; // [box] wall function active in the previous step
+    const double* gut_next;     // [box] adjoint of this step's friction velocity
+    double* gut_prev;           // [box] adjoint of the previous step's friction velocity
+    double* pacc;               // [PACC_SLOTS] pitch-gradient accumulators
+    float wT, wQ;               // objective weights / n_avg for this step (0 outside the window)
 };
+
+constexpr int PACC_SLOTS = 64;
 
 constexpr uint8_t FL_B = 1, FL_W = 2;
 
@@ -304,8 +318,9 @@ __device__ __forceinline__ float blade_sample(const RotorDev& R, float pR, float
     return lerp_rn(w0, w1, tz);
 }
 
-// Signed distance of cell (x,y,z) to the rotor; which = blade, or n_blades for the hub.
-__device__ __forceinline__ float rotor_phi(const RotorDev& R, int x, int y, int z, int& which) {
+// Signed distance of cell (x,y,z) to the rotor at pitch frames (cp, sp);
+// which = blade, or n_blades for the hub.
+__device__ __forceinline__ float rotor_phi(const RotorDev& R, float cp, float sp, int x, int y, int z, int& which) {
     const float rl[3] = {__fsub_rn((float)x, R.cf[0]), __fsub_rn((float)y, R.cf[1]),
                          __fsub_rn((float)z, R.cf[2])};
     const int a = R.axis, b = (a + 1) % 3, c = (a + 2) % 3;
@@ -315,8 +330,8 @@ __device__ __forceinline__ float rotor_phi(const RotorDev& R, int x, int y, int 
     for (int k = 0; k < R.n_blades; ++k) {
         const float pR = __fmaf_rn(R.ck[k], rb, __fmul_rn(R.sk[k], rc));
         const float pT = __fmaf_rn(R.ck[k], rc, -__fmul_rn(R.sk[k], rb));
-        const float qT = __fmaf_rn(R.cp, pT, -__fmul_rn(R.sp, ra));
-        const float qA = __fmaf_rn(R.cp, ra, __fmul_rn(R.sp, pT));
+        const float qT = __fmaf_rn(cp, pT, -__fmul_rn(sp, ra));
+        const float qA = __fmaf_rn(cp, ra, __fmul_rn(sp, pT));
         const float v = blade_sample(R, pR, qT, qA);
         if (v < best) { best = v; which = k; }
     }
@@ -326,6 +341,26 @@ __device__ __forceinline__ float rotor_phi(const RotorDev& R, int x, int y, int 
         if (v < best) { best = v; which = R.n_blades; }
     }
     return best;
+}
+
+// Signed distance of one component (blade `which`, or the hub) at the
+// current pitch frames, with the operations of rotor_phi: for the component
+// that attains the minimum the two agree bit for bit.
+__device__ __forceinline__ float component_phi(const RotorDev& R, int which, int x, int y, int z) {
+    const float rl[3] = {__fsub_rn((float)x, R.cf[0]), __fsub_rn((float)y, R.cf[1]),
+                         __fsub_rn((float)z, R.cf[2])};
+    const int a = R.axis, b = (a + 1) % 3, c = (a + 2) % 3;
+    const float rb = rl[b], rc = rl[c], ra = rl[a];
+    if (which >= R.n_blades) {
+        const float r2 = __fmaf_rn(rb, rb, __fmaf_rn(rc, rc, __fmul_rn(ra, ra)));
+        return __fsub_rn(__fsqrt_rn(r2), R.hub);
+    }
+    const int k = which;
+    const float pR = __fmaf_rn(R.ck[k], rb, __fmul_rn(R.sk[k], rc));
+    const float pT = __fmaf_rn(R.ck[k], rc, -__fmul_rn(R.sk[k], rb));
+    const float qT = __fmaf_rn(R.cp, pT, -__fmul_rn(R.sp, ra));
+    const float qA = __fmaf_rn(R.cp, ra, __fmul_rn(R.sp, pT));
+    return blade_sample(R, pR, qT, qA);
 }
 
 // Outward unit normal (lab frame): trilinear interpolation of the grid's

@@ -1,0 +1,878 @@
+// Discrete adjoint of the rotor time step and the checkpointed reverse
+// sweep behind hl_grad().
+//
+// Objective (Sec. 3.2 forces, time-averaged over a window):
+//   J = (1/n_avg) sum over the last n_avg of T steps of
+//       sum_k [ wT_k F_k(t).a_k + wQ_k M_k(t).a_k ],
+// gradients with respect to each rotor's pitch and the static porosity
+// multiplier d0 (d = d0 d_rotor in Eq. (convexVelocity)), with the cell sets
+// held at their forward values.
+//
+// Per reverse step t (the forward quantities of step t recomputed from the
+// stored pre-collision state f_t):
+//   band_kernel (tangent)   porosity, sets and d(porosity)/d(pitch)
+//   wall_kernel             wall-model outputs of step t (linearisation point)
+//   adj_bulk_kernel         cells outside every rotor box and the open planes:
+//                           lam*_i(x) = lam_{t+1,i}(x + c_i) (transpose of the
+//                           streaming), collision VJP, outlet equilibrium and
+//                           the outlet's use of the upstream velocity
+//   adj_box_kernel          rotor-box cells: the same plus the transpose of the
+//                           momentum exchange and the band parameters
+//   adj_wall_kernel         reverse pass of the wall model: corner populations,
+//                           pitch, the next step's Newton start
+// Memory: checkpoints of the full state every K steps, and the K states of a
+// segment recomputed out of place (read buffer j, write buffer j + 1).
+#include <cmath>
+#include <cstring>
+
+#include "hl_adjoint.cuh"
+#include "hl_host.h"
+
+namespace hl {
+
+struct AdjArgs {
+    const float* lam_next;   // [Q][N] adjoint of the pre-collision populations of step t + 1
+    float* lam;              // [Q][N] adjoint of the pre-collision populations of step t
+    float* dJdd0;            // [N] accumulated gradient, or null
+    const float* gup_cur;    // [3][plane] adjoint of the upstream velocity this step hands to the outlet
+    float* gup_prev;         // [3][plane] adjoint of the velocity the outlet read in this step
+};
+
+namespace {
+
+struct Offs {
+    int x[3], y[3], z[3];
+};
+
+__device__ __forceinline__ void make_offs(const StepArgs& a, int x, int y, int z, Offs& o) {
+    const int nx = a.n[0], ny = a.n[1], nz = a.n[2], nxy = a.nxy;
+    o.x[0] = x == 0 ? nx - 1 : x - 1;
+    o.x[1] = x;
+    o.x[2] = x == nx - 1 ? 0 : x + 1;
+    o.y[0] = (y == 0 ? ny - 1 : y - 1) * nx;
+    o.y[1] = y * nx;
+    o.y[2] = (y == ny - 1 ? 0 : y + 1) * nx;
+    o.z[0] = (z == 0 ? nz - 1 : z - 1) * nxy;
+    o.z[1] = z * nxy;
+    o.z[2] = (z == nz - 1 ? 0 : z + 1) * nxy;
+}
+
+__device__ __forceinline__ int sel3(int ax, int a0, int a1, int a2) { return ax == 0 ? a0 : (ax == 1 ? a1 : a2); }
+
+// pre-collision populations of a cell in the AA layout of phase PH
+template <int Q, int S, int PH>
+__device__ __forceinline__ void load_pre(const StepArgs& a, int cell, const Offs& o, float (&g)[Q]) {
+#pragma unroll
+    for (int s = 0; s < Q; ++s) {
+        if (PH == 0) {
+            g[s] = Store<S>::ld(static_cast<const typename Store<S>::T*>(a.slot[s]) + cell);
+        } else {
+            const int cx = cslot(Q, s, 0), cy = cslot(Q, s, 1), cz = cslot(Q, s, 2);
+            const int src = o.x[1 - cx] + o.y[1 - cy] + o.z[1 - cz];
+            g[s] = Store<S>::ld(static_cast<const typename Store<S>::T*>(a.slot[oslot(Q, s)]) + src);
+        }
+    }
+}
+
+// lam*_s(x) = lam_{t+1, s}(x + c_s); the adjoint is zero on the open planes,
+// so the periodic index of a neighbour across an open face reads a zero
+template <int Q>
+__device__ __forceinline__ void gather_next(const AdjArgs& j, long long N, const Offs& o, float (&ls)[Q]) {
+#pragma unroll
+    for (int s = 0; s < Q; ++s) {
+        const int cx = cslot(Q, s, 0), cy = cslot(Q, s, 1), cz = cslot(Q, s, 2);
+        ls[s] = __ldg(j.lam_next + (long long)s * N + (o.x[1 + cx] + o.y[1 + cy] + o.z[1 + cz]));
+    }
+}
+
+__device__ __forceinline__ void solid_vel(const RotorDev& R, float x, float y, float z, float us[3]) {
+    const float r[3] = {x - R.cf[0], y - R.cf[1], z - R.cf[2]};
+    const int ax = R.axis;
+    if (ax == 0) { us[0] = 0.f; us[1] = -R.omega * r[2]; us[2] = R.omega * r[1]; }
+    else if (ax == 1) { us[1] = 0.f; us[2] = -R.omega * r[0]; us[0] = R.omega * r[2]; }
+    else { us[2] = 0.f; us[0] = -R.omega * r[1]; us[1] = R.omega * r[0]; }
+}
+
+// objective weight vector of a force cell: J_step = F . v, v = wT a + wQ (a x r)
+__device__ __forceinline__ void force_weight(const RotorDev& R, float x, float y, float z, float v[3]) {
+    const float r[3] = {x - R.cf[0], y - R.cf[1], z - R.cf[2]};
+    const int ax = R.axis, b = (ax + 1) % 3, c = (ax + 2) % 3;
+    v[ax] = R.wT;
+    v[b] = -R.wQ * r[c];
+    v[c] = R.wQ * r[b];
+}
+
+// ---------------------------------------------------------------------------
+// cells outside every rotor box (and the open planes)
+// ---------------------------------------------------------------------------
+template <int Q, int S, int PH, bool D0>
+__global__ void __launch_bounds__(128) adj_bulk_kernel(const StepArgs a, const AdjArgs j) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= a.n[0] || y >= a.n[1]) return;
+    const int cell = (z * a.n[1] + y) * a.n[0] + x;
+    for (int k = 0; k < a.nrot; ++k) {
+        const unsigned dx = (unsigned)(x - a.rot[k].lo[0]), dy = (unsigned)(y - a.rot[k].lo[1]),
+                       dz = (unsigned)(z - a.rot[k].lo[2]);
+        if (dx < (unsigned)a.rot[k].n[0] && dy < (unsigned)a.rot[k].n[1] && dz < (unsigned)a.rot[k].n[2]) return;
+    }
+    const long long N = a.N;
+    const int ax = a.flow_axis;
+    const int ca = sel3(ax, x, y, z);
+    const int na = sel3(ax, a.n[0], a.n[1], a.n[2]);
+    const bool inlet = a.open && ca == 0;
+    const bool outlet = a.open && ca == na - 1;
+    if (inlet) {
+        // f* = f^eq(1, u_in(t)): no dependence on the state
+#pragma unroll
+        for (int s = 0; s < Q; ++s) j.lam[(long long)s * N + cell] = 0.0f;
+        return;
+    }
+    Offs o;
+    make_offs(a, x, y, z, o);
+    float ls[Q];
+    gather_next<Q>(j, N, o, ls);
+    const int nb = sel3(ax, a.n[1], a.n[2], a.n[0]);
+    const int pl = sel3(ax, z, x, y) * nb + sel3(ax, y, z, x);
+    if (outlet) {
+        // f* = f^eq(1, u_plane), u_plane = upstream velocity of the previous step
+        const float up[3] = {a.uplane_prev[pl], a.uplane_prev[a.nplane + pl], a.uplane_prev[2 * a.nplane + pl]};
+        float ub[3];
+        equilibrium_vjp<Q>(ls, up, ub);
+        j.gup_prev[pl] = ub[0];
+        j.gup_prev[a.nplane + pl] = ub[1];
+        j.gup_prev[2 * a.nplane + pl] = ub[2];
+#pragma unroll
+        for (int s = 0; s < Q; ++s) j.lam[(long long)s * N + cell] = 0.0f;
+        return;
+    }
+    float g[Q];
+    load_pre<Q, S, PH>(a, cell, o, g);
+    float gd, guB[3], gS[6], u[3], rho;
+    if (D0) {
+        Band B;
+        B.d = a.d0[cell];
+        B.uB[0] = B.uB[1] = B.uB[2] = 0.0f;
+        B.sigma = 1.0f;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) B.S[k] = 0.0f;
+        collide_vjp<Q, true>(g, B, a.tau_mo, a.Ksmag, ls, gd, guB, gS, u, rho);
+    } else {
+        Band B0;
+        collide_vjp<Q, false>(g, B0, a.tau_mo, a.Ksmag, ls, gd, guB, gS, u, rho);
+    }
+    if (j.dJdd0) j.dJdd0[cell] += gd;
+    if (a.open && ca == na - 2) {
+        // this cell's velocity is the outlet's u_plane of the next step
+        const float inv = 1.0f / rho;
+        const float gu[3] = {j.gup_cur[pl] * inv, j.gup_cur[a.nplane + pl] * inv, j.gup_cur[2 * a.nplane + pl] * inv};
+        const float gu_u = gu[0] * u[0] + gu[1] * u[1] + gu[2] * u[2];
+#pragma unroll
+        for (int s = 0; s < Q; ++s) {
+            const int cx = cslot(Q, s, 0), cy = cslot(Q, s, 1), cz = cslot(Q, s, 2);
+            ls[s] += float(cx) * gu[0] + float(cy) * gu[1] + float(cz) * gu[2] - gu_u;
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < Q; ++s) j.lam[(long long)s * N + cell] = ls[s];
+}
+
+// ---------------------------------------------------------------------------
+// the box of one rotor: band collision, momentum-exchange transpose, pitch
+// ---------------------------------------------------------------------------
+template <int Q, int S, int PH, bool D0>
+__global__ void __launch_bounds__(128) adj_box_kernel(const StepArgs a, const AdjArgs j, int rk, int force_on) {
+    const RotorDev& R = a.rot[rk];
+    const int bx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int by = blockIdx.y * blockDim.y + threadIdx.y;
+    const int bz = blockIdx.z;
+    const bool valid = bx < R.n[0] && by < R.n[1];
+    double pv = 0.0;
+    if (valid) {
+        const int x = R.lo[0] + bx, y = R.lo[1] + by, z = R.lo[2] + bz;
+        const int cell = (z * a.n[1] + y) * a.n[0] + x;
+        const long long bi = ((long long)bz * R.n[1] + by) * R.n[0] + bx;
+        const long long N = a.N, BC = R.box_cells;
+        Offs o;
+        make_offs(a, x, y, z, o);
+        float ls[Q];
+        gather_next<Q>(j, N, o, ls);
+        const uint8_t fl = R.flags[bi];
+        if (force_on) {
+            // transpose of the momentum exchange over the force cells (force_kernel)
+            if (fl & FL_B) {
+                float us[3], v[3];
+                solid_vel(R, (float)x, (float)y, (float)z, us);
+                force_weight(R, (float)x, (float)y, (float)z, v);
+                const float uv = us[0] * v[0] + us[1] * v[1] + us[2] * v[2];
+#pragma unroll
+                for (int s = 1; s < Q; ++s) {
+                    const int cx = cslot(Q, s, 0), cy = cslot(Q, s, 1), cz = cslot(Q, s, 2);
+                    ls[s] -= float(cx) * v[0] + float(cy) * v[1] + float(cz) * v[2] - uv;
+                }
+            }
+#pragma unroll
+            for (int s = 1; s < Q; ++s) {
+                const int cx = cslot(Q, s, 0), cy = cslot(Q, s, 1), cz = cslot(Q, s, 2);
+                const int nx = bx + cx, ny = by + cy, nz = bz + cz;
+                if (nx < 0 || ny < 0 || nz < 0 || nx >= R.n[0] || ny >= R.n[1] || nz >= R.n[2]) continue;
+                if (!(R.flags[((long long)nz * R.n[1] + ny) * R.n[0] + nx] & FL_B)) continue;
+                float us[3], v[3];
+                const float X = (float)(x + cx), Y = (float)(y + cy), Z = (float)(z + cz);
+                solid_vel(R, X, Y, Z, us);
+                force_weight(R, X, Y, Z, v);
+                ls[s] += float(cx) * v[0] + float(cy) * v[1] + float(cz) * v[2] -
+                         (us[0] * v[0] + us[1] * v[1] + us[2] * v[2]);
+            }
+        }
+        float g[Q];
+        load_pre<Q, S, PH>(a, cell, o, g);
+        Band B;
+        const float d0 = D0 ? a.d0[cell] : 1.0f;
+        B.d = d0 * R.d[bi];
+        if (fl & FL_B) {
+            solid_vel(R, (float)x, (float)y, (float)z, B.uB);
+        } else {
+            B.uB[0] = B.uB[1] = B.uB[2] = 0.0f;
+        }
+        B.sigma = a.sigma_band;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) B.S[k] = 0.0f;
+        const bool wall = a.wall_model && (fl & FL_W);
+        if (wall) {
+            const float* wm = R.wm + bi;
+            B.uB[0] += wm[0];
+            B.uB[1] += wm[BC];
+            B.uB[2] += wm[2 * BC];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) B.S[k] = wm[(3 + k) * BC];
+            B.sigma = 0.0f;
+        }
+        float gd, guB[3], gS[6], u[3], rho;
+        collide_vjp<Q, true>(g, B, a.tau_mo, a.Ksmag, ls, gd, guB, gS, u, rho);
+        if (j.dJdd0) j.dJdd0[cell] += gd * R.d[bi];
+        if (fl & FL_B) pv = (double)(gd * d0 * R.ddp[bi]);
+        if (wall) {
+            R.gub[bi] = guB[0];
+            R.gub[BC + bi] = guB[1];
+            R.gub[2 * BC + bi] = guB[2];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) R.gS[k * BC + bi] = gS[k];
+        }
+#pragma unroll
+        for (int s = 0; s < Q; ++s) j.lam[(long long)s * N + cell] = ls[s];
+    }
+    // pitch contribution of the block: FP64 block sum, one atomic per block
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) pv += __shfl_down_sync(0xffffffffu, pv, off);
+    __shared__ double sh[4];
+    const int warp = (threadIdx.y * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) sh[warp] = pv;
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        double t = 0.0;
+        const int nw = (blockDim.x * blockDim.y) >> 5;
+        for (int w = 0; w < nw; ++w) t += sh[w];
+        if (t != 0.0) {
+            const unsigned b = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+            atomicAdd(R.pacc + b % PACC_SLOTS, t);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// reverse pass of the wall model (Sec. 2.2.1) on the wall-cell list
+// ---------------------------------------------------------------------------
+template <int Q, int S, int PH>
+__global__ void __launch_bounds__(128) adj_wall_kernel(const StepArgs a, const AdjArgs j) {
+    const RotorDev& R = a.rot[blockIdx.y];
+    int count = *((volatile int*)(R.count + 1));
+    if ((long long)count > R.box_cells) count = (int)R.box_cells;
+    const long long N = a.N, BC = R.box_cells;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < count; idx += gridDim.x * blockDim.x) {
+        const long long bi = R.wlist[idx];
+        const float phi = R.wphi[idx];
+        const int which = R.wwhich[idx];
+        const int bx = (int)(bi % R.n[0]);
+        const long long r2 = bi / R.n[0];
+        const int by = (int)(r2 % R.n[1]);
+        const int bz = (int)(r2 / R.n[1]);
+        const int x = R.lo[0] + bx, y = R.lo[1] + by, z = R.lo[2] + bz;
+        float n[3], dn[3], dphi;
+        rotor_normal_tan(R, which, x, y, z, n, dn);
+        component_phi_tan(R, which, x, y, z, dphi);
+        const bool far = phi > 0.5f;
+        const float y1 = far ? phi : 0.5f;
+        const float ys = a.wmYs;
+        const float xs[3] = {x + ys * n[0], y + ys * n[1], z + ys * n[2]};
+        int i0[3];
+        float t[3];
+        bool clamped[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float fl = floorf(xs[k]);
+            i0[k] = (int)fl;
+            t[k] = xs[k] - fl;
+            clamped[k] = false;
+            if (a.open && k == a.flow_axis) {
+                if (i0[k] < 0) { i0[k] = 0; t[k] = 0.f; clamped[k] = true; }
+                if (i0[k] > a.n[k] - 2) { i0[k] = a.n[k] - 2; t[k] = 1.f; clamped[k] = true; }
+            }
+        }
+        int cidx[8];
+        float uc[8][3], irho[8];
+        float us[3] = {0.f, 0.f, 0.f};
+        for (int m = 0; m < 8; ++m) {
+            const int cx = m & 1, cy = (m >> 1) & 1, cz = m >> 2;
+            int p[3] = {i0[0] + cx, i0[1] + cy, i0[2] + cz};
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                if (!(a.open && k == a.flow_axis)) p[k] = ((p[k] % a.n[k]) + a.n[k]) % a.n[k];
+            const int c = (p[2] * a.n[1] + p[1]) * a.n[0] + p[0];
+            cidx[m] = c;
+            Offs o;
+            make_offs(a, p[0], p[1], p[2], o);
+            float g[Q];
+            load_pre<Q, S, PH>(a, c, o, g);
+            float drho, jj[3];
+            moments01<Q>(g, drho, jj);
+            irho[m] = 1.0f / (1.0f + drho);
+            uc[m][0] = jj[0] * irho[m]; uc[m][1] = jj[1] * irho[m]; uc[m][2] = jj[2] * irho[m];
+            const float wgt = (cx ? t[0] : 1.f - t[0]) * (cy ? t[1] : 1.f - t[1]) * (cz ? t[2] : 1.f - t[2]);
+            us[0] += wgt * uc[m][0]; us[1] += wgt * uc[m][1]; us[2] += wgt * uc[m][2];
+        }
+        float usol[3];
+        solid_vel(R, (float)x, (float)y, (float)z, usol);
+        const float ur[3] = {us[0] - usol[0], us[1] - usol[1], us[2] - usol[2]};
+        const float un = ur[0] * n[0] + ur[1] * n[1] + ur[2] * n[2];
+        const float ut[3] = {ur[0] - un * n[0], ur[1] - un * n[1], ur[2] - un * n[2]};
+        const float utm = sqrtf(ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2]);
+        R.gut_prev[bi] = 0.0;
+        if (!(utm >= 1e-12f)) continue;   // the forward left this cell inactive
+        const float th[3] = {ut[0] / utm, ut[1] / utm, ut[2] / utm};
+        // forward Newton solves with derivatives along (|u_t|, y_sample, start value)
+        const double ysamp = (double)y1 + (double)ys;
+        const bool warm = R.tape_active[bi] != 0;
+        D3 guess;
+        if (warm) {
+            guess = dmk(R.tape_utau[bi], 0.0, 0.0, 1.0);
+        } else {
+            const double g0 = sqrt(a.nu * (double)utm / (double)ys);
+            guess = dmk(g0, a.nu / ((double)ys * 2.0 * g0), 0.0, 0.0);
+        }
+        const D3 utau = wall_newton_d(dmk((double)utm, 1.0, 0.0, 0.0), dmk(ysamp, 0.0, 1.0, 0.0), a.nu, guess, a.wmE,
+                                      a.wmK, a.wmTol, a.wmMaxit);
+        const double y1p = (double)y1 * utau.v / a.nu;
+        const D3 up = spalding_uplus_d(dmk(y1p, 1.0, 0.0, 0.0), a.wmE, a.wmK, a.wmTol, a.wmMaxit);
+        const float uw = (float)(utau.v * up.v);
+        const float gs = (float)(0.5 * ((double)utm - utau.v * up.v) / (double)ys);
+        // ---- reverse ----
+        const float gdu[3] = {R.gub[bi], R.gub[BC + bi], R.gub[2 * BC + bi]};
+        float Sb[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) Sb[k] = R.gS[k * BC + bi];
+        // du = uw th
+        float uwb = gdu[0] * th[0] + gdu[1] * th[1] + gdu[2] * th[2];
+        float thb[3] = {uw * gdu[0], uw * gdu[1], uw * gdu[2]};
+        // S = gs (2 th_a n_a | th_a n_b + n_a th_b)
+        const float gsb = 2.0f * (Sb[0] * th[0] * n[0] + Sb[1] * th[1] * n[1] + Sb[2] * th[2] * n[2]) +
+                          Sb[3] * (th[0] * n[1] + n[0] * th[1]) + Sb[4] * (th[0] * n[2] + n[0] * th[2]) +
+                          Sb[5] * (th[1] * n[2] + n[1] * th[2]);
+        thb[0] += gs * (2.0f * Sb[0] * n[0] + Sb[3] * n[1] + Sb[4] * n[2]);
+        thb[1] += gs * (2.0f * Sb[1] * n[1] + Sb[3] * n[0] + Sb[5] * n[2]);
+        thb[2] += gs * (2.0f * Sb[2] * n[2] + Sb[4] * n[0] + Sb[5] * n[1]);
+        float nb[3] = {gs * (2.0f * Sb[0] * th[0] + Sb[3] * th[1] + Sb[4] * th[2]),
+                       gs * (2.0f * Sb[1] * th[1] + Sb[3] * th[0] + Sb[5] * th[2]),
+                       gs * (2.0f * Sb[2] * th[2] + Sb[4] * th[0] + Sb[5] * th[1])};
+        // gs = (|u_t| - utau u+) / (2 y_s)
+        float utmb = 0.5f * gsb / ys;
+        const double uwdb = (double)uwb - 0.5 * (double)gsb / (double)ys;
+        double utaub = uwdb * up.v + R.gut_next[bi];
+        const double upb = uwdb * utau.v;
+        // u+ = U(y1 utau / nu)
+        const double y1pb = upb * up.d[0];
+        utaub += y1pb * (double)y1 / a.nu;
+        double y1b = y1pb * utau.v / a.nu;
+        // utau = Newton(|u_t|, y1 + y_s, start)
+        utmb += (float)(utaub * utau.d[0]);
+        y1b += utaub * utau.d[1];
+        R.gut_prev[bi] = warm ? utaub * utau.d[2] : 0.0;
+        // th = u_t / |u_t|
+        const float td = thb[0] * th[0] + thb[1] * th[1] + thb[2] * th[2];
+        float utb[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) utb[k] = (thb[k] - td * th[k]) / utm + utmb * th[k];
+        // u_t = u_r - (u_r . n) n
+        const float utn = utb[0] * n[0] + utb[1] * n[1] + utb[2] * n[2];
+        float urb[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            urb[k] = utb[k] - utn * n[k];
+            nb[k] -= un * utb[k] + utn * ur[k];
+        }
+        // u_s = sum_m w_m u_m (trilinear at x_s = x + y_s n)
+        float xsb[3] = {0.f, 0.f, 0.f};
+        for (int m = 0; m < 8; ++m) {
+            const int cx = m & 1, cy = (m >> 1) & 1, cz = m >> 2;
+            const float wx = cx ? t[0] : 1.f - t[0], wy = cy ? t[1] : 1.f - t[1], wz = cz ? t[2] : 1.f - t[2];
+            const float wgt = wx * wy * wz;
+            const float ucb[3] = {wgt * urb[0], wgt * urb[1], wgt * urb[2]};
+            const float dot = uc[m][0] * urb[0] + uc[m][1] * urb[1] + uc[m][2] * urb[2];
+            if (!clamped[0]) xsb[0] += (cx ? 1.f : -1.f) * wy * wz * dot;
+            if (!clamped[1]) xsb[1] += (cy ? 1.f : -1.f) * wx * wz * dot;
+            if (!clamped[2]) xsb[2] += (cz ? 1.f : -1.f) * wx * wy * dot;
+            // u_m = j_m / rho_m: d u_m / d g_s = (c_s - u_m) / rho_m
+            const float ir = irho[m];
+            const float cu = (ucb[0] * uc[m][0] + ucb[1] * uc[m][1] + ucb[2] * uc[m][2]) * ir;
+            float* lp = j.lam + cidx[m];
+#pragma unroll
+            for (int s = 0; s < Q; ++s) {
+                const int sx = cslot(Q, s, 0), sy = cslot(Q, s, 1), sz = cslot(Q, s, 2);
+                const float v = (float(sx) * ucb[0] + float(sy) * ucb[1] + float(sz) * ucb[2]) * ir - cu;
+                if (v != 0.0f) atomicAdd(lp + (long long)s * N, v);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) nb[k] += ys * xsb[k];
+        // pitch: through the normal and the wall distance y1 = max(phi, 1/2)
+        double pg = (double)(nb[0] * dn[0] + nb[1] * dn[1] + nb[2] * dn[2]);
+        if (far) pg += y1b * (double)dphi;
+        atomicAdd(R.pacc + (unsigned)idx % PACC_SLOTS, pg);
+    }
+}
+
+// collision VJP of n independent cells (unit checks)
+template <int Q>
+__global__ void debug_collide_vjp_kernel(int n, const float* gin, const float* d, const float* uB, const float* sigma,
+                                         const float* S, float tau_mo, float Ksmag, const float* lin, float* lout,
+                                         float* gd_out, float* guB_out, float* gS_out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    float g[Q], l[Q];
+#pragma unroll
+    for (int s = 0; s < Q; ++s) { g[s] = gin[(long long)c * Q + s]; l[s] = lin[(long long)c * Q + s]; }
+    float gd, guB[3], gS[6], u[3], rho;
+    if (d) {
+        Band B;
+        B.d = d[c];
+        B.uB[0] = uB[3 * c]; B.uB[1] = uB[3 * c + 1]; B.uB[2] = uB[3 * c + 2];
+        B.sigma = sigma[c];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) B.S[k] = S[6 * c + k];
+        collide_vjp<Q, true>(g, B, tau_mo, Ksmag, l, gd, guB, gS, u, rho);
+    } else {
+        Band B0;
+        collide_vjp<Q, false>(g, B0, tau_mo, Ksmag, l, gd, guB, gS, u, rho);
+    }
+#pragma unroll
+    for (int s = 0; s < Q; ++s) lout[(long long)c * Q + s] = l[s];
+    if (gd_out) gd_out[c] = gd;
+    if (guB_out) for (int k = 0; k < 3; ++k) guB_out[3 * c + k] = guB[k];
+    if (gS_out) for (int k = 0; k < 6; ++k) gS_out[6 * c + k] = gS[k];
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+dim3 cell_block(int nx) {
+    if (nx >= 128) return dim3(128, 1, 1);
+    const int bx = ((nx + 31) / 32) * 32;
+    return dim3(bx, 128 / bx >= 1 ? 128 / bx : 1, 1);
+}
+
+template <int Q, int S>
+cudaError_t launch_adj_t(const StepArgs& a, const AdjArgs& j, bool force_on, cudaStream_t s) {
+    {
+        const dim3 blk = cell_block(a.n[0]);
+        const dim3 grd((a.n[0] + blk.x - 1) / blk.x, (a.n[1] + blk.y - 1) / blk.y, a.n[2]);
+        if (a.d0) {
+            if (a.phase == 0) adj_bulk_kernel<Q, S, 0, true><<<grd, blk, 0, s>>>(a, j);
+            else adj_bulk_kernel<Q, S, 1, true><<<grd, blk, 0, s>>>(a, j);
+        } else {
+            if (a.phase == 0) adj_bulk_kernel<Q, S, 0, false><<<grd, blk, 0, s>>>(a, j);
+            else adj_bulk_kernel<Q, S, 1, false><<<grd, blk, 0, s>>>(a, j);
+        }
+    }
+    for (int k = 0; k < a.nrot; ++k) {
+        const int* n = a.rot[k].n;
+        const dim3 blk = cell_block(n[0]);
+        const dim3 grd((n[0] + blk.x - 1) / blk.x, (n[1] + blk.y - 1) / blk.y, n[2]);
+        const int fo = force_on ? 1 : 0;
+        if (a.d0) {
+            if (a.phase == 0) adj_box_kernel<Q, S, 0, true><<<grd, blk, 0, s>>>(a, j, k, fo);
+            else adj_box_kernel<Q, S, 1, true><<<grd, blk, 0, s>>>(a, j, k, fo);
+        } else {
+            if (a.phase == 0) adj_box_kernel<Q, S, 0, false><<<grd, blk, 0, s>>>(a, j, k, fo);
+            else adj_box_kernel<Q, S, 1, false><<<grd, blk, 0, s>>>(a, j, k, fo);
+        }
+    }
+    if (a.nrot > 0 && a.wall_model) {
+        const dim3 grd(WALL_BLOCKS, a.nrot);
+        if (a.phase == 0) adj_wall_kernel<Q, S, 0><<<grd, 128, 0, s>>>(a, j);
+        else adj_wall_kernel<Q, S, 1><<<grd, 128, 0, s>>>(a, j);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj(int Q, int S, const StepArgs& a, const AdjArgs& j, bool force_on, cudaStream_t s) {
+    if (Q == 19 && S == ST_F32) return launch_adj_t<19, ST_F32>(a, j, force_on, s);
+    if (Q == 19 && S == ST_F16S) return launch_adj_t<19, ST_F16S>(a, j, force_on, s);
+    if (Q == 19 && S == ST_BF16S) return launch_adj_t<19, ST_BF16S>(a, j, force_on, s);
+    if (Q == 27 && S == ST_F32) return launch_adj_t<27, ST_F32>(a, j, force_on, s);
+    if (Q == 27 && S == ST_F16S) return launch_adj_t<27, ST_F16S>(a, j, force_on, s);
+    if (Q == 27 && S == ST_BF16S) return launch_adj_t<27, ST_BF16S>(a, j, force_on, s);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace
+}  // namespace hl
+
+// ===========================================================================
+// host driver
+// ===========================================================================
+using namespace hl;
+using namespace hl::host;
+
+namespace {
+
+long long pop_bytes(const hl_lattice* lat) {
+    return (long long)lat->cfg.q * lat->N * store_bytes(lat->cfg.storage);
+}
+
+// one checkpoint: populations, both outlet planes (in buffer order), and
+// per rotor the wall-model state (u_tau, active)
+size_t ckpt_bytes(const hl_lattice* lat) {
+    size_t o = align_up((size_t)pop_bytes(lat));
+    o += 2 * align_up(sizeof(float) * 3 * plane_cells(lat->cfg));
+    for (int k = 0; k < lat->nrot; ++k) {
+        o += align_up(sizeof(double) * lat->rot[k].dev.box_cells);
+        o += align_up((size_t)lat->rot[k].dev.box_cells);
+    }
+    return o;
+}
+
+// per step of a segment: the outlet velocity read by the step and the
+// wall-model state at its start
+size_t small_bytes(const hl_lattice* lat) {
+    size_t o = align_up(sizeof(float) * 3 * plane_cells(lat->cfg));
+    for (int k = 0; k < lat->nrot; ++k) {
+        o += align_up(sizeof(double) * lat->rot[k].dev.box_cells);
+        o += align_up((size_t)lat->rot[k].dev.box_cells);
+    }
+    return o;
+}
+
+size_t rotor_adj_bytes(const hl_lattice* lat, int k) {
+    const long long b = lat->rot[k].dev.box_cells;
+    return align_up(sizeof(float) * b) + align_up(sizeof(float) * 3 * b) + align_up(sizeof(float) * 6 * b) +
+           2 * align_up(sizeof(double) * b) + align_up(sizeof(double) * PACC_SLOTS) + align_up(sizeof(double) * 12);
+}
+
+struct GradLayout {
+    int n_ck;
+    size_t ck, seg, small, lam, gup, radj[MAXROT], total;
+};
+
+GradLayout grad_layout(const hl_lattice* lat, int steps, int K) {
+    GradLayout G{};
+    G.n_ck = (steps + K - 1) / K;
+    size_t o = 0;
+    G.ck = o; o += (size_t)(G.n_ck + 1) * ckpt_bytes(lat);
+    G.seg = o; o += (size_t)(K - 1) * align_up((size_t)pop_bytes(lat));
+    G.small = o; o += (size_t)K * small_bytes(lat);
+    G.lam = o; o += 2 * align_up(sizeof(float) * lat->cfg.q * lat->N);
+    G.gup = o; o += 2 * align_up(sizeof(float) * 3 * plane_cells(lat->cfg));
+    for (int k = 0; k < lat->nrot; ++k) {
+        G.radj[k] = o;
+        o += rotor_adj_bytes(lat, k);
+    }
+    G.total = o;
+    return G;
+}
+
+float* uplane_prev_of(hl_lattice* lat, long long t) { return lat->uplane[(t + 1) & 1]; }
+
+// copy the lattice state (populations, outlet planes, wall-model state) to
+// or from a checkpoint
+hl_status ckpt_copy(hl_lattice* lat, char* ck, bool save, bool with_pops) {
+    const cudaMemcpyKind kd = cudaMemcpyDeviceToDevice;
+    cudaStream_t st = lat->stream;
+    size_t o = 0;
+    const size_t pb = (size_t)pop_bytes(lat);
+    if (with_pops)
+        HL_CUDA(lat, save ? cudaMemcpyAsync(ck, lat->f, pb, kd, st) : cudaMemcpyAsync(lat->f, ck, pb, kd, st));
+    o = align_up(pb);
+    const size_t plb = sizeof(float) * 3 * plane_cells(lat->cfg);
+    for (int b = 0; b < 2; ++b) {
+        HL_CUDA(lat, save ? cudaMemcpyAsync(ck + o, lat->uplane[b], plb, kd, st)
+                          : cudaMemcpyAsync(lat->uplane[b], ck + o, plb, kd, st));
+        o += align_up(plb);
+    }
+    for (int k = 0; k < lat->nrot; ++k) {
+        RotorDev& D = lat->rot[k].dev;
+        const size_t ub = sizeof(double) * D.box_cells;
+        HL_CUDA(lat, save ? cudaMemcpyAsync(ck + o, D.utau, ub, kd, st) : cudaMemcpyAsync(D.utau, ck + o, ub, kd, st));
+        o += align_up(ub);
+        const size_t ab = (size_t)D.box_cells;
+        HL_CUDA(lat, save ? cudaMemcpyAsync(ck + o, D.active, ab, kd, st)
+                          : cudaMemcpyAsync(D.active, ck + o, ab, kd, st));
+        o += align_up(ab);
+    }
+    return HL_OK;
+}
+
+// save (save = true) the step's small state from the lattice, or restore the
+// wall-model part of it
+hl_status small_copy(hl_lattice* lat, char* sm, long long t, bool save) {
+    const cudaMemcpyKind kd = cudaMemcpyDeviceToDevice;
+    cudaStream_t st = lat->stream;
+    size_t o = 0;
+    const size_t plb = sizeof(float) * 3 * plane_cells(lat->cfg);
+    if (save) HL_CUDA(lat, cudaMemcpyAsync(sm, uplane_prev_of(lat, t), plb, kd, st));
+    o = align_up(plb);
+    for (int k = 0; k < lat->nrot; ++k) {
+        RotorDev& D = lat->rot[k].dev;
+        const size_t ub = sizeof(double) * D.box_cells;
+        HL_CUDA(lat, save ? cudaMemcpyAsync(sm + o, D.utau, ub, kd, st) : cudaMemcpyAsync(D.utau, sm + o, ub, kd, st));
+        o += align_up(ub);
+        const size_t ab = (size_t)D.box_cells;
+        HL_CUDA(lat, save ? cudaMemcpyAsync(sm + o, D.active, ab, kd, st)
+                          : cudaMemcpyAsync(D.active, sm + o, ab, kd, st));
+        o += align_up(ab);
+    }
+    return HL_OK;
+}
+
+// arguments of step t with explicit read / write population buffers
+StepArgs args_at(hl_lattice* lat, long long t, void* rd, void* wr) {
+    const long long keep = lat->t;
+    lat->t = t;
+    StepArgs a = make_args(lat);
+    lat->t = keep;
+    const size_t sb = (size_t)lat->N * store_bytes(lat->cfg.storage);
+    for (int q = 0; q < lat->cfg.q; ++q) {
+        a.f = rd;
+        a.slot[q] = static_cast<char*>(rd) + q * sb;
+        a.wslot[q] = static_cast<char*>(wr) + q * sb;
+    }
+    return a;
+}
+
+hl_status fork_aux(hl_lattice* lat) {
+    if (!(lat->have_aux && lat->nrot > 0)) return HL_OK;
+    HL_CUDA(lat, cudaEventRecord(lat->ev_fork, lat->stream));
+    HL_CUDA(lat, cudaStreamWaitEvent(lat->aux, lat->ev_fork, 0));
+    return HL_OK;
+}
+
+hl_status join_aux(hl_lattice* lat) {
+    if (!(lat->have_aux && lat->nrot > 0)) return HL_OK;
+    HL_CUDA(lat, cudaEventRecord(lat->ev_join, lat->aux));
+    HL_CUDA(lat, cudaStreamWaitEvent(lat->stream, lat->ev_join, 0));
+    return HL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hl_status hl_grad_workspace_size(const hl_lattice* lat, int steps, int ckpt_every, size_t* bytes) {
+    if (!lat || steps < 1 || ckpt_every < 1 || !bytes) return HL_ERR_ARG;
+    *bytes = grad_layout(lat, steps, ckpt_every).total;
+    return HL_OK;
+}
+
+hl_status hl_grad(hl_lattice* lat, int steps, int avg_last, int ckpt_every, const double* w_thrust,
+                  const double* w_torque, double* J, double* dJ_dpitch, float* d_dJ_dd0, void* d_work,
+                  size_t bytes) {
+    if (!lat) return HL_ERR_ARG;
+    if (steps < 1 || avg_last < 1 || avg_last > steps || ckpt_every < 1 || !w_thrust || !w_torque || !d_work)
+        return fail(lat, HL_ERR_ARG, "hl_grad: invalid arguments");
+    if (reinterpret_cast<size_t>(d_work) % ALIGN) return fail(lat, HL_ERR_ARG, "hl_grad: workspace not aligned");
+    const int T = steps, K = ckpt_every, na = avg_last;
+    const GradLayout G = grad_layout(lat, T, K);
+    if (bytes < G.total) return fail(lat, HL_ERR_WORKSPACE, "hl_grad: workspace too small");
+    char* ws = static_cast<char*>(d_work);
+    const int Q = lat->cfg.q, S = lat->cfg.storage;
+    cudaStream_t st = lat->stream;
+    const long long t0 = lat->t;
+    const size_t ckb = ckpt_bytes(lat), smb = small_bytes(lat), pb = align_up((size_t)pop_bytes(lat));
+    const size_t plb = sizeof(float) * 3 * plane_cells(lat->cfg);
+    hl_status rc;
+
+    // per-rotor adjoint arrays
+    struct RAdj { float *ddp, *gub, *gS; double *gut[2], *pacc, *accsnap; } ra[MAXROT];
+    for (int k = 0; k < lat->nrot; ++k) {
+        const long long b = lat->rot[k].dev.box_cells;
+        char* p = ws + G.radj[k];
+        ra[k].ddp = reinterpret_cast<float*>(p); p += align_up(sizeof(float) * b);
+        ra[k].gub = reinterpret_cast<float*>(p); p += align_up(sizeof(float) * 3 * b);
+        ra[k].gS = reinterpret_cast<float*>(p); p += align_up(sizeof(float) * 6 * b);
+        ra[k].gut[0] = reinterpret_cast<double*>(p); p += align_up(sizeof(double) * b);
+        ra[k].gut[1] = reinterpret_cast<double*>(p); p += align_up(sizeof(double) * b);
+        ra[k].pacc = reinterpret_cast<double*>(p); p += align_up(sizeof(double) * PACC_SLOTS);
+        ra[k].accsnap = reinterpret_cast<double*>(p);
+    }
+
+    // ---- forward pass: checkpoints every K steps, force sums at the window start ----
+    for (int s = 0; s < T;) {
+        if (s % K == 0) {
+            if ((rc = ckpt_copy(lat, ws + G.ck + (size_t)(s / K) * ckb, true, true)) != HL_OK) return rc;
+        }
+        if (s == T - na)
+            for (int k = 0; k < lat->nrot; ++k)
+                HL_CUDA(lat, cudaMemcpyAsync(ra[k].accsnap, lat->rot[k].dev.acc, 12 * sizeof(double),
+                                             cudaMemcpyDeviceToDevice, st));
+        int n = K - s % K;
+        if (s < T - na && s + n > T - na) n = T - na - s;
+        if (s + n > T) n = T - s;
+        if ((rc = hl_step_async(lat, n)) != HL_OK) return rc;
+        s += n;
+    }
+    if ((rc = ckpt_copy(lat, ws + G.ck + (size_t)G.n_ck * ckb, true, true)) != HL_OK) return rc;
+    if ((rc = read_error_word(lat)) != HL_OK) return rc;
+    // J from the force sums at the window start and end
+    {
+        double Jv = 0.0;
+        for (int k = 0; k < lat->nrot; ++k) {
+            double a0[12], a1[12];
+            HL_CUDA(lat, cudaMemcpyAsync(a0, ra[k].accsnap, sizeof a0, cudaMemcpyDeviceToHost, st));
+            HL_CUDA(lat, cudaMemcpyAsync(a1, lat->rot[k].dev.acc, sizeof a1, cudaMemcpyDeviceToHost, st));
+            HL_CUDA(lat, cudaStreamSynchronize(st));
+            const int ax = lat->rot[k].geom.axis;
+            Jv += (w_thrust[k] * (a1[6 + ax] - a0[6 + ax]) + w_torque[k] * (a1[9 + ax] - a0[9 + ax])) / na;
+        }
+        if (J) *J = Jv;
+    }
+
+    // ---- reverse sweep ----
+    float* lam[2] = {reinterpret_cast<float*>(ws + G.lam),
+                     reinterpret_cast<float*>(ws + G.lam + align_up(sizeof(float) * Q * lat->N))};
+    float* gup[2] = {reinterpret_cast<float*>(ws + G.gup), reinterpret_cast<float*>(ws + G.gup + align_up(plb))};
+    HL_CUDA(lat, cudaMemsetAsync(ws + G.lam, 0, 2 * align_up(sizeof(float) * Q * lat->N), st));
+    HL_CUDA(lat, cudaMemsetAsync(ws + G.gup, 0, 2 * align_up(plb), st));
+    for (int k = 0; k < lat->nrot; ++k) HL_CUDA(lat, cudaMemsetAsync(ws + G.radj[k], 0, rotor_adj_bytes(lat, k), st));
+    if (d_dJ_dd0) HL_CUDA(lat, cudaMemsetAsync(d_dJ_dd0, 0, sizeof(float) * lat->N, st));
+    int ln = 0;      // lam[ln] = adjoint of the populations at t + 1
+    int gc = 0;      // gup[gc] = adjoint of the outlet velocity written at t
+    int uc = 0;      // gut[uc] = adjoint of the friction velocity of step t
+    for (int m = G.n_ck - 1; m >= 0; --m) {
+        const long long ts = t0 + (long long)m * K;
+        const int L = (int)std::min<long long>(K, T - (long long)m * K);
+        char* ck = ws + G.ck + (size_t)m * ckb;
+        auto buf = [&](int jj) -> void* { return jj == 0 ? (void*)ck : (void*)(ws + G.seg + (size_t)(jj - 1) * pb); };
+        // recompute the segment out of place, recording each step's small state;
+        // the cell lists start empty (the last reverse step left them filled)
+        if ((rc = ckpt_copy(lat, ck, false, false)) != HL_OK) return rc;
+        for (int k = 0; k < lat->nrot; ++k) HL_CUDA(lat, cudaMemsetAsync(lat->rot[k].dev.count, 0, 2 * sizeof(int), st));
+        if ((rc = fork_aux(lat)) != HL_OK) return rc;
+        for (int jj = 0; jj < L; ++jj) {
+            const long long t = ts + jj;
+            if ((rc = join_aux(lat)) != HL_OK) return rc;
+            if ((rc = small_copy(lat, ws + G.small + (size_t)jj * smb, t, true)) != HL_OK) return rc;
+            if ((rc = fork_aux(lat)) != HL_OK) return rc;
+            if (jj == L - 1) break;
+            StepArgs a = args_at(lat, t, buf(jj), buf(jj + 1));
+            if ((rc = issue_step(lat, a, false)) != HL_OK) return rc;
+        }
+        if ((rc = join_aux(lat)) != HL_OK) return rc;
+        // adjoint steps of the segment, last to first
+        for (int jj = L - 1; jj >= 0; --jj) {
+            const long long t = ts + jj;
+            char* sm = ws + G.small + (size_t)jj * smb;
+            if ((rc = small_copy(lat, sm, t, false)) != HL_OK) return rc;
+            StepArgs a = args_at(lat, t, buf(jj), buf(jj));
+            a.uplane_prev = reinterpret_cast<const float*>(sm);
+            a.tangent = 1;
+            const bool force_on = t >= t0 + T - na;
+            size_t o = align_up(plb);
+            for (int k = 0; k < lat->nrot; ++k) {
+                RotorDev& D = a.rot[k];
+                D.ddp = ra[k].ddp;
+                D.gub = ra[k].gub;
+                D.gS = ra[k].gS;
+                D.tape_utau = reinterpret_cast<const double*>(sm + o);
+                o += align_up(sizeof(double) * D.box_cells);
+                D.tape_active = reinterpret_cast<const uint8_t*>(sm + o);
+                o += align_up((size_t)D.box_cells);
+                D.gut_next = ra[k].gut[uc];
+                D.gut_prev = ra[k].gut[uc ^ 1];
+                D.pacc = ra[k].pacc;
+                D.wT = force_on ? (float)(w_thrust[k] / na) : 0.0f;
+                D.wQ = force_on ? (float)(w_torque[k] / na) : 0.0f;
+                HL_CUDA(lat, cudaMemsetAsync(lat->rot[k].dev.count, 0, 2 * sizeof(int), st));
+                // only this step's wall cells hand an adjoint to the previous step's u_tau
+                HL_CUDA(lat, cudaMemsetAsync(ra[k].gut[uc ^ 1], 0, sizeof(double) * D.box_cells, st));
+            }
+            if (lat->nrot > 0) {
+                a.part = 0;
+                HL_CUDA(lat, launch_band(Q, S, a, st));
+                if (lat->cfg.wall_model) HL_CUDA(lat, launch_wall(Q, S, a, st));
+            }
+            AdjArgs adj;
+            adj.lam_next = lam[ln];
+            adj.lam = lam[ln ^ 1];
+            adj.dJdd0 = d_dJ_dd0;
+            adj.gup_cur = gup[gc];
+            adj.gup_prev = gup[gc ^ 1];
+            HL_CUDA(lat, launch_adj(Q, S, a, adj, force_on, st));
+            ln ^= 1;
+            gc ^= 1;
+            uc ^= 1;
+        }
+    }
+    // the lattice ends where the forward pass ended
+    if ((rc = ckpt_copy(lat, ws + G.ck + (size_t)G.n_ck * ckb, false, true)) != HL_OK) return rc;
+    for (int k = 0; k < lat->nrot; ++k) HL_CUDA(lat, cudaMemsetAsync(lat->rot[k].dev.count, 0, 2 * sizeof(int), st));
+    for (int k = 0; k < lat->nrot; ++k) {
+        double pacc[PACC_SLOTS];
+        HL_CUDA(lat, cudaMemcpyAsync(pacc, ra[k].pacc, sizeof pacc, cudaMemcpyDeviceToHost, st));
+        HL_CUDA(lat, cudaStreamSynchronize(st));
+        double s = 0.0;
+        for (int i = 0; i < PACC_SLOTS; ++i) s += pacc[i];
+        if (dJ_dpitch) dJ_dpitch[k] = s;
+    }
+    return read_error_word(lat);
+}
+
+hl_status hl_set_d0(hl_lattice* lat, const float* d_d0) {
+    if (!lat) return HL_ERR_ARG;
+    lat->d0 = d_d0;
+    return HL_OK;
+}
+
+hl_status hl_set_pitch(hl_lattice* lat, int rotor, double pitch) {
+    if (!lat || rotor < 0 || rotor >= lat->nrot || !std::isfinite(pitch)) return HL_ERR_ARG;
+    lat->rot[rotor].pitch = pitch;
+    if (!lat->frozen) lat->rot[rotor].pitch_sets = pitch;
+    return HL_OK;
+}
+
+hl_status hl_freeze_sets(hl_lattice* lat, int on) {
+    if (!lat) return HL_ERR_ARG;
+    lat->frozen = on != 0;
+    for (int k = 0; k < lat->nrot; ++k) lat->rot[k].pitch_sets = lat->rot[k].pitch;
+    return HL_OK;
+}
+
+hl_status hl_debug_collide_vjp(int q, int n, const float* d_g_in, const float* d_d, const float* d_uB,
+                               const float* d_sigma, const float* d_S, double tau_mo, double c_smag,
+                               const float* d_lam_star, float* d_lam, float* d_gd, float* d_guB, float* d_gS,
+                               void* stream) {
+    if ((q != 19 && q != 27) || n < 0 || !d_g_in || !d_lam_star || !d_lam) return HL_ERR_ARG;
+    if (d_d && (!d_uB || !d_sigma || !d_S)) return HL_ERR_ARG;
+    if (n == 0) return HL_OK;
+    const float Ks = (float)(18.0 * std::sqrt(2.0) * c_smag * c_smag);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int blocks = (n + 127) / 128;
+    if (q == 19)
+        debug_collide_vjp_kernel<19><<<blocks, 128, 0, s>>>(n, d_g_in, d_d, d_uB, d_sigma, d_S, (float)tau_mo, Ks,
+                                                            d_lam_star, d_lam, d_gd, d_guB, d_gS);
+    else
+        debug_collide_vjp_kernel<27><<<blocks, 128, 0, s>>>(n, d_g_in, d_d, d_uB, d_sigma, d_S, (float)tau_mo, Ks,
+                                                            d_lam_star, d_lam, d_gd, d_guB, d_gS);
+    return cudaGetLastError() == cudaSuccess ? HL_OK : HL_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -17,7 +17,8 @@ enum ErrBits : unsigned { ERR_NONFINITE = 1u, ERR_MASS = 2u };
 
 struct StepArgs {
     void* f;                 // populations [Q][N], storage type
-    void* slot[27];          // f + s * N: base of slot s
+    void* slot[27];          // base of slot s of the pre-collision state (read)
+    void* wslot[27];         // base of slot s of the post-collision state (written; = slot in place)
     long long N;
     int n[3];
     int nxy, nplane;         // nx * ny; cells of an inlet/outlet plane
@@ -39,6 +40,8 @@ struct StepArgs {
     unsigned* err;
     int part;                // collide cells: 0 all, 1 outside every rotor box, 2 the box of part_rotor
     int part_rotor;
+    const float* d0;         // [N] static porosity multiplier, null = 1
+    int tangent;             // band kernel also writes d(porosity)/d(pitch) (reverse sweep)
     int nrot;
     RotorDev rot[MAXROT];
 };

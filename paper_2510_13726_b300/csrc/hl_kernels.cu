@@ -18,6 +18,7 @@
 //          of x + c_i.
 // Every memory location is read and written by the same thread, so one
 // buffer suffices and no synchronisation is needed inside the kernel.
+#include "hl_adjoint.cuh"
 #include "hl_internal.h"
 
 namespace hl {
@@ -43,6 +44,10 @@ __device__ __forceinline__ void make_offs(const StepArgs& a, int x, int y, int z
 template <int Q, int S>
 __device__ __forceinline__ typename Store<S>::T* slot_ptr(const StepArgs& a, int s) {
     return static_cast<typename Store<S>::T*>(a.slot[s]);
+}
+template <int Q, int S>
+__device__ __forceinline__ typename Store<S>::T* wslot_ptr(const StepArgs& a, int s) {
+    return static_cast<typename Store<S>::T*>(a.wslot[s]);
 }
 
 // pre-collision populations of a cell in the layout of phase PH (the
@@ -76,7 +81,7 @@ __device__ __forceinline__ int sel3(int ax, int a0, int a1, int a2) { return ax 
 // ---------------------------------------------------------------------------
 // fused collide and stream
 // ---------------------------------------------------------------------------
-template <int Q, int S, int PH>
+template <int Q, int S, int PH, bool D0>
 __global__ void __launch_bounds__(128) collide_kernel(const StepArgs a) {
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -118,9 +123,15 @@ __global__ void __launch_bounds__(128) collide_kernel(const StepArgs a) {
         if (rk >= 0) {
             const RotorDev& R = a.rot[rk];
             Band B;
-            B.d = R.d[bi];
+            B.d = D0 ? a.d0[cell] * R.d[bi] : R.d[bi];
             const uint8_t fl = R.flags[bi];
-            solid_velocity(R, x, y, z, B.uB);
+            // u^B is the rotor's velocity on its force cells; elsewhere in the
+            // box d = d0 (1 unless a static multiplier is set) with u^B = 0
+            if (fl & FL_B) {
+                solid_velocity(R, x, y, z, B.uB);
+            } else {
+                B.uB[0] = B.uB[1] = B.uB[2] = 0.0f;
+            }
             B.sigma = a.sigma_band;
 #pragma unroll
             for (int k = 0; k < 6; ++k) B.S[k] = 0.0f;
@@ -134,6 +145,15 @@ __global__ void __launch_bounds__(128) collide_kernel(const StepArgs a) {
                 for (int k = 0; k < 6; ++k) B.S[k] = wm[(3 + k) * bc];
                 B.sigma = 0.0f;
             }
+            rho = collide<Q, true>(g, B, a.tau_mo, a.Ksmag, u);
+        } else if (D0) {
+            // static porous medium at rest: d = d0, u^B = 0
+            Band B;
+            B.d = a.d0[cell];
+            B.uB[0] = B.uB[1] = B.uB[2] = 0.0f;
+            B.sigma = 1.0f;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) B.S[k] = 0.0f;
             rho = collide<Q, true>(g, B, a.tau_mo, a.Ksmag, u);
         } else {
             Band B0;
@@ -151,10 +171,10 @@ __global__ void __launch_bounds__(128) collide_kernel(const StepArgs a) {
 #pragma unroll
         for (int s = 0; s < Q; ++s) {
             if (PH == 0) {
-                Store<S>::st(slot_ptr<Q, S>(a, oslot(Q, s)) + cell, g[s]);
+                Store<S>::st(wslot_ptr<Q, S>(a, oslot(Q, s)) + cell, g[s]);
             } else {
                 const int cx = cslot(Q, s, 0), cy = cslot(Q, s, 1), cz = cslot(Q, s, 2);
-                Store<S>::st(slot_ptr<Q, S>(a, s) + (o.x[1 + cx] + o.y[1 + cy] + o.z[1 + cz]), g[s]);
+                Store<S>::st(wslot_ptr<Q, S>(a, s) + (o.x[1 + cx] + o.y[1 + cy] + o.z[1 + cz]), g[s]);
             }
         }
         return;
@@ -187,12 +207,12 @@ __global__ void __launch_bounds__(128) collide_kernel(const StepArgs a) {
 #pragma unroll
     for (int s = 0; s < Q; ++s) {
         if (PH == 0) {
-            Store<S>::st(slot_ptr<Q, S>(a, oslot(Q, s)) + cell, g[s]);
+            Store<S>::st(wslot_ptr<Q, S>(a, oslot(Q, s)) + cell, g[s]);
         } else {
             const int cx = cslot(Q, s, 0), cy = cslot(Q, s, 1), cz = cslot(Q, s, 2);
             const int cas = sel3(ax, cx, cy, cz);
             if ((inlet && cas < 0) || (outlet && cas > 0)) continue;
-            Store<S>::st(slot_ptr<Q, S>(a, s) + (o.x[1 + cx] + o.y[1 + cy] + o.z[1 + cz]), g[s]);
+            Store<S>::st(wslot_ptr<Q, S>(a, s) + (o.x[1 + cx] + o.y[1 + cy] + o.z[1 + cz]), g[s]);
         }
     }
 }
@@ -233,20 +253,30 @@ __global__ void __launch_bounds__(BAND_THREADS) band_kernel(const StepArgs a) {
             const float rx = (float)x - R.cf[0], ry = (float)y - R.cf[1], rz = (float)z - R.cf[2];
             const float ra = R.axis == 0 ? rx : (R.axis == 1 ? ry : rz);
             const float rr = rx * rx + ry * ry + rz * rz - ra * ra;
+            float dd = 0.0f;
             if (rr <= R.reach_plane2 && fabsf(ra) <= R.reach_axial) {
-                phi = rotor_phi(R, x, y, z, which);
+                phi = rotor_phi(R, R.cpD, R.spD, x, y, z, which);
                 if (phi < a.eps_half) {
                     fl |= FL_B;
+                    if (phi >= 0.0f) fl |= FL_W;
+                    // sets frozen: porosity and wall distance of the same component at the current pitch
+                    if (R.frozen) phi = component_phi(R, which, x, y, z);
                     if (phi <= -a.eps_half) {
                         d = 0.0f;
-                    } else {
+                    } else if (phi < a.eps_half) {
                         const float tt = phi * a.inv_eps + 0.5f;
                         d = a.transition ? tt : tt * tt * (3.0f - 2.0f * tt);
+                        if (a.tangent) {
+                            float dphi;
+                            component_phi_tan(R, which, x, y, z, dphi);
+                            const float ds = a.transition ? a.inv_eps : 6.0f * tt * (1.0f - tt) * a.inv_eps;
+                            dd = ds * dphi;
+                        }
                     }
-                    if (phi >= 0.0f) fl |= FL_W;
                 }
             }
             R.d[bi] = d;
+            if (a.tangent) R.ddp[bi] = dd;
             R.flags[bi] = fl;
             isB = (fl & FL_B) != 0;
             isW = a.wall_model && (fl & FL_W);
@@ -397,11 +427,11 @@ __global__ void __launch_bounds__(256) force_kernel(const StepArgs a) {
             const int nbx = o.x[1 + c0] + o.y[1 + c1] + o.z[1 + c2];
             float out_s, in_o;   // f*_s(x) and f*_o(x + c_s)
             if (PH == 0) {
-                out_s = Store<S>::ld(slot_ptr<Q, S>(a, o_s) + cell);
-                in_o = Store<S>::ld(slot_ptr<Q, S>(a, s) + nbx);
+                out_s = Store<S>::ld(wslot_ptr<Q, S>(a, o_s) + cell);
+                in_o = Store<S>::ld(wslot_ptr<Q, S>(a, s) + nbx);
             } else {
-                out_s = Store<S>::ld(slot_ptr<Q, S>(a, s) + nbx);
-                in_o = Store<S>::ld(slot_ptr<Q, S>(a, o_s) + cell);
+                out_s = Store<S>::ld(wslot_ptr<Q, S>(a, s) + nbx);
+                in_o = Store<S>::ld(wslot_ptr<Q, S>(a, o_s) + cell);
             }
             Fc[0] += (float(-c0) - us[0]) * in_o - (float(c0) - us[0]) * out_s;
             Fc[1] += (float(-c1) - us[1]) * in_o - (float(c1) - us[1]) * out_s;
@@ -604,8 +634,13 @@ static cudaError_t launch_collide_t(const StepArgs& a, cudaStream_t s) {
     const int* n = a.part == 2 ? a.rot[a.part_rotor].n : a.n;
     const dim3 blk = cell_block(n[0]);
     const dim3 grd((n[0] + blk.x - 1) / blk.x, (n[1] + blk.y - 1) / blk.y, n[2]);
-    if (a.phase == 0) collide_kernel<Q, S, 0><<<grd, blk, 0, s>>>(a);
-    else collide_kernel<Q, S, 1><<<grd, blk, 0, s>>>(a);
+    if (a.d0) {
+        if (a.phase == 0) collide_kernel<Q, S, 0, true><<<grd, blk, 0, s>>>(a);
+        else collide_kernel<Q, S, 1, true><<<grd, blk, 0, s>>>(a);
+    } else {
+        if (a.phase == 0) collide_kernel<Q, S, 0, false><<<grd, blk, 0, s>>>(a);
+        else collide_kernel<Q, S, 1, false><<<grd, blk, 0, s>>>(a);
+    }
     return cudaGetLastError();
 }
 

@@ -231,6 +231,61 @@ class Lattice:
         with torch.cuda.device(self.device):
             self._check(lib().hl_load_state(self._h, buf.data_ptr(), buf.numel()))
 
+    # -- gradients ------------------------------------------------------------
+    def set_d0(self, d0):
+        """Static porosity multiplier d0 (device tensor of N or (nz, ny, nx) floats; None = 1).
+        The tensor is kept alive by the lattice while set."""
+        import torch
+        if d0 is None:
+            self._d0 = None
+            self._check(lib().hl_set_d0(self._h, None))
+            return
+        t = torch.as_tensor(d0, dtype=torch.float32, device=self.device).contiguous().view(-1)
+        if t.numel() != self.N:
+            raise ValueError("d0 must have one value per cell")
+        self._d0 = t
+        self._check(lib().hl_set_d0(self._h, t.data_ptr()))
+
+    def set_pitch(self, k: int, pitch: float):
+        self._check(lib().hl_set_pitch(self._h, int(k), float(pitch)))
+
+    def freeze_sets(self, on: bool = True):
+        """Hold the cell sets at the current pitches (finite-difference checks)."""
+        self._check(lib().hl_freeze_sets(self._h, int(bool(on))))
+
+    def grad_workspace_size(self, steps: int, ckpt_every: int) -> int:
+        s = C.c_size_t()
+        self._check(lib().hl_grad_workspace_size(self._h, int(steps), int(ckpt_every), C.byref(s)))
+        return s.value
+
+    def grad(self, steps: int, avg_last: int, w_thrust, w_torque, ckpt_every: int = 100, want_d0: bool = True,
+             work=None):
+        """Run `steps` steps and return (J, dJ/dpitch (nrot,), dJ/dd0 (nz, ny, nx) device tensor or None)
+        for J = mean over the last avg_last steps of sum_k wT_k F_k.a_k + wQ_k M_k.a_k."""
+        import torch
+        wT = np.zeros(max(1, self.nrot))
+        wQ = np.zeros(max(1, self.nrot))
+        wT[:self.nrot] = w_thrust
+        wQ[:self.nrot] = w_torque
+        nbytes = self.grad_workspace_size(steps, ckpt_every)
+        with torch.cuda.device(self.device):
+            if work is None:
+                buf, ptr = _aligned_bytes(nbytes, self.device)
+            else:
+                buf, ptr = work, work.data_ptr()
+                if ptr % _ALIGN or work.numel() * work.element_size() < nbytes:
+                    raise ValueError("gradient workspace too small or not 256-byte aligned")
+            gd0 = torch.empty(self.N, dtype=torch.float32, device=self.device) if want_d0 else None
+            J = C.c_double()
+            gp = np.zeros(max(1, self.nrot))
+            self._check(lib().hl_grad(self._h, int(steps), int(avg_last), int(ckpt_every),
+                                      wT.ctypes.data_as(C.POINTER(C.c_double)),
+                                      wQ.ctypes.data_as(C.POINTER(C.c_double)), C.byref(J),
+                                      gp.ctypes.data_as(C.POINTER(C.c_double)),
+                                      None if gd0 is None else gd0.data_ptr(), C.c_void_p(ptr), nbytes))
+        del buf
+        return J.value, gp[:self.nrot], (None if gd0 is None else gd0.view(self.shape))
+
     @classmethod
     def from_workload(cls, wl, storage="f32", q=None, rotor_kw=None, **overrides):
         """Lattice and rotors of a ``workloads.Workload``."""

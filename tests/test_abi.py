@@ -24,7 +24,7 @@ def L():
 def _declared():
     txt = open(os.path.join(ROOT, "include", "hlbm.h")).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(hl_[a-z_]+)\s*\(", txt)))
+    return sorted(set(re.findall(r"\b(hl_[a-z0-9_]+)\s*\(", txt)))
 
 
 def test_every_declared_symbol_is_exported_and_bound(L):

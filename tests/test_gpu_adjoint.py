@@ -1,0 +1,237 @@
+"""Parity of the CUDA discrete adjoint (hl_grad) with the FP64 oracle's
+adjoint, and of the forward extensions it relies on (static porosity
+multiplier d0, frozen cell sets).
+
+The oracle differentiates by complex step (pinned against finite
+differences in test_oracle_adjoint.py); the CUDA path uses a hand-derived
+FP32 vector-Jacobian product of the collision, a hand-derived reverse pass
+of the wall model with FP64 forward-mode Newton derivatives, and FP32 pitch
+tangents of the geometry.  Tolerances: FP32 rounding of the forward state
+and of the adjoint arithmetic: 1e-4 relative on the gradients (observed
+a few 1e-6).
+"""
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("a CUDA device is required for the gpu-marked tests")
+    from paper_2510_13726_b300.build import build
+    build()
+    import paper_2510_13726_b300 as pkg
+    return pkg
+
+
+def _perm_to_oracle(q, P):
+    c, _ = P.velocity_set(q)
+    co, _, _ = O.lattice(q)
+    idx = {tuple(v): i for i, v in enumerate(co)}
+    return np.array([idx[tuple(v)] for v in c])
+
+
+@pytest.mark.parametrize("q", [19, 27])
+@pytest.mark.parametrize("branch", ["bulk", "band", "wall"])
+def test_collision_vjp_unit_parity(P, q, branch):
+    """hl_debug_collide_vjp against the oracle's complex-step VJP on 4096
+    random cells (FP32 inputs seen exactly by both sides)."""
+    import torch
+    c, w = P.velocity_set(q)
+    perm = _perm_to_oracle(q, P)
+    inv = np.argsort(perm)
+    n = 4096
+    f = W.random_populations(31 + q, n, w, amplitude=0.1)
+    g32 = (f - w).astype(np.float32)
+    fin = w + g32.astype(np.float64)
+    rng = np.random.default_rng(9)
+    lam = rng.normal(0, 1, (n, q)).astype(np.float32)
+    tau_mo, cs = 0.52, 0.1
+    dev = "cuda"
+    gin = torch.tensor(g32, device=dev)
+    lin = torch.tensor(lam, device=dev)
+    lout = torch.empty_like(lin)
+    gd = torch.empty(n, device=dev)
+    gu = torch.empty(n, 3, device=dev)
+    gS = torch.empty(n, 6, device=dev)
+    kw = {}
+    if branch == "bulk":
+        args = [0, 0, 0, 0]
+    else:
+        d = rng.uniform(0, 1, n).astype(np.float32)
+        d[:256] = 0.0
+        d[256:512] = 1.0
+        uB = rng.uniform(-0.3, 0.3, (n, 3)).astype(np.float32)
+        sig = (np.ones(n) if branch == "band" else np.zeros(n)).astype(np.float32)
+        S6 = (rng.normal(size=(n, 6)) * 1e-3).astype(np.float32)
+        td = [torch.tensor(a, device=dev).contiguous() for a in (d, uB, sig, S6)]
+        args = [t.data_ptr() for t in td]
+        S33 = np.zeros((n, 3, 3))
+        for k, (a, b) in enumerate([(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]):
+            S33[:, a, b] = S33[:, b, a] = S6[:, k]
+        kw = dict(d=d.astype(np.float64), uB=uB.astype(np.float64), sigma=sig.astype(np.float64), Sfd=S33)
+    rc = P.lib().hl_debug_collide_vjp(q, n, gin.data_ptr(), *args, tau_mo, cs, lin.data_ptr(), lout.data_ptr(),
+                                      gd.data_ptr(), gu.data_ptr(), gS.data_ptr(),
+                                      torch.cuda.current_stream().cuda_stream)
+    assert rc == 0
+    torch.cuda.synchronize()
+    lf_o, gd_o, gu_o, gS_o = O.collide_vjp_cells(q, fin[:, inv], lam.astype(np.float64)[:, inv],
+                                                 tau_mo=tau_mo, c_smag=cs, **kw)
+    lf_o = lf_o[:, perm]
+    lf = lout.cpu().numpy().astype(np.float64)
+    scale = np.abs(lf_o).max()
+    assert np.abs(lf - lf_o).max() <= 2e-5 * scale, np.abs(lf - lf_o).max() / scale
+    gdg = gd.cpu().numpy().astype(np.float64)
+    assert np.abs(gdg - gd_o).max() <= 2e-5 * max(1e-3, np.abs(gd_o).max())
+    if branch != "bulk":
+        gug = gu.cpu().numpy().astype(np.float64)
+        assert np.abs(gug - gu_o).max() <= 2e-5 * max(1e-3, np.abs(gu_o).max())
+        gSg = gS.cpu().numpy().astype(np.float64)
+        want = np.stack([gS_o[:, 0, 0], gS_o[:, 1, 1], gS_o[:, 2, 2], gS_o[:, 0, 1] + gS_o[:, 1, 0],
+                         gS_o[:, 0, 2] + gS_o[:, 2, 0], gS_o[:, 1, 2] + gS_o[:, 2, 1]], 1)
+        assert np.abs(gSg - want).max() <= 2e-5 * max(1e-3, np.abs(want).max())
+
+
+def _wl():
+    return W.workload("rotor48_adj")
+
+
+def _rel_l2(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def test_forward_with_d0_and_frozen_sets_matches_oracle(P):
+    """Forward extensions used by the gradient checks: a static porosity
+    field d0 and a pitch change with the cell sets frozen."""
+    import torch
+    wl = _wl()
+    rng = np.random.default_rng(3)
+    d0 = 1.0 - 0.3 * rng.uniform(0, 1, (wl.nz, wl.ny, wl.nx))
+    d0 = d0.astype(np.float32)
+    lat = P.Lattice.from_workload(wl)
+    o = O.from_workload(wl)
+    lat.set_d0(torch.tensor(d0, device=lat.device))
+    o.set_d0(d0.astype(np.float64))
+    lat.freeze_sets(True)
+    o.freeze_sets(True)
+    lat.set_pitch(0, 0.05)
+    o.set_pitch(0, 0.05)
+    lat.step(12)
+    o.step(12)
+    rg, ug = (a.cpu().numpy().astype(np.float64) for a in lat.fields())
+    ro, uo = o.fields()
+    assert _rel_l2(ug[:, 1:-1], uo[:, 1:-1]) <= 1e-5
+    assert np.linalg.norm((rg - ro)[1:-1]) / np.linalg.norm(ro[1:-1]) <= 1e-5
+    Fg, _ = lat.forces()
+    Fo, _, _, _ = o.forces()
+    assert np.abs(Fg - Fo).max() <= 1e-3 * np.abs(Fo).max()
+
+
+@pytest.mark.parametrize("wall_model", [True, False])
+def test_gradient_parity_with_oracle(P, wall_model):
+    """J, dJ/dpitch and dJ/dd0 of J = mean over the last 8 of 16 steps of
+    thrust - 0.3 torque, checkpoints every 5 steps, against the oracle."""
+    import torch
+    wl = _wl()
+    T, navg, wT, wQ = 16, 8, 1.0, -0.3
+    lat = P.Lattice.from_workload(wl, wall_model=wall_model)
+    Jg, gpg, gdg = lat.grad(T, navg, [wT], [wQ], ckpt_every=5)
+    gdg = gdg.cpu().numpy().astype(np.float64)
+    o = O.from_workload(wl, wall_model=wall_model)
+    Jo, gpo, gdo = o.adjoint(T, navg, [wT], [wQ])
+    print(f"J {Jg:.8e} vs {Jo:.8e}; dJ/dpitch {gpg[0]:.8e} vs {gpo[0]:.8e}; "
+          f"dJ/dd0 rel L2 {_rel_l2(gdg, gdo):.2e}")
+    # observed: J 4e-7, dJ/dpitch 5e-6, dJ/dd0 4e-6 (wall model on)
+    assert abs(Jg - Jo) <= 1e-5 * abs(Jo)
+    assert abs(gpg[0] - gpo[0]) <= 1e-4 * abs(gpo[0])
+    assert _rel_l2(gdg, gdo) <= 1e-4
+    # the lattice ends where hl_step(T) would leave it
+    ref = P.Lattice.from_workload(wl, wall_model=wall_model)
+    ref.step(T)
+    r1, u1 = lat.fields()
+    r2, u2 = ref.fields()
+    assert torch.equal(r1, r2) and torch.equal(u1, u2)
+    assert lat.t == T
+
+
+def test_gradient_independent_of_checkpoint_spacing(P):
+    """The segment recomputation reproduces the forward states: the gradient
+    with a checkpoint every step, every 5 steps and one checkpoint agree."""
+    wl = _wl()
+    out = []
+    for K in (1, 5, 16):
+        lat = P.Lattice.from_workload(wl)
+        J, gp, gd = lat.grad(16, 8, [1.0], [0.5], ckpt_every=K)
+        out.append((J, gp[0], gd.cpu().numpy().astype(np.float64)))
+    for J, gp, gd in out[1:]:
+        assert J == out[0][0]
+        assert abs(gp - out[0][1]) <= 1e-6 * abs(out[0][1])
+        assert _rel_l2(gd, out[0][2]) <= 1e-6
+
+
+def test_gradient_against_gpu_finite_differences(P):
+    """dJ/dpitch against central differences of the CUDA forward itself
+    (h = 1e-3 rad, cell sets frozen) and dJ/dd0 at cells around the rotor
+    (h = 1e-2 on d0)."""
+    import torch
+    wl = _wl()
+    T, navg, wT, wQ = 16, 8, 1.0, 0.5
+    lat = P.Lattice.from_workload(wl)
+    J0, gp, gd = lat.grad(T, navg, [wT], [wQ], ckpt_every=8)
+    gd = gd.cpu().numpy()
+
+    def J(pitch=0.0, d0=None):
+        m = P.Lattice.from_workload(wl)
+        if d0 is not None:
+            m.set_d0(torch.tensor(d0, device=m.device))
+        m.freeze_sets(True)
+        m.set_pitch(0, pitch)
+        m.step(T - navg)
+        m.forces(reset_avg=True)
+        m.step(navg)
+        _, Fa = m.forces()
+        _, Ma = m.moments()
+        return wT * Fa[0, 2] + wQ * Ma[0, 2]
+
+    h = 1e-3
+    fd = (J(h) - J(-h)) / (2 * h)
+    print("dJ/dpitch adjoint", gp[0], "FD", fd)
+    assert abs(gp[0] - fd) <= 5e-3 * abs(fd)
+    rng = np.random.default_rng(4)
+    c = wl.rotors[0].center
+    worst = 0.0
+    for _ in range(6):
+        cell = (int(c[2] + rng.integers(-6, 7)), int(c[1] + rng.integers(-12, 13)), int(c[0] + rng.integers(-12, 13)))
+        e = np.ones((wl.nz, wl.ny, wl.nx), dtype=np.float32)
+        hd = 1e-2
+        e[cell] = 1.0 + hd
+        Jp = J(d0=e)
+        e[cell] = 1.0 - hd
+        Jm = J(d0=e)
+        fdd = (Jp - Jm) / (2 * hd)
+        worst = max(worst, abs(gd[cell] - fdd) / max(abs(fdd), 1e-3 * abs(gp[0])))
+    assert worst <= 2e-2, worst
+
+
+def test_rotor_objective_autograd(P):
+    """torch.autograd through rotor_objective equals hl_grad with the same weights."""
+    import torch
+    wl = _wl()
+    lat = P.Lattice.from_workload(wl)
+    pitch = torch.zeros(1, dtype=torch.float64, requires_grad=True)
+    d0 = torch.ones(wl.nz, wl.ny, wl.nx, device=lat.device, requires_grad=True)
+    T, Qv = P.rotor_objective(lat, pitch, d0, steps=12, avg_last=6, ckpt_every=4)
+    (T.sum() - 0.2 * Qv.sum()).backward()
+    ref = P.Lattice.from_workload(wl)
+    ref.set_d0(torch.ones(wl.nz, wl.ny, wl.nx, device=ref.device))
+    Jr, gpr, gdr = ref.grad(12, 6, [1.0], [-0.2], ckpt_every=4)
+    assert abs(float(T[0] - 0.2 * Qv[0]) - Jr) <= 1e-9 * abs(Jr)
+    assert abs(float(pitch.grad[0]) - gpr[0]) <= 1e-6 * abs(gpr[0])
+    assert _rel_l2(d0.grad.cpu().numpy().astype(np.float64), gdr.cpu().numpy().astype(np.float64)) <= 1e-6

@@ -120,9 +120,9 @@ def _make() -> dict:
         "rotor128_adj", 128, 128, 256, steps=4000,
         rotors=_single(128, 128, 256, 32.0, 6.0),
         note="D3Q19 R=32, 4000 steps, checkpoint every 100 (gradient study)")
-    w["rotor32_adj"] = Workload(
-        "rotor32_adj", 32, 32, 64, steps=16, rotors=_single(32, 32, 64, 10.0, 6.0),
-        note="D3Q19 R=10, 16 steps (gradient checks at oracle size)")
+    w["rotor48_adj"] = Workload(
+        "rotor48_adj", 48, 48, 64, steps=16, rotors=_single(48, 48, 64, 10.0, 6.0),
+        note="D3Q19 48x48x64, R=10, 16 steps (gradient checks at oracle size)")
     w["farm"] = Workload(
         "farm", 1536, 512, 1024, flow_axis=0, steps=1000, turbulence=0.05,
         rotors=_farm(0),
