@@ -40,6 +40,8 @@ typedef int hl_status;
 #define HL_ERR_WORKSPACE (-4)   /* workspace or buffer smaller than required */
 #define HL_ERR_STATE (-5)       /* call not valid in the current state */
 #define HL_ERR_MASS (-8)        /* total mass drifted beyond mass_tol */
+#define HL_ERR_GEOMETRY (-9)    /* a wall-model sample point left its rotor's box: the blade
+                                   grid needs more padding (the cell was left unmodelled) */
 
 #define HL_STORE_F32 0          /* populations stored as FP32 of f_i - w_i */
 #define HL_STORE_F16S 1         /* populations stored as FP16 of f_i - w_i */
@@ -151,7 +153,7 @@ hl_status hl_set_rotor(hl_lattice* lat, int* rotor_id, const hl_rotor_geometry* 
  * embedding of every rotor box and wall model on the wall cells; fused
  * collide-and-stream; momentum-exchange force and torque per rotor; evolve
  * the rotor angle.  Then synchronises the stream and reports the device
- * error word (HL_ERR_NONFINITE, HL_ERR_MASS; sticky until hl_load_state or
+ * error word (HL_ERR_NONFINITE, HL_ERR_MASS, HL_ERR_GEOMETRY; sticky until hl_load_state or
  * hl_lattice_init). */
 hl_status hl_step(hl_lattice* lat, int n);
 

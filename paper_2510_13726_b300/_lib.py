@@ -12,7 +12,7 @@ LIBPATH = os.path.join(HERE, "libhlbm.so")
 
 HL_OK = 0
 STATUS = {0: "HL_OK", -1: "HL_ERR_ARG", -2: "HL_ERR_CUDA", -3: "HL_ERR_NONFINITE",
-          -4: "HL_ERR_WORKSPACE", -5: "HL_ERR_STATE", -8: "HL_ERR_MASS"}
+          -4: "HL_ERR_WORKSPACE", -5: "HL_ERR_STATE", -8: "HL_ERR_MASS", -9: "HL_ERR_GEOMETRY"}
 STORAGE = {"f32": 0, "f16s": 1, "bf16s": 2}
 
 _dp = C.POINTER(C.c_double)

@@ -389,19 +389,26 @@ __device__ __forceinline__ D3 operator-(const D3& x, const D3& y) {
 __device__ __forceinline__ D3 operator*(const D3& x, const D3& y) {
     return dmk(x.v * y.v, x.d[0] * y.v + x.v * y.d[0], x.d[1] * y.v + x.v * y.d[1], x.d[2] * y.v + x.v * y.d[2]);
 }
+// the value is divided as in the plain solve (same rounding, same stopping
+// decisions); the derivative parts use one reciprocal
 __device__ __forceinline__ D3 operator/(const D3& x, const D3& y) {
     const double q = x.v / y.v;
-    return dmk(q, (x.d[0] - q * y.d[0]) / y.v, (x.d[1] - q * y.d[1]) / y.v, (x.d[2] - q * y.d[2]) / y.v);
+    const double r = 1.0 / y.v;
+    return dmk(q, (x.d[0] - q * y.d[0]) * r, (x.d[1] - q * y.d[1]) * r, (x.d[2] - q * y.d[2]) * r);
 }
 __device__ __forceinline__ D3 operator*(double s, const D3& x) { return dmk(s * x.v, s * x.d[0], s * x.d[1], s * x.d[2]); }
-__device__ __forceinline__ D3 operator/(const D3& x, double s) { return dmk(x.v / s, x.d[0] / s, x.d[1] / s, x.d[2] / s); }
+__device__ __forceinline__ D3 operator/(const D3& x, double s) {
+    const double r = 1.0 / s;
+    return dmk(x.v / s, x.d[0] * r, x.d[1] * r, x.d[2] * r);
+}
 __device__ __forceinline__ D3 operator+(double s, const D3& x) { return dmk(s + x.v, x.d[0], x.d[1], x.d[2]); }
 __device__ __forceinline__ D3 dexp(const D3& x) {
     const double e = exp(x.v);
     return dmk(e, e * x.d[0], e * x.d[1], e * x.d[2]);
 }
 __device__ __forceinline__ D3 dlog(const D3& x) {
-    return dmk(log(x.v), x.d[0] / x.v, x.d[1] / x.v, x.d[2] / x.v);
+    const double r = 1.0 / x.v;
+    return dmk(log(x.v), x.d[0] * r, x.d[1] * r, x.d[2] * r);
 }
 __device__ __forceinline__ D3 dsqrt(const D3& x) {
     const double s = sqrt(x.v);

@@ -115,6 +115,8 @@ hl_status read_error_word(hl_lattice* lat) {
     HL_CUDA(lat, cudaStreamSynchronize(lat->stream));
     if (e & ERR_NONFINITE) return fail(lat, HL_ERR_NONFINITE, "non-finite density on the device");
     if (e & ERR_MASS) return fail(lat, HL_ERR_MASS, "total mass drifted beyond mass_tol");
+    if (e & ERR_GEOMETRY)
+        return fail(lat, HL_ERR_GEOMETRY, "a wall-model sample left the rotor box: pad the blade grid");
     return HL_OK;
 }
 

@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(128) adj_wall_kernel(const StepArgs a, const A
     int count = *((volatile int*)(R.count + 1));
     if ((long long)count > R.box_cells) count = (int)R.box_cells;
     const long long N = a.N, BC = R.box_cells;
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < count; idx += gridDim.x * blockDim.x) {
+    for (int idx = list_first(); idx < count; idx += list_stride()) {
         const long long bi = R.wlist[idx];
         const float phi = R.wphi[idx];
         const int which = R.wwhich[idx];
@@ -320,6 +320,12 @@ __global__ void __launch_bounds__(128) adj_wall_kernel(const StepArgs a, const A
                 if (i0[k] > a.n[k] - 2) { i0[k] = a.n[k] - 2; t[k] = 1.f; clamped[k] = true; }
             }
         }
+        R.gut_prev[bi] = 0.0;
+        bool inside = true;
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            inside = inside && i0[k] - R.lo[k] >= 0 && i0[k] + 1 - R.lo[k] < R.n[k];
+        if (!inside) continue;   // the forward left this cell unmodelled (error word set)
         int cidx[8];
         float uc[8][3], irho[8];
         float us[3] = {0.f, 0.f, 0.f};
@@ -348,7 +354,6 @@ __global__ void __launch_bounds__(128) adj_wall_kernel(const StepArgs a, const A
         const float un = ur[0] * n[0] + ur[1] * n[1] + ur[2] * n[2];
         const float ut[3] = {ur[0] - un * n[0], ur[1] - un * n[1], ur[2] - un * n[2]};
         const float utm = sqrtf(ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2]);
-        R.gut_prev[bi] = 0.0;
         if (!(utm >= 1e-12f)) continue;   // the forward left this cell inactive
         const float th[3] = {ut[0] / utm, ut[1] / utm, ut[2] / utm};
         // forward Newton solves with derivatives along (|u_t|, y_sample, start value)
@@ -481,19 +486,24 @@ dim3 cell_block(int nx) {
     return dim3(bx, 128 / bx >= 1 ? 128 / bx : 1, 1);
 }
 
+// cells outside every rotor box (and the open planes)
 template <int Q, int S>
-cudaError_t launch_adj_t(const StepArgs& a, const AdjArgs& j, bool force_on, cudaStream_t s) {
-    {
-        const dim3 blk = cell_block(a.n[0]);
-        const dim3 grd((a.n[0] + blk.x - 1) / blk.x, (a.n[1] + blk.y - 1) / blk.y, a.n[2]);
-        if (a.d0) {
-            if (a.phase == 0) adj_bulk_kernel<Q, S, 0, true><<<grd, blk, 0, s>>>(a, j);
-            else adj_bulk_kernel<Q, S, 1, true><<<grd, blk, 0, s>>>(a, j);
-        } else {
-            if (a.phase == 0) adj_bulk_kernel<Q, S, 0, false><<<grd, blk, 0, s>>>(a, j);
-            else adj_bulk_kernel<Q, S, 1, false><<<grd, blk, 0, s>>>(a, j);
-        }
+cudaError_t launch_adj_bulk_t(const StepArgs& a, const AdjArgs& j, cudaStream_t s) {
+    const dim3 blk = cell_block(a.n[0]);
+    const dim3 grd((a.n[0] + blk.x - 1) / blk.x, (a.n[1] + blk.y - 1) / blk.y, a.n[2]);
+    if (a.d0) {
+        if (a.phase == 0) adj_bulk_kernel<Q, S, 0, true><<<grd, blk, 0, s>>>(a, j);
+        else adj_bulk_kernel<Q, S, 1, true><<<grd, blk, 0, s>>>(a, j);
+    } else {
+        if (a.phase == 0) adj_bulk_kernel<Q, S, 0, false><<<grd, blk, 0, s>>>(a, j);
+        else adj_bulk_kernel<Q, S, 1, false><<<grd, blk, 0, s>>>(a, j);
     }
+    return cudaGetLastError();
+}
+
+// the rotor boxes, then the wall-model reverse pass
+template <int Q, int S>
+cudaError_t launch_adj_box_t(const StepArgs& a, const AdjArgs& j, bool force_on, cudaStream_t s) {
     for (int k = 0; k < a.nrot; ++k) {
         const int* n = a.rot[k].n;
         const dim3 blk = cell_block(n[0]);
@@ -509,20 +519,28 @@ cudaError_t launch_adj_t(const StepArgs& a, const AdjArgs& j, bool force_on, cud
     }
     if (a.nrot > 0 && a.wall_model) {
         const dim3 grd(WALL_BLOCKS, a.nrot);
-        if (a.phase == 0) adj_wall_kernel<Q, S, 0><<<grd, 128, 0, s>>>(a, j);
-        else adj_wall_kernel<Q, S, 1><<<grd, 128, 0, s>>>(a, j);
+        if (a.phase == 0) adj_wall_kernel<Q, S, 0><<<grd, WALL_THREADS, 0, s>>>(a, j);
+        else adj_wall_kernel<Q, S, 1><<<grd, WALL_THREADS, 0, s>>>(a, j);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_adj(int Q, int S, const StepArgs& a, const AdjArgs& j, bool force_on, cudaStream_t s) {
-    if (Q == 19 && S == ST_F32) return launch_adj_t<19, ST_F32>(a, j, force_on, s);
-    if (Q == 19 && S == ST_F16S) return launch_adj_t<19, ST_F16S>(a, j, force_on, s);
-    if (Q == 19 && S == ST_BF16S) return launch_adj_t<19, ST_BF16S>(a, j, force_on, s);
-    if (Q == 27 && S == ST_F32) return launch_adj_t<27, ST_F32>(a, j, force_on, s);
-    if (Q == 27 && S == ST_F16S) return launch_adj_t<27, ST_F16S>(a, j, force_on, s);
-    if (Q == 27 && S == ST_BF16S) return launch_adj_t<27, ST_BF16S>(a, j, force_on, s);
-    return cudaErrorInvalidValue;
+#define HL_ADJ_DISPATCH(Q, S, FN, ...)                                        \
+    do {                                                                      \
+        if (Q == 19 && S == ST_F32) return FN<19, ST_F32>(__VA_ARGS__);       \
+        if (Q == 19 && S == ST_F16S) return FN<19, ST_F16S>(__VA_ARGS__);     \
+        if (Q == 19 && S == ST_BF16S) return FN<19, ST_BF16S>(__VA_ARGS__);   \
+        if (Q == 27 && S == ST_F32) return FN<27, ST_F32>(__VA_ARGS__);       \
+        if (Q == 27 && S == ST_F16S) return FN<27, ST_F16S>(__VA_ARGS__);     \
+        if (Q == 27 && S == ST_BF16S) return FN<27, ST_BF16S>(__VA_ARGS__);   \
+        return cudaErrorInvalidValue;                                         \
+    } while (0)
+
+cudaError_t launch_adj_bulk(int Q, int S, const StepArgs& a, const AdjArgs& j, cudaStream_t s) {
+    HL_ADJ_DISPATCH(Q, S, launch_adj_bulk_t, a, j, s);
+}
+cudaError_t launch_adj_box(int Q, int S, const StepArgs& a, const AdjArgs& j, bool force_on, cudaStream_t s) {
+    HL_ADJ_DISPATCH(Q, S, launch_adj_box_t, a, j, force_on, s);
 }
 
 }  // namespace
@@ -554,14 +572,27 @@ size_t ckpt_bytes(const hl_lattice* lat) {
 
 // per step of a segment: the outlet velocity read by the step and the
 // wall-model state at its start
-size_t small_bytes(const hl_lattice* lat) {
+// layout of one step's tape entry: outlet plane | per rotor: u_tau, active
+// (at the start of the step), wall-model output of the step [9][box]
+struct SmallOff {
+    size_t utau[MAXROT], active[MAXROT], wm[MAXROT];
+};
+
+size_t small_layout(const hl_lattice* lat, SmallOff* so) {
     size_t o = align_up(sizeof(float) * 3 * plane_cells(lat->cfg));
     for (int k = 0; k < lat->nrot; ++k) {
-        o += align_up(sizeof(double) * lat->rot[k].dev.box_cells);
-        o += align_up((size_t)lat->rot[k].dev.box_cells);
+        const long long b = lat->rot[k].dev.box_cells;
+        if (so) so->utau[k] = o;
+        o += align_up(sizeof(double) * b);
+        if (so) so->active[k] = o;
+        o += align_up((size_t)b);
+        if (so) so->wm[k] = o;
+        o += align_up(sizeof(float) * 9 * b);
     }
     return o;
 }
+
+size_t small_bytes(const hl_lattice* lat) { return small_layout(lat, nullptr); }
 
 size_t rotor_adj_bytes(const hl_lattice* lat, int k) {
     const long long b = lat->rot[k].dev.box_cells;
@@ -622,24 +653,33 @@ hl_status ckpt_copy(hl_lattice* lat, char* ck, bool save, bool with_pops) {
     return HL_OK;
 }
 
-// save (save = true) the step's small state from the lattice, or restore the
-// wall-model part of it
-hl_status small_copy(hl_lattice* lat, char* sm, long long t, bool save) {
+// the step's small state: the outlet velocity it reads (saved on the
+// lattice stream, which writes it) and the wall-model state at its start
+// (saved on the box stream bs, which owns it)
+hl_status small_save(hl_lattice* lat, char* sm, long long t, cudaStream_t bs) {
     const cudaMemcpyKind kd = cudaMemcpyDeviceToDevice;
-    cudaStream_t st = lat->stream;
-    size_t o = 0;
-    const size_t plb = sizeof(float) * 3 * plane_cells(lat->cfg);
-    if (save) HL_CUDA(lat, cudaMemcpyAsync(sm, uplane_prev_of(lat, t), plb, kd, st));
-    o = align_up(plb);
+    SmallOff so;
+    small_layout(lat, &so);
+    HL_CUDA(lat, cudaMemcpyAsync(sm, uplane_prev_of(lat, t), sizeof(float) * 3 * plane_cells(lat->cfg), kd,
+                                 lat->stream));
     for (int k = 0; k < lat->nrot; ++k) {
         RotorDev& D = lat->rot[k].dev;
-        const size_t ub = sizeof(double) * D.box_cells;
-        HL_CUDA(lat, save ? cudaMemcpyAsync(sm + o, D.utau, ub, kd, st) : cudaMemcpyAsync(D.utau, sm + o, ub, kd, st));
-        o += align_up(ub);
-        const size_t ab = (size_t)D.box_cells;
-        HL_CUDA(lat, save ? cudaMemcpyAsync(sm + o, D.active, ab, kd, st)
-                          : cudaMemcpyAsync(D.active, sm + o, ab, kd, st));
-        o += align_up(ab);
+        HL_CUDA(lat, cudaMemcpyAsync(sm + so.utau[k], D.utau, sizeof(double) * D.box_cells, kd, bs));
+        HL_CUDA(lat, cudaMemcpyAsync(sm + so.active[k], D.active, (size_t)D.box_cells, kd, bs));
+    }
+    return HL_OK;
+}
+
+// the wall-model output of a step, saved after the step's wall model ran
+// (box stream) or put back for the step's reverse pass
+hl_status wm_copy(hl_lattice* lat, char* sm, bool save, cudaStream_t bs) {
+    const cudaMemcpyKind kd = cudaMemcpyDeviceToDevice;
+    SmallOff so;
+    small_layout(lat, &so);
+    for (int k = 0; k < lat->nrot; ++k) {
+        RotorDev& D = lat->rot[k].dev;
+        const size_t b = sizeof(float) * 9 * D.box_cells;
+        HL_CUDA(lat, save ? cudaMemcpyAsync(sm + so.wm[k], D.wm, b, kd, bs) : cudaMemcpyAsync(D.wm, sm + so.wm[k], b, kd, bs));
     }
     return HL_OK;
 }
@@ -754,6 +794,19 @@ hl_status hl_grad(hl_lattice* lat, int steps, int avg_last, int ckpt_every, cons
     HL_CUDA(lat, cudaMemsetAsync(ws + G.gup, 0, 2 * align_up(plb), st));
     for (int k = 0; k < lat->nrot; ++k) HL_CUDA(lat, cudaMemsetAsync(ws + G.radj[k], 0, rotor_adj_bytes(lat, k), st));
     if (d_dJ_dd0) HL_CUDA(lat, cudaMemsetAsync(d_dJ_dd0, 0, sizeof(float) * lat->N, st));
+    // streams and events of the reverse sweep (the box chain on the aux stream)
+    const bool two = lat->have_aux && lat->nrot > 0;
+    cudaStream_t bs = two ? lat->aux : st;
+    struct Events {
+        cudaEvent_t e[4] = {nullptr, nullptr, nullptr, nullptr};
+        ~Events() {
+            for (cudaEvent_t x : e)
+                if (x) cudaEventDestroy(x);
+        }
+    } evs;
+    for (int i = 0; two && i < 4; ++i)
+        HL_CUDA(lat, cudaEventCreateWithFlags(&evs.e[i], cudaEventDisableTiming));
+    cudaEvent_t ev_bulk[2] = {evs.e[0], evs.e[1]}, ev_box[2] = {evs.e[2], evs.e[3]};
     int ln = 0;      // lam[ln] = adjoint of the populations at t + 1
     int gc = 0;      // gup[gc] = adjoint of the outlet velocity written at t
     int uc = 0;      // gut[uc] = adjoint of the friction velocity of step t
@@ -769,58 +822,83 @@ hl_status hl_grad(hl_lattice* lat, int steps, int avg_last, int ckpt_every, cons
         if ((rc = fork_aux(lat)) != HL_OK) return rc;
         for (int jj = 0; jj < L; ++jj) {
             const long long t = ts + jj;
-            if ((rc = join_aux(lat)) != HL_OK) return rc;
-            if ((rc = small_copy(lat, ws + G.small + (size_t)jj * smb, t, true)) != HL_OK) return rc;
-            if ((rc = fork_aux(lat)) != HL_OK) return rc;
-            if (jj == L - 1) break;
-            StepArgs a = args_at(lat, t, buf(jj), buf(jj + 1));
-            if ((rc = issue_step(lat, a, false)) != HL_OK) return rc;
+            char* sm = ws + G.small + (size_t)jj * smb;
+            if ((rc = small_save(lat, sm, t, bs)) != HL_OK) return rc;
+            if (jj < L - 1) {
+                StepArgs a = args_at(lat, t, buf(jj), buf(jj + 1));
+                if ((rc = issue_step(lat, a, false)) != HL_OK) return rc;
+            } else if (lat->nrot > 0) {
+                // the segment's last state is not advanced: run its embedding and
+                // wall model alone
+                StepArgs a = args_at(lat, t, buf(jj), buf(jj));
+                a.part = 0;
+                HL_CUDA(lat, launch_band(Q, S, a, bs));
+                if (lat->cfg.wall_model) HL_CUDA(lat, launch_wall(Q, S, a, bs));
+                for (int k = 0; k < lat->nrot; ++k)
+                    HL_CUDA(lat, cudaMemsetAsync(lat->rot[k].dev.count, 0, 2 * sizeof(int), bs));
+            }
+            if (lat->nrot > 0 && lat->cfg.wall_model && (rc = wm_copy(lat, sm, true, bs)) != HL_OK) return rc;
         }
+        // both halves of the reverse step read states written by both halves
+        // of the recomputation
         if ((rc = join_aux(lat)) != HL_OK) return rc;
-        // adjoint steps of the segment, last to first
+        if ((rc = fork_aux(lat)) != HL_OK) return rc;
+        // adjoint steps of the segment, last to first: the cells outside the
+        // rotor boxes on the lattice stream, the box chain (embedding, wall
+        // model, box adjoint, wall-model adjoint) on the box stream; step t
+        // gathers the adjoint of step t + 1 from both halves and overwrites
+        // the buffer step t + 1 read, so each half waits for the other's t + 1
         for (int jj = L - 1; jj >= 0; --jj) {
             const long long t = ts + jj;
+            const int p = (int)(t & 1), q = p ^ 1;
             char* sm = ws + G.small + (size_t)jj * smb;
-            if ((rc = small_copy(lat, sm, t, false)) != HL_OK) return rc;
             StepArgs a = args_at(lat, t, buf(jj), buf(jj));
             a.uplane_prev = reinterpret_cast<const float*>(sm);
             a.tangent = 1;
             const bool force_on = t >= t0 + T - na;
-            size_t o = align_up(plb);
-            for (int k = 0; k < lat->nrot; ++k) {
-                RotorDev& D = a.rot[k];
-                D.ddp = ra[k].ddp;
-                D.gub = ra[k].gub;
-                D.gS = ra[k].gS;
-                D.tape_utau = reinterpret_cast<const double*>(sm + o);
-                o += align_up(sizeof(double) * D.box_cells);
-                D.tape_active = reinterpret_cast<const uint8_t*>(sm + o);
-                o += align_up((size_t)D.box_cells);
-                D.gut_next = ra[k].gut[uc];
-                D.gut_prev = ra[k].gut[uc ^ 1];
-                D.pacc = ra[k].pacc;
-                D.wT = force_on ? (float)(w_thrust[k] / na) : 0.0f;
-                D.wQ = force_on ? (float)(w_torque[k] / na) : 0.0f;
-                HL_CUDA(lat, cudaMemsetAsync(lat->rot[k].dev.count, 0, 2 * sizeof(int), st));
-                // only this step's wall cells hand an adjoint to the previous step's u_tau
-                HL_CUDA(lat, cudaMemsetAsync(ra[k].gut[uc ^ 1], 0, sizeof(double) * D.box_cells, st));
-            }
-            if (lat->nrot > 0) {
-                a.part = 0;
-                HL_CUDA(lat, launch_band(Q, S, a, st));
-                if (lat->cfg.wall_model) HL_CUDA(lat, launch_wall(Q, S, a, st));
-            }
             AdjArgs adj;
             adj.lam_next = lam[ln];
             adj.lam = lam[ln ^ 1];
             adj.dJdd0 = d_dJ_dd0;
             adj.gup_cur = gup[gc];
             adj.gup_prev = gup[gc ^ 1];
-            HL_CUDA(lat, launch_adj(Q, S, a, adj, force_on, st));
+            // lattice stream: bulk cells
+            if (two) HL_CUDA(lat, cudaStreamWaitEvent(st, ev_box[q], 0));
+            HL_CUDA(lat, launch_adj_bulk(Q, S, a, adj, st));
+            if (two) HL_CUDA(lat, cudaEventRecord(ev_bulk[p], st));
+            // box stream: forward quantities of step t, then the box adjoint
+            if (lat->nrot > 0) {
+                // the step's wall-model output from the tape (the linearisation point)
+                if (lat->cfg.wall_model && (rc = wm_copy(lat, sm, false, bs)) != HL_OK) return rc;
+                SmallOff so;
+                small_layout(lat, &so);
+                for (int k = 0; k < lat->nrot; ++k) {
+                    RotorDev& D = a.rot[k];
+                    D.ddp = ra[k].ddp;
+                    D.gub = ra[k].gub;
+                    D.gS = ra[k].gS;
+                    D.tape_utau = reinterpret_cast<const double*>(sm + so.utau[k]);
+                    D.tape_active = reinterpret_cast<const uint8_t*>(sm + so.active[k]);
+                    D.gut_next = ra[k].gut[uc];
+                    D.gut_prev = ra[k].gut[uc ^ 1];
+                    D.pacc = ra[k].pacc;
+                    D.wT = force_on ? (float)(w_thrust[k] / na) : 0.0f;
+                    D.wQ = force_on ? (float)(w_torque[k] / na) : 0.0f;
+                    HL_CUDA(lat, cudaMemsetAsync(lat->rot[k].dev.count, 0, 2 * sizeof(int), bs));
+                    // only this step's wall cells hand an adjoint to the previous step's u_tau
+                    HL_CUDA(lat, cudaMemsetAsync(ra[k].gut[uc ^ 1], 0, sizeof(double) * D.box_cells, bs));
+                }
+                a.part = 0;
+                HL_CUDA(lat, launch_band(Q, S, a, bs));
+                if (two) HL_CUDA(lat, cudaStreamWaitEvent(bs, ev_bulk[q], 0));
+                HL_CUDA(lat, launch_adj_box(Q, S, a, adj, force_on, bs));
+                if (two) HL_CUDA(lat, cudaEventRecord(ev_box[p], bs));
+            }
             ln ^= 1;
             gc ^= 1;
             uc ^= 1;
         }
+        if ((rc = join_aux(lat)) != HL_OK) return rc;
     }
     // the lattice ends where the forward pass ended
     if ((rc = ckpt_copy(lat, ws + G.ck + (size_t)G.n_ck * ckb, false, true)) != HL_OK) return rc;

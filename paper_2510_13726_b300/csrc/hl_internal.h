@@ -10,10 +10,21 @@ namespace hl {
 
 constexpr int FORCE_BLOCKS = 296;    // blocks per rotor in the force reduction (2 x 148 SMs)
 constexpr int WALL_BLOCKS = 148;     // blocks per rotor in the wall model
+constexpr int WALL_THREADS = 128;    // four warps per block
+
+// Cell lists (force cells, wall cells): consecutive entries (neighbouring
+// cells) go to consecutive threads, so each warp's gathers share cache lines
+// and each warp carries a full set of lanes through the FP64 wall-function
+// solve, whose pipe bounds the wall kernel (spreading the entries one per
+// warp lane across all SMs left most lanes idle and ran 3.4x slower).
+__device__ __forceinline__ int list_first(void) { return blockIdx.x * blockDim.x + threadIdx.x; }
+__device__ __forceinline__ int list_stride(void) { return gridDim.x * blockDim.x; }
 constexpr int MASS_BLOCKS = 592;     // 4 x 148 SMs
 constexpr int BAND_THREADS = 256;
 
-enum ErrBits : unsigned { ERR_NONFINITE = 1u, ERR_MASS = 2u };
+// device error word; ERR_GEOMETRY: a wall cell's velocity sample reached
+// outside its rotor box (the blade grid needs more padding around the blade)
+enum ErrBits : unsigned { ERR_NONFINITE = 1u, ERR_MASS = 2u, ERR_GEOMETRY = 4u };
 
 struct StepArgs {
     void* f;                 // populations [Q][N], storage type

@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(128) wall_kernel(const StepArgs a) {
     const RotorDev& R = a.rot[blockIdx.y];
     int count = *((volatile int*)(R.count + 1));
     if ((long long)count > R.box_cells) count = (int)R.box_cells;
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < count; idx += gridDim.x * blockDim.x) {
+    for (int idx = list_first(); idx < count; idx += list_stride()) {
         const long long bi = R.wlist[idx];
         const float phi = R.wphi[idx];
         const int which = R.wwhich[idx];
@@ -340,6 +340,22 @@ __global__ void __launch_bounds__(128) wall_kernel(const StepArgs a) {
                 if (i0[k] > a.n[k] - 2) { i0[k] = a.n[k] - 2; t[k] = 1.f; }
             }
         }
+        // the sample's corner cells must lie in the rotor box: the box chain
+        // runs beside the bulk launch, which updates every cell outside it
+        bool inside = true;
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            inside = inside && i0[k] - R.lo[k] >= 0 && i0[k] + 1 - R.lo[k] < R.n[k];
+        const long long B = R.box_cells;
+        float* wm = R.wm + bi;
+        if (!inside) {
+            atomicOr(a.err, ERR_GEOMETRY);
+#pragma unroll
+            for (int k = 0; k < 9; ++k) wm[k * B] = 0.f;
+            R.active[bi] = 0;
+            R.utau[bi] = 0.0;
+            continue;
+        }
         float us[3] = {0.f, 0.f, 0.f};
         for (int cz = 0; cz < 2; ++cz)
             for (int cy = 0; cy < 2; ++cy)
@@ -359,8 +375,6 @@ __global__ void __launch_bounds__(128) wall_kernel(const StepArgs a) {
         const float un = ur[0] * n[0] + ur[1] * n[1] + ur[2] * n[2];
         const float ut[3] = {ur[0] - un * n[0], ur[1] - un * n[1], ur[2] - un * n[2]};
         const float utm = sqrtf(ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2]);
-        const long long B = R.box_cells;
-        float* wm = R.wm + bi;
         if (!(utm >= 1e-12f)) {
 #pragma unroll
             for (int k = 0; k < 9; ++k) wm[k * B] = 0.f;
@@ -405,7 +419,7 @@ __global__ void __launch_bounds__(256) force_kernel(const StepArgs a) {
     int count = *((volatile int*)R.count);
     if ((long long)count > R.box_cells) count = (int)R.box_cells;
     double acc[6] = {0, 0, 0, 0, 0, 0};
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < count; idx += gridDim.x * blockDim.x) {
+    for (int idx = list_first(); idx < count; idx += list_stride()) {
         const long long bi = R.list[idx];
         const int bx = (int)(bi % R.n[0]);
         const long long r2 = bi / R.n[0];
@@ -660,8 +674,8 @@ template <int Q, int S>
 static cudaError_t launch_wall_t(const StepArgs& a, cudaStream_t s) {
     if (a.nrot == 0 || !a.wall_model) return cudaSuccess;
     const dim3 grd(WALL_BLOCKS, a.nrot);
-    if (a.phase == 0) wall_kernel<Q, S, 0><<<grd, 128, 0, s>>>(a);
-    else wall_kernel<Q, S, 1><<<grd, 128, 0, s>>>(a);
+    if (a.phase == 0) wall_kernel<Q, S, 0><<<grd, WALL_THREADS, 0, s>>>(a);
+    else wall_kernel<Q, S, 1><<<grd, WALL_THREADS, 0, s>>>(a);
     return cudaGetLastError();
 }
 

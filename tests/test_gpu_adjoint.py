@@ -235,3 +235,28 @@ def test_rotor_objective_autograd(P):
     assert abs(float(T[0] - 0.2 * Qv[0]) - Jr) <= 1e-9 * abs(Jr)
     assert abs(float(pitch.grad[0]) - gpr[0]) <= 1e-6 * abs(gpr[0])
     assert _rel_l2(d0.grad.cpu().numpy().astype(np.float64), gdr.cpu().numpy().astype(np.float64)) <= 1e-6
+
+
+def test_wall_sample_outside_box_is_reported(P):
+    """A blade grid without padding: a thin sheet (half a cell along T) whose
+    signed distance is about 0.5 everywhere and rises along the axis, so the
+    wall normals point axially and wall cells reach the axial edge of the
+    rotor's reach.  Their velocity samples would leave the rotor box, which
+    the second stream must not read: the step reports HL_ERR_GEOMETRY and
+    leaves those cells unmodelled."""
+    import dataclasses
+    wl = _wl()
+    g0 = wl.blade_grids()[0]
+    gx = g0.sdf.shape[2]
+    gz = 17
+    sdf = 0.5 + 1e-3 * np.arange(gz, dtype=np.float32)[:, None, None] + np.zeros((gz, 2, gx), np.float32)
+    grid = dataclasses.replace(g0, sdf=np.ascontiguousarray(sdf, dtype=np.float32),
+                               origin=(g0.origin[0], -0.25, -4.0))
+    # sample 4 cells off the wall: from the axial edge of the reach (3 cells
+    # off the centre plane) the trilinear corners reach 8 cells, the box 7
+    lat = P.Lattice(wl.nx, wl.ny, wl.nz, wm_ysample=4.0)
+    spec = wl.rotors[0]
+    lat.add_rotor(grid, center=spec.center, omega=spec.omega(wl.u_in))
+    with pytest.raises(P.HlError) as e:
+        lat.step(1)
+    assert e.value.code == -9
