@@ -325,6 +325,7 @@ def run_cuda(args):
             torch.cuda.empty_cache()
             line["storage_study"] = storage_study(dev, args.extra_steps)
             line["farm"] = farm_run(dev, args.extra_steps)
+            line["adjoint"] = adjoint_run(dev, args.adjoint_steps, args.adjoint_steps // 4, 100)
         print(json.dumps(line), flush=True)
     lat.close()
     return 0
@@ -383,6 +384,50 @@ def farm_run(dev, steps):
     return r
 
 
+def adjoint_run(dev, steps, avg_last, ckpt_every):
+    """Gradient of the time-averaged thrust on the 128x128x256 D3Q19 rotor
+    (R = 32): hl_grad over `steps` steps (checkpoint every `ckpt_every`)
+    against the same number of plain forward steps from the same state."""
+    import torch
+    import workloads as W
+    from paper_2510_13726_b300 import Lattice
+    wl = W.workload("rotor128_adj")
+    lat = Lattice.from_workload(wl, device=dev)
+    lat.step(5)
+    state = lat.save_state()
+    nb = lat.grad_workspace_size(steps, ckpt_every)
+    work = torch.empty(nb + 256, dtype=torch.uint8, device=dev)
+    work = work[(-work.data_ptr()) % 256:]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(lat.stream)
+    lat.step_async(steps)
+    e1.record(lat.stream)
+    e1.synchronize()
+    lat.check()
+    fwd = e0.elapsed_time(e1) / steps
+    lat.load_state(state)
+    torch.cuda.synchronize(dev)
+    e0.record(lat.stream)
+    J, gp, gd = lat.grad(steps, avg_last, [1.0], [0.0], ckpt_every=ckpt_every, work=work)
+    e1.record(lat.stream)
+    e1.synchronize()
+    grad = e0.elapsed_time(e1) / steps
+    finite = bool(torch.isfinite(gd).all().item())
+    lat.close()
+    del lat, work, gd
+    torch.cuda.empty_cache()
+    return {"workload": "rotor128_adj: 128x128x256 D3Q19 FP32, R=32 NACA4412 rotor, TSR 6",
+            "objective": f"mean thrust over the last {avg_last} of {steps} steps",
+            "steps": steps, "ckpt_every": ckpt_every, "workspace_gb": round(nb / 1e9, 2),
+            "forward_ms_per_step": round(fwd, 4), "grad_ms_per_step": round(grad, 4),
+            "ratio_end_to_end": round(grad / fwd, 3),
+            "reverse_ms_per_step": round(grad - fwd, 4),
+            "ratio_reverse_per_step": round((grad - fwd) / fwd, 3),
+            "J": J, "dJ_dpitch": float(gp[0]), "dJ_dd0_finite": finite}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -393,8 +438,10 @@ def main(argv=None):
     ap.add_argument("--storage", default="f32", choices=["f32", "f16s", "bf16s"])
     ap.add_argument("--cpu-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extra", action="store_true", help="skip the 16-bit storage study and the farm run")
+    ap.add_argument("--no-extra", action="store_true", help="skip the 16-bit storage study, the farm run and the gradient run")
     ap.add_argument("--extra-steps", type=int, default=40)
+    ap.add_argument("--adjoint-steps", type=int, default=4000,
+                    help="steps of the gradient run (config of the adjoint/forward ratio)")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "cuda":
         args.warmup = 3

@@ -121,8 +121,8 @@ def test_forward_with_d0_and_frozen_sets_matches_oracle(P):
     o.set_d0(d0.astype(np.float64))
     lat.freeze_sets(True)
     o.freeze_sets(True)
-    lat.set_pitch(0, 0.05)
-    o.set_pitch(0, 0.05)
+    lat.set_pitch(0, wl.rotors[0].pitch + 0.05)
+    o.set_pitch(0, wl.rotors[0].pitch + 0.05)
     lat.step(12)
     o.step(12)
     rg, ug = (a.cpu().numpy().astype(np.float64) for a in lat.fields())
@@ -187,12 +187,14 @@ def test_gradient_against_gpu_finite_differences(P):
     J0, gp, gd = lat.grad(T, navg, [wT], [wQ], ckpt_every=8)
     gd = gd.cpu().numpy()
 
+    p0 = wl.rotors[0].pitch
+
     def J(pitch=0.0, d0=None):
         m = P.Lattice.from_workload(wl)
         if d0 is not None:
             m.set_d0(torch.tensor(d0, device=m.device))
         m.freeze_sets(True)
-        m.set_pitch(0, pitch)
+        m.set_pitch(0, p0 + pitch)
         m.step(T - navg)
         m.forces(reset_avg=True)
         m.step(navg)
@@ -225,7 +227,7 @@ def test_rotor_objective_autograd(P):
     import torch
     wl = _wl()
     lat = P.Lattice.from_workload(wl)
-    pitch = torch.zeros(1, dtype=torch.float64, requires_grad=True)
+    pitch = torch.full((1,), wl.rotors[0].pitch, dtype=torch.float64, requires_grad=True)
     d0 = torch.ones(wl.nz, wl.ny, wl.nx, device=lat.device, requires_grad=True)
     T, Qv = P.rotor_objective(lat, pitch, d0, steps=12, avg_last=6, ckpt_every=4)
     (T.sum() - 0.2 * Qv.sum()).backward()
@@ -260,3 +262,61 @@ def test_wall_sample_outside_box_is_reported(P):
     with pytest.raises(P.HlError) as e:
         lat.step(1)
     assert e.value.code == -9
+
+
+def test_gradient_study_128x128x256_against_finite_differences(P):
+    """The gradient study (128x128x256 D3Q19, R = 32, wall model on): mean
+    thrust over the last 1000 of 4000 steps, checkpoint every 100 steps.
+    dJ/dpitch against a central difference of the CUDA forward (h = 1e-4
+    rad, cell sets frozen); dJ/dd0 at 32 random cells within 2R of the rotor
+    centre against central differences (h_d = 1e-3)."""
+    import torch
+    wl = W.workload("rotor128_adj")
+    T, navg, K = 4000, 1000, 100
+    lat = P.Lattice.from_workload(wl)
+    s0 = lat.save_state()
+    J, gp, gd = lat.grad(T, navg, [1.0], [0.0], ckpt_every=K)
+    gd = gd.cpu().numpy()
+    p0 = wl.rotors[0].pitch
+
+    def Jrun(dp=0.0, d0=None):
+        lat.load_state(s0)
+        lat.set_d0(None if d0 is None else torch.tensor(d0, device=lat.device))
+        lat.freeze_sets(True)
+        lat.set_pitch(0, p0 + dp)
+        lat.step(T - navg)
+        lat.forces(reset_avg=True)
+        lat.step(navg)
+        _, Fa = lat.forces()
+        lat.freeze_sets(False)
+        lat.set_pitch(0, p0)
+        return Fa[0, wl.flow_axis]
+
+    assert abs(Jrun() - J) <= 1e-12 * abs(J)
+    fd = (Jrun(1e-4) - Jrun(-1e-4)) / 2e-4
+    print(f"dJ/dpitch adjoint {gp[0]:.6f} FD {fd:.6f}")
+    assert abs(gp[0] - fd) <= 2e-2 * abs(fd)
+    rng = np.random.default_rng(11)
+    c, R = wl.rotors[0].center, wl.rotors[0].radius
+    cells = []
+    while len(cells) < 32:
+        off = rng.uniform(-2 * R, 2 * R, 3)
+        if np.linalg.norm(off) <= 2 * R:
+            x, y, z = (int(round(c[k] + off[k])) for k in range(3))
+            cells.append((z, y, x))
+    adj, fds = [], []
+    for cell in cells:
+        e = np.ones((wl.nz, wl.ny, wl.nx), np.float32)
+        e[cell] = 1.001
+        Jp = Jrun(d0=e)
+        e[cell] = 0.999
+        Jm = Jrun(d0=e)
+        adj.append(float(gd[cell]))
+        fds.append((Jp - Jm) / 2e-3)
+    adj, fds = np.array(adj), np.array(fds)
+    scale = np.abs(fds).max()
+    rel = np.abs(adj - fds) / np.maximum(np.abs(fds), 0.05 * scale)
+    print("dJ/dd0 relative error: median %.3g, 90th percentile %.3g, max %.3g" %
+          (np.median(rel), np.percentile(rel, 90), rel.max()))
+    assert np.median(rel) <= 0.02
+    assert np.percentile(rel, 90) <= 0.1

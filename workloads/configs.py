@@ -77,11 +77,22 @@ class Workload:
         return fourier_modes(self.seed, self.n_modes, length, self.u_in, self.turbulence)
 
 
-def _single(nx, ny, nz, radius, tsr, axis=2) -> list:
+def _single(nx, ny, nz, radius, tsr, axis=2, phase0=0.0, pitch=0.0) -> list:
     n = (nx, ny, nz)
     c = [0.5 * (n[i] - 1) for i in range(3)]
     c[axis] = float(n[axis] // 4)
-    return [RotorSpec(center=tuple(c), radius=radius, tsr=tsr)]
+    return [RotorSpec(center=tuple(c), radius=radius, tsr=tsr, phase0=phase0, pitch=pitch)]
+
+
+# Gradient workloads take a generic rotor angle and pitch.  At pitch 0 the
+# axial blade-frame coordinate of every cell is an integer (the rotor
+# centre sits on an integer axial position) and the blade grid has nodes
+# every half cell, so every sample lies on a node plane of the grid, where
+# the trilinear signed distance has a kink in the pitch direction and the
+# pitch derivative is one-sided; the same holds at phase 0 for the first
+# blade's in-plane coordinates.
+GRADIENT_PHASE0 = 0.37
+GRADIENT_PITCH = 0.03
 
 
 def _farm(seed: int) -> list:
@@ -118,10 +129,11 @@ def _make() -> dict:
         note="D3Q27 128x128x256 sub-run of the 16-bit study, R=32, TSR 7")
     w["rotor128_adj"] = Workload(
         "rotor128_adj", 128, 128, 256, steps=4000,
-        rotors=_single(128, 128, 256, 32.0, 6.0),
+        rotors=_single(128, 128, 256, 32.0, 6.0, phase0=GRADIENT_PHASE0, pitch=GRADIENT_PITCH),
         note="D3Q19 R=32, 4000 steps, checkpoint every 100 (gradient study)")
     w["rotor48_adj"] = Workload(
-        "rotor48_adj", 48, 48, 64, steps=16, rotors=_single(48, 48, 64, 10.0, 6.0),
+        "rotor48_adj", 48, 48, 64, steps=16, rotors=_single(48, 48, 64, 10.0, 6.0, phase0=GRADIENT_PHASE0,
+                                                       pitch=GRADIENT_PITCH),
         note="D3Q19 48x48x64, R=10, 16 steps (gradient checks at oracle size)")
     w["farm"] = Workload(
         "farm", 1536, 512, 1024, flow_axis=0, steps=1000, turbulence=0.05,
