@@ -1,5 +1,6 @@
 // Host side of the C ABI declared in include/hlbm.h.
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -48,6 +49,21 @@ bool valid_config(const hl_config* c) {
 
 namespace hl {
 namespace host {
+
+void set_shifted_bases(StepArgs* a, int q, int esize) {
+    std::vector<int> c(3 * q);
+    std::vector<double> w(q);
+    hl_velocity_set(q, c.data(), w.data());
+    const int P = (q - 1) / 2;
+    for (int s = 0; s < q; ++s) {
+        const long long D = c[3 * s] + (long long)c[3 * s + 1] * a->n[0] + (long long)c[3 * s + 2] * a->nxy;
+        const int sbar = s == 0 ? 0 : (s <= P ? s + P : s - P);
+        // integer arithmetic on the addresses: the shifted bases may lie
+        // outside the buffer, every address formed from them lies inside
+        a->rshift[s] = reinterpret_cast<const void*>(reinterpret_cast<uintptr_t>(a->slot[sbar]) - D * esize);
+        a->wshift[s] = reinterpret_cast<void*>(reinterpret_cast<uintptr_t>(a->wslot[s]) + D * esize);
+    }
+}
 
 StepArgs make_args(const hl_lattice* lat) {
     const hl_config& c = lat->cfg;
@@ -106,6 +122,7 @@ StepArgs make_args(const hl_lattice* lat) {
         a.rot[k].spD = (float)std::sin(ps);
         a.rot[k].frozen = lat->frozen ? 1 : 0;
     }
+    set_shifted_bases(&a, c.q, store_bytes(c.storage));   // needs n and nxy
     return a;
 }
 

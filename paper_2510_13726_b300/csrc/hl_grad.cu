@@ -696,6 +696,7 @@ StepArgs args_at(hl_lattice* lat, long long t, void* rd, void* wr) {
         a.slot[q] = static_cast<char*>(rd) + q * sb;
         a.wslot[q] = static_cast<char*>(wr) + q * sb;
     }
+    set_shifted_bases(&a, lat->cfg.q, store_bytes(lat->cfg.storage));
     return a;
 }
 

@@ -122,6 +122,8 @@ hl_status cuda_fail(hl_lattice* lat, cudaError_t e, const char* where);
 
 // kernel arguments of the lattice's current step (in-place populations)
 StepArgs make_args(const hl_lattice* lat);
+// odd-step shifted bases from slot / wslot (call after changing either)
+void set_shifted_bases(StepArgs* a, int q, int esize);
 // issue one step with the given arguments: serial, or bulk / box chain on two
 // streams; with_force = false skips the force reduction (and resets the
 // cell-list counters it would reset)

@@ -30,6 +30,11 @@ struct StepArgs {
     void* f;                 // populations [Q][N], storage type
     void* slot[27];          // base of slot s of the pre-collision state (read)
     void* wslot[27];         // base of slot s of the post-collision state (written; = slot in place)
+    // odd-step bases shifted by the slot's velocity: f_s(x) is read at
+    // rshift[s] + x (slot sbar of x - c_s) and f*_s(x) written at wshift[s] + x
+    // (slot s of x + c_s); valid for cells whose neighbours need no periodic wrap
+    const void* rshift[27];
+    void* wshift[27];
     long long N;
     int n[3];
     int nxy, nplane;         // nx * ny; cells of an inlet/outlet plane

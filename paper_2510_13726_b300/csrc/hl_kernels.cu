@@ -102,6 +102,9 @@ __global__ void __launch_bounds__(128) collide_kernel(const StepArgs a) {
     const int na = sel3(ax, a.n[0], a.n[1], a.n[2]);
     const bool inlet = a.open && ca == 0;
     const bool outlet = a.open && ca == na - 1;
+    // odd steps away from the lattice faces: every population at one offset
+    // from a per-slot base (no neighbour index arithmetic)
+    const bool shifted = PH == 1 && x > 0 && x < a.n[0] - 1 && y > 0 && y < a.n[1] - 1 && z > 0 && z < a.n[2] - 1;
     Offs o;
     make_offs(a, x, y, z, o);
     float g[Q];
@@ -117,7 +120,13 @@ __global__ void __launch_bounds__(128) collide_kernel(const StepArgs a) {
             }
         }
         if (a.part == 1 && rk >= 0) return;   // box cells belong to the box launch
-        load_pre<Q, S, PH>(a, cell, o, g);
+        if (shifted) {
+            using T = typename Store<S>::T;
+#pragma unroll
+            for (int s = 0; s < Q; ++s) g[s] = Store<S>::ld(static_cast<const T*>(a.rshift[s]) + cell);
+        } else {
+            load_pre<Q, S, PH>(a, cell, o, g);
+        }
         float u[3];
         float rho;
         if (rk >= 0) {
@@ -167,6 +176,12 @@ __global__ void __launch_bounds__(128) collide_kernel(const StepArgs a) {
             a.uplane_cur[pl] = u[0];
             a.uplane_cur[a.nplane + pl] = u[1];
             a.uplane_cur[2 * a.nplane + pl] = u[2];
+        }
+        if (shifted) {
+            using T = typename Store<S>::T;
+#pragma unroll
+            for (int s = 0; s < Q; ++s) Store<S>::st(static_cast<T*>(a.wshift[s]) + cell, g[s]);
+            return;
         }
 #pragma unroll
         for (int s = 0; s < Q; ++s) {
