@@ -371,101 +371,123 @@ __device__ inline void rotor_normal_tan(const RotorDev& R, int which, int x, int
 }
 
 // ---------------------------------------------------------------------------
-// FP64 forward-mode duals for the two Newton solves of the wall function:
-// value and derivatives along three seeds
+// FP64 forward-mode duals for the two Newton solves of the wall function
+// (wall_newton_t / spalding_uplus_t instantiated on Dual<NS>): the value and
+// its derivatives along NS seeds
 // ---------------------------------------------------------------------------
-struct D3 {
-    double v, d[3];
+template <int NS>
+struct Dual {
+    double v, d[NS];
 };
-__device__ __forceinline__ D3 dmk(double v, double a = 0.0, double b = 0.0, double c = 0.0) {
-    D3 r; r.v = v; r.d[0] = a; r.d[1] = b; r.d[2] = c; return r;
-}
-__device__ __forceinline__ D3 operator+(const D3& x, const D3& y) {
-    return dmk(x.v + y.v, x.d[0] + y.d[0], x.d[1] + y.d[1], x.d[2] + y.d[2]);
-}
-__device__ __forceinline__ D3 operator-(const D3& x, const D3& y) {
-    return dmk(x.v - y.v, x.d[0] - y.d[0], x.d[1] - y.d[1], x.d[2] - y.d[2]);
-}
-__device__ __forceinline__ D3 operator*(const D3& x, const D3& y) {
-    return dmk(x.v * y.v, x.d[0] * y.v + x.v * y.d[0], x.d[1] * y.v + x.v * y.d[1], x.d[2] * y.v + x.v * y.d[2]);
-}
-// the value is divided as in the plain solve (same rounding, same stopping
-// decisions); the derivative parts use one reciprocal
-__device__ __forceinline__ D3 operator/(const D3& x, const D3& y) {
-    const double q = x.v / y.v;
-    const double r = 1.0 / y.v;
-    return dmk(q, (x.d[0] - q * y.d[0]) * r, (x.d[1] - q * y.d[1]) * r, (x.d[2] - q * y.d[2]) * r);
-}
-__device__ __forceinline__ D3 operator*(double s, const D3& x) { return dmk(s * x.v, s * x.d[0], s * x.d[1], s * x.d[2]); }
-__device__ __forceinline__ D3 operator/(const D3& x, double s) {
-    const double r = 1.0 / s;
-    return dmk(x.v / s, x.d[0] * r, x.d[1] * r, x.d[2] * r);
-}
-__device__ __forceinline__ D3 operator+(double s, const D3& x) { return dmk(s + x.v, x.d[0], x.d[1], x.d[2]); }
-__device__ __forceinline__ D3 dexp(const D3& x) {
-    const double e = exp(x.v);
-    return dmk(e, e * x.d[0], e * x.d[1], e * x.d[2]);
-}
-__device__ __forceinline__ D3 dlog(const D3& x) {
-    const double r = 1.0 / x.v;
-    return dmk(log(x.v), x.d[0] * r, x.d[1] * r, x.d[2] * r);
-}
-__device__ __forceinline__ D3 dsqrt(const D3& x) {
-    const double s = sqrt(x.v);
-    const double h = 0.5 / s;
-    return dmk(s, h * x.d[0], h * x.d[1], h * x.d[2]);
-}
 
-// same expression order as spalding_yplus_e / spalding_dyplus_e
-__device__ __forceinline__ D3 yplus_d(const D3& up, const D3& e, double E, double kappa) {
-    const D3 k = kappa * up;
-    return up + (e - dmk(1.0) - k - 0.5 * k * k - k * k * k / 6.0) / E;
+template <int NS>
+__device__ __forceinline__ Dual<NS> dual_const(double v) {
+    Dual<NS> r;
+    r.v = v;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) r.d[k] = 0.0;
+    return r;
 }
-__device__ __forceinline__ D3 dyplus_d(const D3& up, const D3& e, double E, double kappa) {
-    const D3 k = kappa * up;
-    return 1.0 + (kappa / E) * (e - dmk(1.0) - k - 0.5 * k * k);
+template <int NS>
+__device__ __forceinline__ Dual<NS> dual_seed(double v, int k, double dv = 1.0) {
+    Dual<NS> r = dual_const<NS>(v);
+    r.d[k] = dv;
+    return r;
 }
-
-// wall_newton() differentiated along the seeds of u, y and the start value
-__device__ inline D3 wall_newton_d(const D3& u, const D3& y, double nu, const D3& guess, double E, double kappa,
-                                   double tol, int maxit) {
-    D3 ut = guess;
-    D3 up = u / ut;
-    D3 e = dexp(kappa * up);
-    D3 fv = yplus_d(up, e, E, kappa) - y * ut / nu;
-    for (int it = 0; it < maxit; ++it) {
-        const D3 fp = dmk(0.0) - dyplus_d(up, e, E, kappa) * u / (ut * ut) - y / nu;
-        D3 un = ut - fv / fp;
-        if (!(un.v > 0.0)) un = 0.5 * ut;
-        const D3 upn = u / un;
-        const D3 en = dexp(kappa * upn);
-        const D3 fn = yplus_d(upn, en, E, kappa) - y * un / nu;
-        ut = un;
-        up = upn;
-        e = en;
-        if (fabs(fn.v - fv.v) < tol) break;
-        fv = fn;
-    }
-    return ut;
+template <int NS>
+__device__ __forceinline__ Dual<NS> operator+(const Dual<NS>& x, const Dual<NS>& y) {
+    Dual<NS> r;
+    r.v = x.v + y.v;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) r.d[k] = x.d[k] + y.d[k];
+    return r;
 }
-
-// spalding_uplus() differentiated along the seeds of y+
-__device__ inline D3 spalding_uplus_d(const D3& yp, double E, double kappa, double tol, int maxit) {
-    const D3 lg = dlog(1.0 + E * yp) / kappa;
-    D3 up = yp.v < lg.v ? yp : lg;
-    D3 e = dexp(kappa * up);
-    D3 g = yplus_d(up, e, E, kappa) - yp;
-    for (int it = 0; it < maxit; ++it) {
-        D3 un = up - g / dyplus_d(up, e, E, kappa);
-        if (!(un.v > 0.0)) un = 0.5 * up;
-        const D3 en = dexp(kappa * un);
-        const D3 gn = yplus_d(un, en, E, kappa) - yp;
-        up = un;
-        e = en;
-        if (fabs(gn.v - g.v) < tol) break;
-        g = gn;
-    }
-    return up;
+template <int NS>
+__device__ __forceinline__ Dual<NS> operator-(const Dual<NS>& x, const Dual<NS>& y) {
+    Dual<NS> r;
+    r.v = x.v - y.v;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) r.d[k] = x.d[k] - y.d[k];
+    return r;
+}
+template <int NS>
+__device__ __forceinline__ Dual<NS> operator*(const Dual<NS>& x, const Dual<NS>& y) {
+    Dual<NS> r;
+    r.v = x.v * y.v;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) r.d[k] = x.d[k] * y.v + x.v * y.d[k];
+    return r;
+}
+template <int NS>
+__device__ __forceinline__ Dual<NS> operator/(const Dual<NS>& x, const Dual<NS>& y) {
+    Dual<NS> r;
+    r.v = x.v / y.v;
+    const double ry = 1.0 / y.v;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) r.d[k] = (x.d[k] - r.v * y.d[k]) * ry;
+    return r;
+}
+template <int NS>
+__device__ __forceinline__ Dual<NS> operator*(double s, const Dual<NS>& x) {
+    Dual<NS> r;
+    r.v = s * x.v;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) r.d[k] = s * x.d[k];
+    return r;
+}
+template <int NS>
+__device__ __forceinline__ Dual<NS> operator*(const Dual<NS>& x, double s) {
+    return s * x;
+}
+template <int NS>
+__device__ __forceinline__ Dual<NS> operator+(double s, const Dual<NS>& x) {
+    Dual<NS> r = x;
+    r.v = s + x.v;
+    return r;
+}
+template <int NS>
+__device__ __forceinline__ Dual<NS> operator-(const Dual<NS>& x, double s) {
+    Dual<NS> r = x;
+    r.v = x.v - s;
+    return r;
+}
+template <int NS>
+__device__ __forceinline__ Dual<NS> operator-(double s, const Dual<NS>& x) {
+    Dual<NS> r;
+    r.v = s - x.v;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) r.d[k] = -x.d[k];
+    return r;
+}
+template <int NS>
+__device__ __forceinline__ double wf_val(const Dual<NS>& x) {
+    return x.v;
+}
+template <int NS>
+__device__ __forceinline__ Dual<NS> wf_exp(const Dual<NS>& x) {
+    Dual<NS> r;
+    r.v = exp(x.v);
+#pragma unroll
+    for (int k = 0; k < NS; ++k) r.d[k] = r.v * x.d[k];
+    return r;
+}
+template <int NS>
+__device__ __forceinline__ Dual<NS> wf_log(const Dual<NS>& x) {
+    Dual<NS> r;
+    r.v = log(x.v);
+    const double rx = 1.0 / x.v;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) r.d[k] = x.d[k] * rx;
+    return r;
+}
+template <int NS>
+__device__ __forceinline__ Dual<NS> wf_rcp(const Dual<NS>& x) {
+    Dual<NS> r;
+    r.v = 1.0 / x.v;
+    const double m = -r.v * r.v;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) r.d[k] = m * x.d[k];
+    return r;
 }
 
 }  // namespace hl

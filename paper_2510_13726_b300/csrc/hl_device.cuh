@@ -425,56 +425,90 @@ __device__ inline void rotor_normal(const RotorDev& R, int which, int x, int y, 
 // u+ ~ 216, which the iterates of a cold start do reach).  Only the few
 // wall cells run this code.
 // ---------------------------------------------------------------------------
-// y+(u+) of Eq. (spalding) and its derivative, given e = exp(kappa u+)
-__device__ __forceinline__ double spalding_yplus_e(double up, double e, double E, double kappa) {
-    const double k = kappa * up;
-    return up + (e - 1.0 - k - 0.5 * k * k - k * k * k / 6.0) / E;
-}
-__device__ __forceinline__ double spalding_dyplus_e(double up, double e, double E, double kappa) {
-    const double k = kappa * up;
-    return 1.0 + kappa / E * (e - 1.0 - k - 0.5 * k * k);
+// Constants of the wall function; divisions by them become products.
+struct WallFn {
+    double E, kappa, inv_E, kappa_inv_E, inv_kappa, inv_nu, tol;
+    int maxit;
+};
+
+__host__ __device__ inline WallFn make_wallfn(double E, double kappa, double nu, double tol, int maxit) {
+    WallFn W;
+    W.E = E;
+    W.kappa = kappa;
+    W.inv_E = 1.0 / E;
+    W.kappa_inv_E = kappa / E;
+    W.inv_kappa = 1.0 / kappa;
+    W.inv_nu = 1.0 / nu;
+    W.tol = tol;
+    W.maxit = maxit;
+    return W;
 }
 
-// Newton-Raphson on Eq. (implicitWF): stop when the residual changes by less
-// than tol, at most maxit iterations; a non-positive iterate is halved.  The
-// exponential of each iterate is evaluated once and serves both the residual
-// and the derivative.
-__device__ inline double wall_newton(double u, double y, double nu, double guess, double E, double kappa,
-                                     double tol, int maxit) {
-    double ut = guess;
-    double up = u / ut;
-    double e = exp(kappa * up);
-    double fv = spalding_yplus_e(up, e, E, kappa) - y * ut / nu;
-    for (int it = 0; it < maxit; ++it) {
-        const double fp = -spalding_dyplus_e(up, e, E, kappa) * u / (ut * ut) - y / nu;
-        double un = ut - fv / fp;
-        if (!(un > 0.0)) un = 0.5 * ut;
-        const double upn = u / un;
-        const double en = exp(kappa * upn);
-        const double fn = spalding_yplus_e(upn, en, E, kappa) - y * un / nu;
+// The two solves are written once for a scalar type T: double in the time
+// step, forward-mode duals in the reverse sweep (same operations on the
+// value part).
+__device__ __forceinline__ double wf_val(double x) { return x; }
+__device__ __forceinline__ double wf_exp(double x) { return exp(x); }
+__device__ __forceinline__ double wf_log(double x) { return log(x); }
+__device__ __forceinline__ double wf_rcp(double x) { return 1.0 / x; }
+
+// y+(u+) of Eq. (spalding) and its derivative dy+/du+, given e = exp(kappa u+)
+template <class T>
+__device__ __forceinline__ T spalding_yplus_t(const T& up, const T& e, const WallFn& W) {
+    const T k = W.kappa * up;
+    return up + (e - 1.0 - k - 0.5 * k * k - (1.0 / 6.0) * k * k * k) * W.inv_E;
+}
+template <class T>
+__device__ __forceinline__ T spalding_dyplus_t(const T& up, const T& e, const WallFn& W) {
+    const T k = W.kappa * up;
+    return 1.0 + W.kappa_inv_E * (e - 1.0 - k - 0.5 * k * k);
+}
+
+// Newton-Raphson on Eq. (implicitWF), f(u_tau) = y+(u / u_tau) - y u_tau / nu:
+// stop when the residual changes by less than tol, at most maxit
+// iterations; a non-positive iterate is halved.  One exponential and one
+// reciprocal per iterate.
+template <class T>
+__device__ inline T wall_newton_t(const T& u, const T& y, const T& guess, const WallFn& W) {
+    const T y_nu = y * W.inv_nu;
+    T ut = guess;
+    T r = wf_rcp(ut);
+    T up = u * r;
+    T e = wf_exp(W.kappa * up);
+    T fv = spalding_yplus_t(up, e, W) - ut * y_nu;
+    for (int it = 0; it < W.maxit; ++it) {
+        const T fp = 0.0 - spalding_dyplus_t(up, e, W) * u * r * r - y_nu;
+        T un = ut - fv / fp;
+        if (!(wf_val(un) > 0.0)) un = 0.5 * ut;
+        const T rn = wf_rcp(un);
+        const T upn = u * rn;
+        const T en = wf_exp(W.kappa * upn);
+        const T fn = spalding_yplus_t(upn, en, W) - un * y_nu;
         ut = un;
+        r = rn;
         up = upn;
         e = en;
-        if (fabs(fn - fv) < tol) break;
+        if (fabs(wf_val(fn) - wf_val(fv)) < W.tol) break;
         fv = fn;
     }
     return ut;
 }
 
 // inverse of Eq. (spalding): u+ for y+, Newton from the right of the root
-__device__ inline double spalding_uplus(double yp, double E, double kappa, double tol, int maxit) {
-    const double lg = log(1.0 + E * yp) / kappa;
-    double up = yp < lg ? yp : lg;
-    double e = exp(kappa * up);
-    double g = spalding_yplus_e(up, e, E, kappa) - yp;
-    for (int it = 0; it < maxit; ++it) {
-        double un = up - g / spalding_dyplus_e(up, e, E, kappa);
-        if (!(un > 0.0)) un = 0.5 * up;
-        const double en = exp(kappa * un);
-        const double gn = spalding_yplus_e(un, en, E, kappa) - yp;
+template <class T>
+__device__ inline T spalding_uplus_t(const T& yp, const WallFn& W) {
+    const T lg = wf_log(1.0 + W.E * yp) * W.inv_kappa;
+    T up = wf_val(yp) < wf_val(lg) ? yp : lg;
+    T e = wf_exp(W.kappa * up);
+    T g = spalding_yplus_t(up, e, W) - yp;
+    for (int it = 0; it < W.maxit; ++it) {
+        T un = up - g / spalding_dyplus_t(up, e, W);
+        if (!(wf_val(un) > 0.0)) un = 0.5 * up;
+        const T en = wf_exp(W.kappa * un);
+        const T gn = spalding_yplus_t(un, en, W) - yp;
         up = un;
         e = en;
-        if (fabs(gn - g) < tol) break;
+        if (fabs(wf_val(gn) - wf_val(g)) < W.tol) break;
         g = gn;
     }
     return up;

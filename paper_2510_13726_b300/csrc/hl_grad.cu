@@ -32,6 +32,7 @@ namespace hl {
 
 struct AdjArgs {
     const float* lam_next;   // [Q][N] adjoint of the pre-collision populations of step t + 1
+    const float* lshift[27]; // lam_next + s N + (c_s . strides): lam_{t+1,s}(x + c_s) at lshift[s] + x
     float* lam;              // [Q][N] adjoint of the pre-collision populations of step t
     float* dJdd0;            // [N] accumulated gradient, or null
     const float* gup_cur;    // [3][plane] adjoint of the upstream velocity this step hands to the outlet
@@ -129,10 +130,18 @@ __global__ void __launch_bounds__(128) adj_bulk_kernel(const StepArgs a, const A
         for (int s = 0; s < Q; ++s) j.lam[(long long)s * N + cell] = 0.0f;
         return;
     }
+    // away from the lattice faces every neighbour is at a fixed offset: one
+    // per-thread index into per-slot shifted bases
+    const bool shifted = x > 0 && x < a.n[0] - 1 && y > 0 && y < a.n[1] - 1 && z > 0 && z < a.n[2] - 1;
     Offs o;
     make_offs(a, x, y, z, o);
     float ls[Q];
-    gather_next<Q>(j, N, o, ls);
+    if (shifted) {
+#pragma unroll
+        for (int s = 0; s < Q; ++s) ls[s] = __ldg(j.lshift[s] + cell);
+    } else {
+        gather_next<Q>(j, N, o, ls);
+    }
     const int nb = sel3(ax, a.n[1], a.n[2], a.n[0]);
     const int pl = sel3(ax, z, x, y) * nb + sel3(ax, y, z, x);
     if (outlet) {
@@ -148,7 +157,13 @@ __global__ void __launch_bounds__(128) adj_bulk_kernel(const StepArgs a, const A
         return;
     }
     float g[Q];
-    load_pre<Q, S, PH>(a, cell, o, g);
+    if (shifted && PH == 1) {
+        using T = typename Store<S>::T;
+#pragma unroll
+        for (int s = 0; s < Q; ++s) g[s] = Store<S>::ld(static_cast<const T*>(a.rshift[s]) + cell);
+    } else {
+        load_pre<Q, S, PH>(a, cell, o, g);
+    }
     float gd, guB[3], gS[6], u[3], rho;
     if (D0) {
         Band B;
@@ -359,17 +374,18 @@ __global__ void __launch_bounds__(128) adj_wall_kernel(const StepArgs a, const A
         // forward Newton solves with derivatives along (|u_t|, y_sample, start value)
         const double ysamp = (double)y1 + (double)ys;
         const bool warm = R.tape_active[bi] != 0;
-        D3 guess;
+        const WallFn W = make_wallfn(a.wmE, a.wmK, a.nu, a.wmTol, a.wmMaxit);
+        // seeds: 0 = |u_t|, 1 = y_sample, 2 = Newton start value
+        Dual<3> guess;
         if (warm) {
-            guess = dmk(R.tape_utau[bi], 0.0, 0.0, 1.0);
+            guess = dual_seed<3>(R.tape_utau[bi], 2);
         } else {
             const double g0 = sqrt(a.nu * (double)utm / (double)ys);
-            guess = dmk(g0, a.nu / ((double)ys * 2.0 * g0), 0.0, 0.0);
+            guess = dual_seed<3>(g0, 0, a.nu / ((double)ys * 2.0 * g0));
         }
-        const D3 utau = wall_newton_d(dmk((double)utm, 1.0, 0.0, 0.0), dmk(ysamp, 0.0, 1.0, 0.0), a.nu, guess, a.wmE,
-                                      a.wmK, a.wmTol, a.wmMaxit);
-        const double y1p = (double)y1 * utau.v / a.nu;
-        const D3 up = spalding_uplus_d(dmk(y1p, 1.0, 0.0, 0.0), a.wmE, a.wmK, a.wmTol, a.wmMaxit);
+        const Dual<3> utau = wall_newton_t(dual_seed<3>((double)utm, 0), dual_seed<3>(ysamp, 1), guess, W);
+        const double y1p = (double)y1 * utau.v * W.inv_nu;
+        const Dual<1> up = spalding_uplus_t(dual_seed<1>(y1p, 0), W);
         const float uw = (float)(utau.v * up.v);
         const float gs = (float)(0.5 * ((double)utm - utau.v * up.v) / (double)ys);
         // ---- reverse ----
@@ -397,8 +413,8 @@ __global__ void __launch_bounds__(128) adj_wall_kernel(const StepArgs a, const A
         const double upb = uwdb * utau.v;
         // u+ = U(y1 utau / nu)
         const double y1pb = upb * up.d[0];
-        utaub += y1pb * (double)y1 / a.nu;
-        double y1b = y1pb * utau.v / a.nu;
+        utaub += y1pb * (double)y1 * W.inv_nu;
+        double y1b = y1pb * utau.v * W.inv_nu;
         // utau = Newton(|u_t|, y1 + y_s, start)
         utmb += (float)(utaub * utau.d[0]);
         y1b += utaub * utau.d[1];
@@ -808,6 +824,16 @@ hl_status hl_grad(hl_lattice* lat, int steps, int avg_last, int ckpt_every, cons
     for (int i = 0; two && i < 4; ++i)
         HL_CUDA(lat, cudaEventCreateWithFlags(&evs.e[i], cudaEventDisableTiming));
     cudaEvent_t ev_bulk[2] = {evs.e[0], evs.e[1]}, ev_box[2] = {evs.e[2], evs.e[3]};
+    // offsets of the neighbour x + c_s in the adjoint arrays (interior cells)
+    long long lshift_off[27];
+    {
+        std::vector<int> cv(3 * Q);
+        std::vector<double> wv(Q);
+        hl_velocity_set(Q, cv.data(), wv.data());
+        for (int sl = 0; sl < Q; ++sl)
+            lshift_off[sl] = cv[3 * sl] + (long long)cv[3 * sl + 1] * lat->cfg.nx +
+                             (long long)cv[3 * sl + 2] * lat->cfg.nx * lat->cfg.ny;
+    }
     int ln = 0;      // lam[ln] = adjoint of the populations at t + 1
     int gc = 0;      // gup[gc] = adjoint of the outlet velocity written at t
     int uc = 0;      // gut[uc] = adjoint of the friction velocity of step t
@@ -859,6 +885,8 @@ hl_status hl_grad(hl_lattice* lat, int steps, int avg_last, int ckpt_every, cons
             const bool force_on = t >= t0 + T - na;
             AdjArgs adj;
             adj.lam_next = lam[ln];
+            for (int sl = 0; sl < Q; ++sl)
+                adj.lshift[sl] = lam[ln] + (long long)sl * lat->N + lshift_off[sl];
             adj.lam = lam[ln ^ 1];
             adj.dJdd0 = d_dJ_dd0;
             adj.gup_cur = gup[gc];

@@ -401,8 +401,9 @@ __global__ void __launch_bounds__(128) wall_kernel(const StepArgs a) {
         const double ysamp = (double)y1 + (double)a.wmYs;
         // Eq. (guess): previous value if the wall function was active last step
         const double guess = R.active[bi] ? R.utau[bi] : sqrt(a.nu * (double)utm / (double)a.wmYs);
-        const double utau = wall_newton((double)utm, ysamp, a.nu, guess, a.wmE, a.wmK, a.wmTol, a.wmMaxit);
-        const double up = spalding_uplus((double)y1 * utau / a.nu, a.wmE, a.wmK, a.wmTol, a.wmMaxit);
+        const WallFn W = make_wallfn(a.wmE, a.wmK, a.nu, a.wmTol, a.wmMaxit);
+        const double utau = wall_newton_t<double>((double)utm, ysamp, guess, W);
+        const double up = spalding_uplus_t<double>((double)y1 * utau * W.inv_nu, W);
         const float uw = (float)(utau * up);
         const float gs = (float)(0.5 * ((double)utm - utau * up) / (double)a.wmYs);
         wm[0] = uw * th[0];
