@@ -165,6 +165,10 @@ __device__ __forceinline__ void moments01(const float (&g)[Q], float& drho, floa
     }
 }
 
+__device__ __forceinline__ float rcp_approx(float x) { return __fdividef(1.0f, x); }
+// sqrt(x) for x >= 0 from the hardware reciprocal square root
+__device__ __forceinline__ float sqrt_approx(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
+
 // One collision in place on shifted populations.  BAND selects the
 // homogenized (HLBM) branch; the bulk branch is d = 1, sigma = 1.
 // Returns rho; u_out = fluid velocity of the pre-collision state.
@@ -189,7 +193,9 @@ __device__ __forceinline__ float collide(float (&g)[Q], const Band& B, float tau
         if (cy * cz != 0) pg[5] += float(cy * cz) * s;
     }
     const float rho = 1.0f + drho;
-    const float inv = 1.0f / rho;
+    // hardware reciprocal and reciprocal square root (about one ulp): the
+    // collision runs at the instruction-issue limit in its 16-bit D3Q27 form
+    const float inv = rcp_approx(rho);
     const float u[3] = {j[0] * inv, j[1] * inv, j[2] * inv};
     u_out[0] = u[0]; u_out[1] = u[1]; u_out[2] = u[2];
     // non-equilibrium stress Pi_neq = Pi - rho cs2 I - rho u u (fluid velocity)
@@ -200,8 +206,8 @@ __device__ __forceinline__ float collide(float (&g)[Q], const Band& B, float tau
     // tau = tau_mo + 3 C_S^2 |S|, S = -Pi_neq / (2 rho cs2 tau)
     const float Qn = N[0] * N[0] + N[1] * N[1] + N[2] * N[2] +
                      2.0f * (N[3] * N[3] + N[4] * N[4] + N[5] * N[5]);
-    const float tau = 0.5f * (tau_mo + sqrtf(tau_mo * tau_mo + Ksmag * sqrtf(Qn) * inv));
-    const float om = 1.0f - 1.0f / tau;
+    const float tau = 0.5f * (tau_mo + sqrt_approx(fmaf(Ksmag * sqrt_approx(Qn), inv, tau_mo * tau_mo)));
+    const float om = 1.0f - rcp_approx(tau);
     float uh[3] = {u[0], u[1], u[2]};
     float os = om;
     float A[6];
