@@ -110,6 +110,10 @@ def lib():
         L.or_freeze_sets.argtypes = [C.c_void_p, C.c_int]
         L.or_adjoint.restype = C.c_int
         L.or_adjoint.argtypes = [C.c_void_p, C.c_int, C.c_int, _dp, _dp, _dp, _dp, _dp]
+        L.or_set_drive.restype = C.c_int
+        L.or_set_drive.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_double]
+        L.or_drive_state.restype = C.c_int
+        L.or_drive_state.argtypes = [C.c_void_p, C.c_int, _dp, _dp]
         L.or_porosity_tangent.argtypes = [C.c_void_p, _dp]
         L.or_wall_tangent.argtypes = [C.c_void_p, _dp, _dp]
         L.or_rotor_normal_tangent.argtypes = [C.POINTER(Rotor), C.c_long, C.c_int, C.c_int, C.c_int,
@@ -409,6 +413,17 @@ class Oracle:
         if rc:
             raise ValueError(f"oracle adjoint failed ({rc})")
         return float(J[0]), gp[:self.nrot], gd0
+
+    def set_drive(self, k: int, inertia: float, k_gen: float = 0.0, q_gen0: float = 0.0):
+        """Torque-driven rotation of rotor k from now on (I dOmega/dt = M.a - Q_gen)."""
+        if lib().or_set_drive(self._h, int(k), float(inertia), float(k_gen), float(q_gen0)):
+            raise ValueError("bad rotor index or inertia")
+
+    def drive_state(self, k: int):
+        """(theta, Omega) of rotor k at the current step."""
+        th, om = C.c_double(), C.c_double()
+        lib().or_drive_state(self._h, int(k), C.byref(th), C.byref(om))
+        return th.value, om.value
 
     def porosity_tangent(self):
         """d(d_rotor)/d(pitch) of the last porosity update, shape (nz, ny, nx)."""

@@ -337,15 +337,20 @@ typedef struct {
 typedef struct {
     or_rotor r;
     float* sdf;          /* owned copy */
+    /* torque-driven rotation (listing "HHRRLBM-FSI", evolve structure):
+       angle and angular velocity are state, r.omega follows the state */
+    int driven;
+    double theta;        /* rotor angle of the current step */
+    double inertia, k_gen, q_gen0;
 } rotor_store;
 
 /* Per-blade binary32 frame: cos/sin of (theta + 2 pi k / n_blades) and of the
    pitch, rounded once from FP64. */
 typedef struct { float ck[8], sk[8], cp, sp; double ckd[8], skd[8], cpd, spd; } blade_frames;
 
-static void blade_frames_at(const or_rotor* R, long t, blade_frames* B)
+/* frames at rotor angle th (blade k at th + 2 pi k / n_blades) */
+static void blade_frames_theta(const or_rotor* R, double th, blade_frames* B)
 {
-    double th = R->phase0 + R->omega * (double)t;
     for (int k = 0; k < R->n_blades; ++k) {
         double ang = th + 2.0 * M_PI * (double)k / (double)R->n_blades;
         B->ckd[k] = cos(ang); B->skd[k] = sin(ang);
@@ -353,6 +358,18 @@ static void blade_frames_at(const or_rotor* R, long t, blade_frames* B)
     }
     B->cpd = cos(R->pitch); B->spd = sin(R->pitch);
     B->cp = (float)B->cpd; B->sp = (float)B->spd;
+}
+
+/* prescribed rotation: theta = theta0 + Omega t */
+static void blade_frames_at(const or_rotor* R, long t, blade_frames* B)
+{
+    blade_frames_theta(R, R->phase0 + R->omega * (double)t, B);
+}
+
+/* angle of rotor k at the current step: its state when torque-driven */
+static double rotor_angle(const rotor_store* rs, long t)
+{
+    return rs->driven ? rs->theta : rs->r.phase0 + rs->r.omega * (double)t;
 }
 
 static float lerpf_(float a, float b, float t) { return fmaf(t, b - a, a); }
@@ -630,10 +647,11 @@ static void update_porosity(or_state* S)
        (the same unless the sets are frozen for a finite-difference check) */
     blade_frames BF[OR_MAXROT], BD[OR_MAXROT];
     for (int k = 0; k < S->nrot; ++k) {
-        blade_frames_at(&S->rot[k].r, S->step, &BF[k]);
+        const double th = rotor_angle(&S->rot[k], S->step);
+        blade_frames_theta(&S->rot[k].r, th, &BF[k]);
         or_rotor rd = S->rot[k].r;
         if (S->frozen) rd.pitch = S->decision_pitch[k];
-        blade_frames_at(&rd, S->step, &BD[k]);
+        blade_frames_theta(&rd, th, &BD[k]);
     }
     #pragma omp parallel for schedule(static)
     for (int z = 0; z < P->nz; ++z)
@@ -952,6 +970,24 @@ void or_destroy(or_state* S)
     free(S);
 }
 
+/* Evolve structure (listing "HHRRLBM-FSI") for torque-driven rotors: rigid
+   rotation about the rotor axis, I dOmega/dt = Q_aero - Q_gen(Omega), with the
+   aerodynamic torque Q_aero = M . a of this step's momentum exchange and the
+   generator torque Q_gen = q_gen0 + k_gen Omega |Omega|; explicit Euler with
+   dt = 1: theta += Omega, then Omega += (Q_aero - Q_gen(Omega)) / I. */
+static void evolve_structure(or_state* S)
+{
+    for (int k = 0; k < S->nrot; ++k) {
+        rotor_store* rs = &S->rot[k];
+        if (!rs->driven) continue;
+        const double om = rs->r.omega;
+        const double q_aero = S->M[k][rs->r.axis];
+        const double q_gen = rs->q_gen0 + rs->k_gen * om * fabs(om);
+        rs->theta += om;
+        rs->r.omega = om + (q_aero - q_gen) / rs->inertia;
+    }
+}
+
 /* One time step, in the order of the listing "HHRRLBM-FSI": porosity update
    (kinematics theta = theta0 + Omega t), wall model, collide, boundary force,
    stream, time averages; then t += 1 (evolve structure). */
@@ -965,6 +1001,7 @@ void or_step(or_state* S, int n)
         stream_all(S);
         for (int k = 0; k < S->nrot; ++k)
             for (int a = 0; a < 3; ++a) { S->Fsum[k][a] += S->F[k][a]; S->Msum[k][a] += S->M[k][a]; }
+        evolve_structure(S);
         S->navg += 1;
         S->step += 1;
     }
@@ -1623,6 +1660,8 @@ int or_adjoint(or_state* S, int T, int n_avg, const double* wT, const double* wQ
     const int ax = P->flow_axis, bx = (ax + 1) % 3, cxx = (ax + 2) % 3;
     const size_t npl = (size_t)dims[bx] * dims[cxx];
     if (T < 1 || n_avg < 1 || n_avg > T) return -1;
+    for (int k = 0; k < S->nrot; ++k)
+        if (S->rot[k].driven) return -3;   /* gradients cover prescribed rotation only */
     or_tape tp;
     tp.f = (double*)malloc(sizeof(double) * (size_t)T * q * N);
     tp.wm_ut = (double*)malloc(sizeof(double) * (size_t)T * N);
@@ -2006,4 +2045,29 @@ void or_rotor_normal_tangent(const or_rotor* R, long t, int which, int x, int y,
     cplx pc = R->pitch + I * CSTEP, nc[3];
     rotor_normal_c(R, &BF, which, x, y, z, ccos(pc), csin(pc), nc);
     for (int k = 0; k < 3; ++k) dn[k] = cimag(nc[k]) / CSTEP;
+}
+
+
+/* Torque-driven rotation of rotor k from the current step on: moment of
+   inertia about the axis (> 0), generator torque q_gen0 + k_gen Omega |Omega|.
+   The rotor starts from its current angle and angular velocity. */
+int or_set_drive(or_state* S, int k, double inertia, double k_gen, double q_gen0)
+{
+    if (k < 0 || k >= S->nrot || !(inertia > 0.0)) return -1;
+    rotor_store* rs = &S->rot[k];
+    rs->theta = rotor_angle(rs, S->step);
+    rs->driven = 1;
+    rs->inertia = inertia;
+    rs->k_gen = k_gen;
+    rs->q_gen0 = q_gen0;
+    return 0;
+}
+
+/* angle and angular velocity of rotor k at the current step */
+int or_drive_state(const or_state* S, int k, double* theta, double* omega)
+{
+    if (k < 0 || k >= S->nrot) return -1;
+    *theta = rotor_angle(&S->rot[k], S->step);
+    *omega = S->rot[k].r.omega;
+    return 0;
 }
