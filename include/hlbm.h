@@ -193,6 +193,23 @@ hl_status hl_state_size(const hl_lattice* lat, size_t* bytes);
 hl_status hl_save_state(hl_lattice* lat, void* d_buf, size_t bytes);
 hl_status hl_load_state(hl_lattice* lat, const void* d_buf, size_t bytes);
 
+/* Torque-driven rotation ("evolve structure" of the listing "HHRRLBM-FSI"
+ * as a rigid rotor): from the next step on, rotor `rotor` turns with the
+ * angle and angular velocity it has now, advanced after every step by
+ *   theta += Omega;  Omega += (M . a - Q_gen(Omega)) / inertia,
+ *   Q_gen = q_gen0 + k_gen Omega |Omega|   (lattice units, dt = 1),
+ * with M the step's momentum-exchange torque about the rotor centre.  The
+ * state lives on the device (no host round trip per step) and is part of
+ * state snapshots.  inertia > 0 (HL_ERR_ARG otherwise).  Calling it again
+ * changes the parameters and keeps the state.  hl_grad rejects driven
+ * rotors (HL_ERR_STATE).  Synchronises. */
+hl_status hl_set_drive(hl_lattice* lat, int rotor, double inertia, double k_gen, double q_gen0);
+
+/* Angle (rad) and angular velocity (rad per step) of rotor `rotor` at the
+ * current step (host outputs); prescribed rotors report theta0 + Omega t.
+ * Synchronises. */
+hl_status hl_drive_state(hl_lattice* lat, int rotor, double* theta, double* omega);
+
 /* Box of rotor `rotor`: lo[3] first cell, n[3] extent (host outputs). */
 hl_status hl_rotor_box(const hl_lattice* lat, int rotor, int* lo, int* n);
 

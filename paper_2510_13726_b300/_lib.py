@@ -74,6 +74,8 @@ SIGNATURES = {
     "hl_velocity_set": (C.c_int, [C.c_int, _ip, _dp]),
     "hl_debug_collide": (C.c_int, [C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, C.c_double, C.c_double,
                                    _vp, _vp]),
+    "hl_set_drive": (C.c_int, [_vp, C.c_int, C.c_double, C.c_double, C.c_double]),
+    "hl_drive_state": (C.c_int, [_vp, C.c_int, _dp, _dp]),
     "hl_set_d0": (C.c_int, [_vp, _vp]),
     "hl_set_pitch": (C.c_int, [_vp, C.c_int, C.c_double]),
     "hl_freeze_sets": (C.c_int, [_vp, C.c_int]),

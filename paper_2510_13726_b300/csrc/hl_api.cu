@@ -393,6 +393,7 @@ hl_status hl_set_rotor(hl_lattice* lat, int* rotor_id, const hl_rotor_geometry* 
     D.done = reinterpret_cast<unsigned*>(R.ws + L.done);
     D.partial = reinterpret_cast<double*>(R.ws + L.partial);
     D.acc = reinterpret_cast<double*>(R.ws + L.acc);
+    D.drive = nullptr;
     HL_CUDA(lat, cudaMemsetAsync(R.ws, 0, L.total, lat->stream));
     if (geom->n_blades > 0)
         HL_CUDA(lat, cudaMemcpyAsync(R.ws + L.sdf, geom->sdf, sizeof(float) * ng, cudaMemcpyHostToDevice,
@@ -441,6 +442,7 @@ static hl_status step_serial(hl_lattice* lat, const StepArgs& a0, bool with_forc
             HL_CUDA(lat, prof_mark(lat, 2, st));
             HL_CUDA(lat, launch_force(Q, S, a, st));
             HL_CUDA(lat, prof_mark(lat, 2, st));
+            HL_CUDA(lat, launch_evolve(a, st));
         } else {
             for (int k = 0; k < lat->nrot; ++k)
                 HL_CUDA(lat, cudaMemsetAsync(lat->rot[k].dev.count, 0, 2 * sizeof(int), st));
@@ -490,6 +492,7 @@ static hl_status step_overlap(hl_lattice* lat, const StepArgs& a0, bool with_for
         HL_CUDA(lat, prof_mark(lat, 2, ax));
         HL_CUDA(lat, launch_force(Q, S, a, ax));
         HL_CUDA(lat, prof_mark(lat, 2, ax));
+        HL_CUDA(lat, launch_evolve(a, ax));
     } else {
         for (int k = 0; k < lat->nrot; ++k)
             HL_CUDA(lat, cudaMemsetAsync(lat->rot[k].dev.count, 0, 2 * sizeof(int), ax));
@@ -684,6 +687,7 @@ static size_t state_bytes(const hl_lattice* lat) {
         o = align_up(o + sizeof(double) * b);
         o = align_up(o + b);
         o = align_up(o + sizeof(double) * 12);
+        o = align_up(o + sizeof(DriveDev));
     }
     return o;
 }
@@ -722,6 +726,7 @@ static hl_status state_copy(hl_lattice* lat, char* buf, bool save) {
         HL_CUDA(lat, cp(D.utau, sizeof(double) * D.box_cells));
         HL_CUDA(lat, cp(D.active, (size_t)D.box_cells));
         HL_CUDA(lat, cp(D.acc, sizeof(double) * 12));
+        HL_CUDA(lat, cp(lat->rot[k].ws + lat->rot[k].L.drive, sizeof(DriveDev)));
     }
     return HL_OK;
 }
@@ -754,6 +759,57 @@ hl_status hl_load_state(hl_lattice* lat, const void* d_buf, size_t bytes) {
     if (st != HL_OK) return st;
     HL_CUDA(lat, cudaMemsetAsync(lat->err, 0, sizeof(unsigned), lat->stream));
     HL_CUDA(lat, cudaStreamSynchronize(lat->stream));
+    return HL_OK;
+}
+
+hl_status hl_set_drive(hl_lattice* lat, int rotor, double inertia, double k_gen, double q_gen0) {
+    if (!lat || rotor < 0 || rotor >= lat->nrot) return HL_ERR_ARG;
+    if (!(inertia > 0.0) || !std::isfinite(inertia) || !std::isfinite(k_gen) || !std::isfinite(q_gen0))
+        return fail(lat, HL_ERR_ARG, "hl_set_drive: inertia must be positive and finite");
+    RotorHost& R = lat->rot[rotor];
+    DriveDev h;
+    std::memset(&h, 0, sizeof h);
+    double th, om;
+    if (R.driven) {
+        HL_CUDA(lat, cudaMemcpyAsync(&h, R.ws + R.L.drive, sizeof h, cudaMemcpyDeviceToHost, lat->stream));
+        HL_CUDA(lat, cudaStreamSynchronize(lat->stream));
+        th = h.theta;
+        om = h.omega;
+    } else {
+        th = R.geom.phase0 + R.omega * (double)lat->t;
+        om = R.omega;
+    }
+    h.theta = th;
+    h.omega = om;
+    h.inertia = inertia;
+    h.k_gen = k_gen;
+    h.q_gen0 = q_gen0;
+    for (int b = 0; b < R.geom.n_blades; ++b) {
+        const double ang = th + 2.0 * M_PI * (double)b / (double)R.geom.n_blades;
+        h.ck[b] = (float)std::cos(ang);
+        h.sk[b] = (float)std::sin(ang);
+    }
+    h.omegaf = (float)om;
+    HL_CUDA(lat, cudaMemcpyAsync(R.ws + R.L.drive, &h, sizeof h, cudaMemcpyHostToDevice, lat->stream));
+    HL_CUDA(lat, cudaStreamSynchronize(lat->stream));
+    R.driven = true;
+    R.dev.drive = reinterpret_cast<DriveDev*>(R.ws + R.L.drive);
+    return HL_OK;
+}
+
+hl_status hl_drive_state(hl_lattice* lat, int rotor, double* theta, double* omega) {
+    if (!lat || rotor < 0 || rotor >= lat->nrot || !theta || !omega) return HL_ERR_ARG;
+    RotorHost& R = lat->rot[rotor];
+    if (!R.driven) {
+        *theta = R.geom.phase0 + R.omega * (double)lat->t;
+        *omega = R.omega;
+        return HL_OK;
+    }
+    DriveDev h;
+    HL_CUDA(lat, cudaMemcpyAsync(&h, R.ws + R.L.drive, sizeof h, cudaMemcpyDeviceToHost, lat->stream));
+    HL_CUDA(lat, cudaStreamSynchronize(lat->stream));
+    *theta = h.theta;
+    *omega = h.omega;
     return HL_OK;
 }
 

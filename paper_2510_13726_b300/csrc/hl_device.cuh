@@ -255,6 +255,15 @@ __device__ __forceinline__ float collide(float (&g)[Q], const Band& B, float tau
 constexpr int MAXROT = 8;
 constexpr int MAXBLADES = 8;
 
+// Torque-driven rotation (evolve structure): angle and angular velocity are
+// device state, advanced after each step's force reduction; the kernels of a
+// step read that step's frames from here instead of the launch parameters.
+struct DriveDev {
+    double theta, omega;        // angle and angular velocity of the current step
+    double inertia, k_gen, q_gen0;
+    float ck[MAXBLADES], sk[MAXBLADES], omegaf;   // frames of the current step
+};
+
 struct RotorDev {
     int lo[3], n[3];            // box of lattice cells that may be touched
     long long box_cells;
@@ -293,7 +302,13 @@ struct RotorDev {
     double* gut_prev;           // [box] adjoint of the previous step's friction velocity
     double* pacc;               // [PACC_SLOTS] pitch-gradient accumulators
     float wT, wQ;               // objective weights / n_avg for this step (0 outside the window)
+    DriveDev* drive;            // torque-driven rotor state, or null (prescribed rotation)
 };
+
+// frames and angular velocity of the current step
+__device__ __forceinline__ float rot_ck(const RotorDev& R, int k) { return R.drive ? R.drive->ck[k] : R.ck[k]; }
+__device__ __forceinline__ float rot_sk(const RotorDev& R, int k) { return R.drive ? R.drive->sk[k] : R.sk[k]; }
+__device__ __forceinline__ float rot_omega(const RotorDev& R) { return R.drive ? R.drive->omegaf : R.omega; }
 
 constexpr int PACC_SLOTS = 64;
 
@@ -334,8 +349,9 @@ __device__ __forceinline__ float rotor_phi(const RotorDev& R, float cp, float sp
     float best = __int_as_float(0x7f800000);
     which = -1;
     for (int k = 0; k < R.n_blades; ++k) {
-        const float pR = __fmaf_rn(R.ck[k], rb, __fmul_rn(R.sk[k], rc));
-        const float pT = __fmaf_rn(R.ck[k], rc, -__fmul_rn(R.sk[k], rb));
+        const float ck = rot_ck(R, k), sk = rot_sk(R, k);
+        const float pR = __fmaf_rn(ck, rb, __fmul_rn(sk, rc));
+        const float pT = __fmaf_rn(ck, rc, -__fmul_rn(sk, rb));
         const float qT = __fmaf_rn(cp, pT, -__fmul_rn(sp, ra));
         const float qA = __fmaf_rn(cp, ra, __fmul_rn(sp, pT));
         const float v = blade_sample(R, pR, qT, qA);
@@ -362,8 +378,9 @@ __device__ __forceinline__ float component_phi(const RotorDev& R, int which, int
         return __fsub_rn(__fsqrt_rn(r2), R.hub);
     }
     const int k = which;
-    const float pR = __fmaf_rn(R.ck[k], rb, __fmul_rn(R.sk[k], rc));
-    const float pT = __fmaf_rn(R.ck[k], rc, -__fmul_rn(R.sk[k], rb));
+    const float ck = rot_ck(R, k), sk = rot_sk(R, k);
+    const float pR = __fmaf_rn(ck, rb, __fmul_rn(sk, rc));
+    const float pT = __fmaf_rn(ck, rc, -__fmul_rn(sk, rb));
     const float qT = __fmaf_rn(R.cp, pT, -__fmul_rn(R.sp, ra));
     const float qA = __fmaf_rn(R.cp, ra, __fmul_rn(R.sp, pT));
     return blade_sample(R, pR, qT, qA);
@@ -378,7 +395,7 @@ __device__ inline void rotor_normal(const RotorDev& R, int which, int x, int y, 
     if (which >= R.n_blades) {
         v[0] = rl[0]; v[1] = rl[1]; v[2] = rl[2];
     } else {
-        const float ck = R.ck[which], sk = R.sk[which], cp = R.cp, sp = R.sp;
+        const float ck = rot_ck(R, which), sk = rot_sk(R, which), cp = R.cp, sp = R.sp;
         const float rb = rl[b], rc = rl[c], ra = rl[a];
         const float pR = ck * rb + sk * rc, pT = ck * rc - sk * rb;
         const float qT = cp * pT - sp * ra, qA = cp * ra + sp * pT;

@@ -747,6 +747,9 @@ hl_status hl_grad(hl_lattice* lat, int steps, int avg_last, int ckpt_every, cons
     if (steps < 1 || avg_last < 1 || avg_last > steps || ckpt_every < 1 || !w_thrust || !w_torque || !d_work)
         return fail(lat, HL_ERR_ARG, "hl_grad: invalid arguments");
     if (reinterpret_cast<size_t>(d_work) % ALIGN) return fail(lat, HL_ERR_ARG, "hl_grad: workspace not aligned");
+    for (int k = 0; k < lat->nrot; ++k)
+        if (lat->rot[k].driven)
+            return fail(lat, HL_ERR_STATE, "hl_grad: gradients cover prescribed rotation only (rotor is torque-driven)");
     const int T = steps, K = ckpt_every, na = avg_last;
     const GradLayout G = grad_layout(lat, T, K);
     if (bytes < G.total) return fail(lat, HL_ERR_WORKSPACE, "hl_grad: workspace too small");

@@ -44,7 +44,7 @@ inline Layout lattice_layout(const hl_config& c) {
 }
 
 struct RotorLayout {
-    size_t sdf, d, flags, wm, utau, active, list, wlist, wphi, wwhich, count, done, partial, acc, total;
+    size_t sdf, d, flags, wm, utau, active, list, wlist, wphi, wwhich, count, done, partial, acc, drive, total;
 };
 
 inline RotorLayout rotor_layout(long long ngrid, long long box) {
@@ -64,6 +64,7 @@ inline RotorLayout rotor_layout(long long ngrid, long long box) {
     L.done = o; o = align_up(o + sizeof(unsigned));
     L.partial = o; o = align_up(o + sizeof(double) * 6 * FORCE_BLOCKS);
     L.acc = o; o = align_up(o + sizeof(double) * 12);
+    L.drive = o; o = align_up(o + sizeof(DriveDev));
     L.total = o;
     return L;
 }
@@ -72,6 +73,7 @@ struct RotorHost {
     hl_rotor_geometry geom;
     double omega, pitch;
     double pitch_sets;       // pitch that decides the cell sets while they are frozen
+    bool driven;             // torque-driven rotation (device state at dev.drive)
     RotorDev dev;
     char* ws;
     RotorLayout L;

@@ -79,6 +79,7 @@ cudaError_t launch_collide(int Q, int storage, const StepArgs& a, cudaStream_t s
 cudaError_t launch_wall(int Q, int storage, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_force(int Q, int storage, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_mass(int Q, int storage, const MassArgs& m, cudaStream_t s);
+cudaError_t launch_evolve(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_init(int Q, int storage, const StepArgs& a, const float* rho, const float* u, float drho0,
                         const float u0[3], cudaStream_t s);
 cudaError_t launch_fields(int Q, int storage, const StepArgs& a, float* rho, float* u,

@@ -77,9 +77,10 @@ __device__ __forceinline__ void solid_velocity(const RotorDev& R, int x, int y, 
     const float r[3] = {(float)x - R.cf[0], (float)y - R.cf[1], (float)z - R.cf[2]};
     const int ax = R.axis;
     // u_s = Omega a x r: (a x r)_b = -r_c, (a x r)_c = r_b with (b, c) = (a+1, a+2)
-    if (ax == 0) { us[0] = 0.f; us[1] = -R.omega * r[2]; us[2] = R.omega * r[1]; }
-    else if (ax == 1) { us[1] = 0.f; us[2] = -R.omega * r[0]; us[0] = R.omega * r[2]; }
-    else { us[2] = 0.f; us[0] = -R.omega * r[1]; us[1] = R.omega * r[0]; }
+    const float om = rot_omega(R);
+    if (ax == 0) { us[0] = 0.f; us[1] = -om * r[2]; us[2] = om * r[1]; }
+    else if (ax == 1) { us[1] = 0.f; us[2] = -om * r[0]; us[0] = om * r[2]; }
+    else { us[2] = 0.f; us[0] = -om * r[1]; us[1] = om * r[0]; }
 }
 
 __device__ __forceinline__ int sel3(int ax, int a0, int a1, int a2) { return ax == 0 ? a0 : (ax == 1 ? a1 : a2); }
@@ -534,6 +535,30 @@ __global__ void __launch_bounds__(256) force_kernel(const StepArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// evolve structure (torque-driven rotors): rigid rotation about the axis,
+// I dOmega/dt = M.a - Q_gen(Omega), Q_gen = q_gen0 + k_gen Omega |Omega|,
+// explicit Euler (dt = 1) from this step's torque; then the next step's frames
+// ---------------------------------------------------------------------------
+__global__ void evolve_kernel(const StepArgs a) {
+    const int k = threadIdx.x;
+    if (k >= a.nrot) return;
+    const RotorDev& R = a.rot[k];
+    if (!R.drive) return;
+    DriveDev* D = R.drive;
+    const double om = D->omega;
+    const double q_aero = R.acc[3 + R.axis];
+    const double q_gen = D->q_gen0 + D->k_gen * om * fabs(om);
+    D->theta += om;
+    D->omega = om + (q_aero - q_gen) / D->inertia;
+    for (int b = 0; b < R.n_blades; ++b) {
+        const double ang = D->theta + 2.0 * M_PI * (double)b / (double)R.n_blades;
+        D->ck[b] = (float)cos(ang);
+        D->sk[b] = (float)sin(ang);
+    }
+    D->omegaf = (float)D->omega;
+}
+
+// ---------------------------------------------------------------------------
 // FP64 mass total (deterministic two-stage reduction) and drift check;
 // groups of 8 stored values are summed in FP32 first (16-byte loads)
 // ---------------------------------------------------------------------------
@@ -752,6 +777,14 @@ cudaError_t launch_wall(int Q, int S, const StepArgs& a, cudaStream_t s) {
 }
 cudaError_t launch_force(int Q, int S, const StepArgs& a, cudaStream_t s) {
     HL_DISPATCH(Q, S, launch_force_t, a, s);
+}
+
+cudaError_t launch_evolve(const StepArgs& a, cudaStream_t s) {
+    bool any = false;
+    for (int k = 0; k < a.nrot; ++k) any = any || a.rot[k].drive;
+    if (!any) return cudaSuccess;
+    evolve_kernel<<<1, 32, 0, s>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_mass(int Q, int S, const MassArgs& m, cudaStream_t s) {

@@ -231,6 +231,18 @@ class Lattice:
         with torch.cuda.device(self.device):
             self._check(lib().hl_load_state(self._h, buf.data_ptr(), buf.numel()))
 
+    # -- torque-driven rotors ---------------------------------------------------
+    def set_drive(self, k: int, inertia: float, k_gen: float = 0.0, q_gen0: float = 0.0):
+        """Rotor k turns under its aerodynamic torque from now on:
+        I dOmega/dt = M.a - (q_gen0 + k_gen Omega |Omega|)."""
+        self._check(lib().hl_set_drive(self._h, int(k), float(inertia), float(k_gen), float(q_gen0)))
+
+    def drive_state(self, k: int):
+        """(theta, Omega) of rotor k at the current step."""
+        th, om = C.c_double(), C.c_double()
+        self._check(lib().hl_drive_state(self._h, int(k), C.byref(th), C.byref(om)))
+        return th.value, om.value
+
     # -- gradients ------------------------------------------------------------
     def set_d0(self, d0):
         """Static porosity multiplier d0 (device tensor of N or (nz, ny, nx) floats; None = 1).

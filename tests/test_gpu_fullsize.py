@@ -1,7 +1,8 @@
 """Full-size parity: the 256x256x512 rotor workload (33.5M cells, 5 %
-turbulent inflow) and the 1536x512x1024 wind farm (805M cells, 6 rotors), in
-the launch configuration the benchmark times, compared with the FP64 oracle
-at sampled cells.
+turbulent inflow), the 512x512x1024 D3Q27 rotor of the storage study (FP32)
+and the 1536x512x1024 wind farm (805M cells, 6 rotors), in the launch
+configuration the benchmark times, compared with the FP64 oracle at sampled
+cells.
 
 After k steps a cell depends only on cells within a few lattice spacings
 (one cell per step for collide-and-stream, at most 4 per step where the wall
@@ -28,6 +29,8 @@ H = 4 * K + 2         # sub-box half-width (cells)
 def _shift_modes(modes, offset):
     """Modes of a sub-box whose local coordinates are global - offset:
     a cos(k.(x+o)) + b sin(k.(x+o)) = a' cos(k.x) + b' sin(k.x)."""
+    if modes is None:
+        return None
     m = np.array(modes, dtype=np.float64, copy=True)
     ph = m[:, 0:3] @ np.asarray(offset, dtype=np.float64)
     c, s = np.cos(ph)[:, None], np.sin(ph)[:, None]
@@ -54,7 +57,7 @@ def _oracle_at(wl, grids, cell):
     off = [float(lo[k]) for k in range(3)]
     off[a] = 0.0                    # the frozen-turbulence shift acts along the flow axis
     modes = _shift_modes(wl.modes(), off)
-    o = O.Oracle(n[0], n[1], n[2], flow_axis=a, open_boundaries=open_b, tau_mo=wl.tau_mo,
+    o = O.Oracle(n[0], n[1], n[2], q=wl.q, flow_axis=a, open_boundaries=open_b, tau_mo=wl.tau_mo,
                  c_smag=wl.c_smag, u_in=wl.u_in, eps_h=wl.eps_h, modes=modes, rotors=rotors)
     o.step(K)
     rho, u = o.fields()
@@ -70,8 +73,10 @@ def _samples(wl, grids, per_rotor_wall=10, per_rotor_solid=4, n_other=16):
     for spec, grid in zip(wl.rotors, grids):
         # cells that are wall cells or force cells during the run (oracle geometry)
         rot = O.make_rotor(grid, center=spec.center, axis=a, omega=spec.omega(wl.u_in), phase0=spec.phase0)
-        rng_ax = [np.arange(int(spec.center[k]) - 66, int(spec.center[k]) + 67) for k in range(3)]
-        rng_ax[a] = np.arange(int(spec.center[a]) - 10, int(spec.center[a]) + 11)
+        half = int(spec.radius) + 2
+        half_a = int(np.ceil(10 * spec.radius / 64))
+        rng_ax = [np.arange(int(spec.center[k]) - half, int(spec.center[k]) + half + 1) for k in range(3)]
+        rng_ax[a] = np.arange(int(spec.center[a]) - half_a, int(spec.center[a]) + half_a + 1)
         cand = np.stack(np.meshgrid(*rng_ax, indexing="ij"), -1).reshape(-1, 3)
         phi, _ = O.rotor_phi(rot, K - 1, cand)
         wall = cand[(phi >= 0) & (phi < 1)]
@@ -118,6 +123,12 @@ def _run_and_compare(wl):
 
 def test_fullsize_rotor256_sampled_parity():
     _run_and_compare(W.workload("rotor256"))
+
+
+def test_fullsize_rotor1024_q27_sampled_parity():
+    """The storage-study size in FP32 (512x512x1024 D3Q27, 268M cells, R = 128,
+    TSR 7): sampled cells at the rotor and near the inlet."""
+    _run_and_compare(W.workload("rotor1024_q27"))
 
 
 def test_fullsize_farm_sampled_parity():
