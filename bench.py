@@ -326,6 +326,7 @@ def run_cuda(args):
             line["storage_study"] = storage_study(dev, args.extra_steps)
             line["farm"] = farm_run(dev, args.extra_steps)
             line["adjoint"] = adjoint_run(dev, args.adjoint_steps, args.adjoint_steps // 4, 100)
+            line["driven_rotor"] = driven_run(dev, 200)
         print(json.dumps(line), flush=True)
     lat.close()
     return 0
@@ -382,6 +383,38 @@ def farm_run(dev, steps):
     r = timed_run(wl, "f32", steps, 5, dev)
     r["workload"] = "farm: 1536x512x1024 (805M cells) D3Q19 FP32, 6 rotors R=64, flow along x, 5% turbulence"
     return r
+
+
+def driven_run(dev, steps):
+    """rotor256 with the rotor turning under its own torque and a generator
+    law (evolve structure on the device) against the same steps prescribed."""
+    import torch
+    import workloads as W
+    from paper_2510_13726_b300 import Lattice
+    wl = W.workload("rotor256")
+    om0 = wl.rotors[0].omega(wl.u_in)
+    out = {"workload": "rotor256 with a torque-driven rotor (I = 1e6, generator k = 2e3)", "steps": steps}
+    for mode in ("prescribed", "driven"):
+        lat = Lattice.from_workload(wl, device=dev)
+        lat.step(5)
+        if mode == "driven":
+            lat.set_drive(0, 1e6, k_gen=2e3)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(lat.stream)
+        lat.step_async(steps)
+        e1.record(lat.stream)
+        e1.synchronize()
+        lat.check()
+        ms = e0.elapsed_time(e1) / steps
+        th, om = lat.drive_state(0)
+        out[mode] = {"MLUPS": round(wl.cells / ms / 1e3, 1), "ms_per_step": round(ms, 4),
+                     "omega_start": om0, "omega_end": om}
+        lat.close()
+        del lat
+        torch.cuda.empty_cache()
+    return out
 
 
 def adjoint_run(dev, steps, avg_last, ckpt_every):

@@ -1,0 +1,117 @@
+"""Grid-convergence analysis of the time-averaged thrust coefficient
+(Sec. 4: Definition "Thrust coefficient", the experimental order of
+convergence from a log-log regression, and Definition "Grid Convergence
+Index").
+
+The analysis functions are host arithmetic on a handful of numbers; the
+study driver runs the rotor on the GPU library at several resolutions of the
+synthetic rotor with the Reynolds number and the tip-speed ratio held fixed.
+"""
+
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+def thrust_coefficient(thrust: float, radius: float, u_inf: float, rho: float = 1.0) -> float:
+    """C_T = T / (1/2 rho pi r^2 U_inf^2) (Sec. 4, Definition "Thrust coefficient")."""
+    return thrust / (0.5 * rho * math.pi * radius * radius * u_inf * u_inf)
+
+
+def eoc(h, err) -> float:
+    """Experimental order of convergence: slope of the least-squares line
+    through (log h, log err) (Sec. 4, grid convergence analysis)."""
+    h = np.asarray(h, dtype=np.float64)
+    err = np.asarray(err, dtype=np.float64)
+    slope, _ = np.polyfit(np.log(h), np.log(err), 1)
+    return float(slope)
+
+
+def apparent_order(f1: float, f2: float, f3: float, r: float) -> float:
+    """Order p from three grids with a constant refinement ratio r (f1 finest):
+    (f3 - f2) / (f2 - f1) = r^p for f(h) = f* + C h^p."""
+    return math.log(abs((f3 - f2) / (f2 - f1))) / math.log(r)
+
+
+def gci(f1: float, f2: float, r: float, p: float, fs: float = 1.25) -> float:
+    """Grid Convergence Index of the fine-grid value f1 (Sec. 4, Definition
+    "Grid Convergence Index"): F_s |(f2 - f1) / f1| / (r^p - 1), r = h2 / h1 > 1."""
+    return fs * abs((f2 - f1) / f1) / (r ** p - 1.0)
+
+
+def study_workload(radius: int, tsr: float = 6.0, u_in: float = 0.05, tau_ref: float = 0.5005,
+                   radius_ref: int = 32):
+    """The synthetic rotor at resolution `radius` (cells per rotor radius):
+    lattice 4R x 4R x 8R, rotor a quarter of the length downstream of the
+    inlet, uniform inflow.  Reynolds number and tip-speed ratio are those of
+    the reference resolution: nu scales with R (tau - 1/2 = (tau_ref - 1/2) R / R_ref)."""
+    from workloads.configs import Workload, _single
+    n = 4 * radius
+    tau = 0.5 + (tau_ref - 0.5) * radius / radius_ref
+    return Workload(f"convergence_R{radius}", n, n, 2 * n, steps=0, tau_mo=tau, u_in=u_in,
+                    rotors=_single(n, n, 2 * n, float(radius), tsr))
+
+
+def run_study(radii=(16, 32, 64, 128), revolutions_spinup: float = 3.0, revolutions_avg: float = 2.0,
+              device=None, progress=None):
+    """C_T averaged over whole revolutions after a spin-up, at each resolution,
+    on the GPU library.  Returns a dict with per-resolution results, the EOC
+    against the finest grid and the GCI of the finest grid from the three
+    finest (constant refinement ratio)."""
+    import torch
+    from paper_2510_13726_b300 import Lattice
+    rows = []
+    for R in radii:
+        wl = study_workload(R)
+        om = wl.rotors[0].omega(wl.u_in)
+        steps_rev = 2.0 * math.pi / om
+        n_spin = int(round(revolutions_spinup * steps_rev))
+        n_avg = int(round(revolutions_avg * steps_rev))
+        lat = Lattice.from_workload(wl, device=device)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(lat.stream)
+        lat.step(n_spin)
+        lat.forces(reset_avg=True)
+        lat.step(n_avg)
+        t1.record(lat.stream)
+        t1.synchronize()
+        _, Fa = lat.forces()
+        T = float(Fa[0, wl.flow_axis])
+        ms = t0.elapsed_time(t1)
+        rows.append({"R": R, "cells": wl.cells, "tau": wl.tau_mo, "steps": n_spin + n_avg,
+                     "thrust": T, "C_T": thrust_coefficient(T, R, wl.u_in), "seconds": round(ms / 1e3, 2)})
+        if progress:
+            progress(rows[-1])
+        lat.close()
+        del lat
+        torch.cuda.empty_cache()
+    out = {"resolutions": rows}
+    ct = [r["C_T"] for r in rows]
+    if len(rows) >= 3:
+        h = [1.0 / r["R"] for r in rows[:-1]]
+        err = [abs(c - ct[-1]) for c in ct[:-1]]
+        if all(e > 0 for e in err):
+            out["eoc"] = eoc(h, err)
+        r = rows[-1]["R"] / rows[-2]["R"]
+        p = apparent_order(ct[-1], ct[-2], ct[-3], r)
+        out["apparent_order"] = p
+        out["gci_finest"] = gci(ct[-1], ct[-2], r, p)
+    return out
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+    import sys
+    ap = argparse.ArgumentParser(description="grid-convergence study of the synthetic rotor on one GPU")
+    ap.add_argument("--radii", default="16,32,64,128")
+    ap.add_argument("--spinup", type=float, default=3.0, help="revolutions before averaging")
+    ap.add_argument("--average", type=float, default=2.0, help="revolutions averaged")
+    args = ap.parse_args()
+    radii = tuple(int(v) for v in args.radii.split(","))
+    res = run_study(radii, args.spinup, args.average,
+                    progress=lambda row: print(json.dumps(row), file=sys.stderr, flush=True))
+    print(json.dumps(res))

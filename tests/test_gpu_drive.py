@@ -122,3 +122,14 @@ def test_driven_snapshot_resume_and_gradient_refusal(P):
     with pytest.raises(P.HlError) as e:
         lat.grad(4, 2, [1.0], [0.0], ckpt_every=2)
     assert e.value.code == -5
+
+
+def test_convergence_study_driver(P):
+    """The grid-convergence driver on three resolutions (one revolution
+    of spin-up, one averaged): finite thrust coefficients and the derived
+    orders and index."""
+    from paper_2510_13726_b300 import convergence as C
+    res = C.run_study(radii=(16, 32, 64), revolutions_spinup=1.0, revolutions_avg=1.0)
+    ct = [r["C_T"] for r in res["resolutions"]]
+    assert all(np.isfinite(ct)) and all(c > 0 for c in ct)
+    assert np.isfinite(res["apparent_order"]) and res["gci_finest"] >= 0.0
