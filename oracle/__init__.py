@@ -115,6 +115,7 @@ def lib():
         L.or_drive_state.restype = C.c_int
         L.or_drive_state.argtypes = [C.c_void_p, C.c_int, _dp, _dp]
         L.or_porosity_tangent.argtypes = [C.c_void_p, _dp]
+        L.or_fd_strain.argtypes = [C.c_void_p, _dp]
         L.or_wall_tangent.argtypes = [C.c_void_p, _dp, _dp]
         L.or_rotor_normal_tangent.argtypes = [C.POINTER(Rotor), C.c_long, C.c_int, C.c_int, C.c_int,
                                               C.c_int, _dp]
@@ -424,6 +425,12 @@ class Oracle:
         th, om = C.c_double(), C.c_double()
         lib().or_drive_state(self._h, int(k), C.byref(th), C.byref(om))
         return th.value, om.value
+
+    def fd_strain(self):
+        """Central-difference rate of strain of the current velocity field, (nz, ny, nx, 3, 3)."""
+        out = np.zeros(self.shape + (3, 3))
+        lib().or_fd_strain(self._h, _ptr(out))
+        return out
 
     def porosity_tangent(self):
         """d(d_rotor)/d(pitch) of the last porosity update, shape (nz, ny, nx)."""

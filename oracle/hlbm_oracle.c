@@ -32,6 +32,10 @@
  *  - a1^(3) follows the recursion a1_abg = u_a a1_bg + u_b a1_ag + u_g a1_ab
  *    with a1^(2) = Pi_neq taken against the fluid velocity u;
  *  - f(1,FD) = w_i rho tau_eff / cs^2 H2 : S_FD;
+ *  - away from wall cells, S_FD of a band cell with sigma < 1 is the
+ *    symmetric part of the velocity gradient by central differences of the
+ *    pre-collision velocity j/rho of the six axis neighbours (periodic
+ *    wrap laterally; one-sided where a neighbour is across an open face);
  *  - tau_eff is the positive root of tau = tau_mo + 3 C_S^2 |S| with
  *    S = -Pi_neq / (2 rho cs^2 tau) and |S| = sqrt(2 S:S);
  *  - the transition function is a smoothstep t^2 (3 - 2t), t = phi/eps + 1/2
@@ -772,6 +776,34 @@ static void wall_model(or_state* S)
 /* Band parameters of interior cell o at (x, y, z) for this step's collision:
    d = d0 d_rotor (d0 = static multiplier, 1 unless set), u^B = u_s + du_WM,
    sigma, S^FD (Sec. 2.2, 2.2.1; d_rotor = 1 and u^B = 0 outside the force set). */
+/* Finite-difference rate of strain of the fluid velocity at (x, y, z):
+   S = (grad u + grad u^T) / 2 with central differences of u = j / rho of the
+   pre-collision populations of the six axis neighbours (one-sided where a
+   neighbour lies across an open face); the non-local strain of the hybrid
+   non-equilibrium part (Sec. 2.2, f^(1,FD)). */
+static void fd_strain(const or_state* S, int x, int y, int z, double Sfd[3][3])
+{
+    const int xi[3] = {x, y, z};
+    double u0[3];
+    cell_velocity(S, cidx(S, x, y, z), u0, NULL);
+    double g[3][3];
+    for (int a = 0; a < 3; ++a) {
+        int e[3] = {0, 0, 0};
+        e[a] = 1;
+        int xp[3], xm[3];
+        const int okp = neighbour(S, xi, e, +1, xp), okm = neighbour(S, xi, e, -1, xm);
+        double up[3], um[3];
+        if (okp) cell_velocity(S, cidx(S, xp[0], xp[1], xp[2]), up, NULL);
+        else for (int b = 0; b < 3; ++b) up[b] = u0[b];
+        if (okm) cell_velocity(S, cidx(S, xm[0], xm[1], xm[2]), um, NULL);
+        else for (int b = 0; b < 3; ++b) um[b] = u0[b];
+        const double h = (okp && okm) ? 2.0 : 1.0;
+        for (int b = 0; b < 3; ++b) g[a][b] = (up[b] - um[b]) / h;
+    }
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) Sfd[a][b] = 0.5 * (g[a][b] + g[b][a]);
+}
+
 static void band_of_cell(const or_state* S, size_t o, int x, int y, int z, cell_band* B)
 {
     const or_params* P = &S->P;
@@ -789,6 +821,8 @@ static void band_of_cell(const or_state* S, size_t o, int x, int y, int z, cell_
             for (int p = 0; p < 3; ++p)
                 for (int q = 0; q < 3; ++q) B->Sfd[p][q] = S->wm_S[9 * o + 3 * p + q];
             B->sigma = 0.0;
+        } else if (P->sigma_band < 1.0) {
+            fd_strain(S, x, y, z, B->Sfd);
         }
     }
 }
@@ -1662,6 +1696,7 @@ int or_adjoint(or_state* S, int T, int n_avg, const double* wT, const double* wQ
     if (T < 1 || n_avg < 1 || n_avg > T) return -1;
     for (int k = 0; k < S->nrot; ++k)
         if (S->rot[k].driven) return -3;   /* gradients cover prescribed rotation only */
+    if (P->sigma_band < 1.0) return -3;    /* and the local (sigma = 1) band collision */
     or_tape tp;
     tp.f = (double*)malloc(sizeof(double) * (size_t)T * q * N);
     tp.wm_ut = (double*)malloc(sizeof(double) * (size_t)T * N);
@@ -2070,4 +2105,21 @@ int or_drive_state(const or_state* S, int k, double* theta, double* omega)
     *theta = rotor_angle(&S->rot[k], S->step);
     *omega = S->rot[k].r.omega;
     return 0;
+}
+
+
+/* finite-difference strain of every cell of the current state, [N][3][3] */
+void or_fd_strain(const or_state* S, double* out)
+{
+    const or_params* P = &S->P;
+    #pragma omp parallel for schedule(static)
+    for (int z = 0; z < P->nz; ++z)
+        for (int y = 0; y < P->ny; ++y)
+            for (int x = 0; x < P->nx; ++x) {
+                double Sm[3][3];
+                fd_strain(S, x, y, z, Sm);
+                double* o = out + 9 * cidx(S, x, y, z);
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b) o[3 * a + b] = Sm[a][b];
+            }
 }
