@@ -40,8 +40,9 @@ typedef int hl_status;
 #define HL_ERR_WORKSPACE (-4)   /* workspace or buffer smaller than required */
 #define HL_ERR_STATE (-5)       /* call not valid in the current state */
 #define HL_ERR_MASS (-8)        /* total mass drifted beyond mass_tol */
-#define HL_ERR_GEOMETRY (-9)    /* a wall-model sample point left its rotor's box: the blade
-                                   grid needs more padding (the cell was left unmodelled) */
+#define HL_ERR_GEOMETRY (-9)    /* a wall-model sample point or a band-strain stencil left its
+                                   rotor's box: the blade grid needs more padding (the cell
+                                   was left unmodelled) */
 
 #define HL_STORE_F32 0          /* populations stored as FP32 of f_i - w_i */
 #define HL_STORE_F16S 1         /* populations stored as FP16 of f_i - w_i */
@@ -59,9 +60,13 @@ typedef int hl_status;
  *                  Eqs. (turbVisc), (tauEff)
  *  u_in            inflow speed along +flow_axis (the initial state is the
  *                  equilibrium at this velocity)
- *  sigma_band      hybridisation factor of non-wall band cells (only 1.0 is
- *                  supported: the finite-difference strain is provided on
- *                  wall cells by the wall model)
+ *  sigma_band      hybridisation factor of the band cells off the wall set,
+ *                  0 <= sigma_band <= 1 (Sec. 2.2, hybrid non-equilibrium):
+ *                  below 1 their non-equilibrium part mixes in the
+ *                  Chapman-Enskog term of the finite-difference strain
+ *                  (central differences of the pre-collision velocity of
+ *                  the six axis neighbours); wall cells use sigma = 0 with
+ *                  the wall model's strain; hl_grad needs sigma_band = 1
  *  eps_h           width of the porosity transition (Definition "Lattice Porosity")
  *  transition      0 smoothstep t^2 (3 - 2t), 1 linear s = phi/eps + 1/2
  *  wall_model      1: Spalding wall function on the wall cells (Sec. 2.2.1)
@@ -272,7 +277,8 @@ hl_status hl_grad_workspace_size(const hl_lattice* lat, int steps, int ckpt_ever
  * spacing (memory vs. one recomputed forward step per step).  d_work:
  * caller's device workspace of hl_grad_workspace_size bytes, 256-byte
  * aligned, overwritten.  Synchronises; HL_ERR_NONFINITE / HL_ERR_MASS as
- * hl_step. */
+ * hl_step; HL_ERR_STATE for a torque-driven rotor or sigma_band < 1 (the
+ * derivative covers prescribed rotation and the local band collision). */
 hl_status hl_grad(hl_lattice* lat, int steps, int avg_last, int ckpt_every, const double* w_thrust,
                   const double* w_torque, double* J, double* dJ_dpitch, float* d_dJ_dd0, void* d_work,
                   size_t bytes);

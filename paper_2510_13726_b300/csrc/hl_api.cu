@@ -38,7 +38,7 @@ bool valid_config(const hl_config* c) {
     if (c->storage < 0 || c->storage > 2) return false;
     if (c->flow_axis < 0 || c->flow_axis > 2) return false;
     if (!(c->tau_mo > 0.5) || !(c->c_smag >= 0.0) || !(c->eps_h > 0.0)) return false;
-    if (c->sigma_band != 1.0) return false;
+    if (!(c->sigma_band >= 0.0 && c->sigma_band <= 1.0)) return false;
     if (c->n_modes < 0 || (c->n_modes > 0 && !c->modes)) return false;
     if (c->wm_maxit < 0 || c->wm_maxit > 1000 || !(c->wm_ysample > 0.0)) return false;
     if (c->mass_check_every < 0) return false;
@@ -133,7 +133,7 @@ hl_status read_error_word(hl_lattice* lat) {
     if (e & ERR_NONFINITE) return fail(lat, HL_ERR_NONFINITE, "non-finite density on the device");
     if (e & ERR_MASS) return fail(lat, HL_ERR_MASS, "total mass drifted beyond mass_tol");
     if (e & ERR_GEOMETRY)
-        return fail(lat, HL_ERR_GEOMETRY, "a wall-model sample left the rotor box: pad the blade grid");
+        return fail(lat, HL_ERR_GEOMETRY, "a wall-model sample or a band-strain stencil left the rotor box: pad the blade grid");
     return HL_OK;
 }
 
@@ -427,6 +427,7 @@ static hl_status step_serial(hl_lattice* lat, const StepArgs& a0, bool with_forc
     if (lat->nrot > 0) {
         HL_CUDA(lat, prof_mark(lat, 0, st));
         HL_CUDA(lat, launch_band(Q, S, a, st));
+        HL_CUDA(lat, launch_band_strain(Q, S, a, st));
         HL_CUDA(lat, prof_mark(lat, 0, st));
         if (lat->cfg.wall_model) {
             HL_CUDA(lat, prof_mark(lat, 4, st));
@@ -472,6 +473,7 @@ static hl_status step_overlap(hl_lattice* lat, const StepArgs& a0, bool with_for
     // aux stream: embedding, wall model, box collision, force
     HL_CUDA(lat, prof_mark(lat, 0, ax));
     HL_CUDA(lat, launch_band(Q, S, a, ax));
+    HL_CUDA(lat, launch_band_strain(Q, S, a, ax));
     HL_CUDA(lat, prof_mark(lat, 0, ax));
     if (lat->cfg.wall_model) {
         HL_CUDA(lat, prof_mark(lat, 4, ax));

@@ -750,6 +750,8 @@ hl_status hl_grad(hl_lattice* lat, int steps, int avg_last, int ckpt_every, cons
     for (int k = 0; k < lat->nrot; ++k)
         if (lat->rot[k].driven)
             return fail(lat, HL_ERR_STATE, "hl_grad: gradients cover prescribed rotation only (rotor is torque-driven)");
+    if (lat->cfg.sigma_band != 1.0)
+        return fail(lat, HL_ERR_STATE, "hl_grad: gradients cover the local band collision only (sigma_band = 1)");
     const int T = steps, K = ckpt_every, na = avg_last;
     const GradLayout G = grad_layout(lat, T, K);
     if (bytes < G.total) return fail(lat, HL_ERR_WORKSPACE, "hl_grad: workspace too small");

@@ -48,7 +48,7 @@ struct StepArgs {
     float wmYs;
     double wmE, wmK, wmTol, nu;      // wall-function solve runs in FP64
     int wmMaxit;
-    float sigma_band;
+    float sigma_band;        // hybridisation factor of the force cells off the wall set
     const float* modes;      // [n_modes][9]
     int n_modes;
     const float* uplane_prev;  // [3][plane]
@@ -77,6 +77,7 @@ struct MassArgs {
 cudaError_t launch_band(int Q, int storage, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_collide(int Q, int storage, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_wall(int Q, int storage, const StepArgs& a, cudaStream_t s);
+cudaError_t launch_band_strain(int Q, int storage, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_force(int Q, int storage, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_mass(int Q, int storage, const MassArgs& m, cudaStream_t s);
 cudaError_t launch_evolve(const StepArgs& a, cudaStream_t s);

@@ -135,7 +135,8 @@ __device__ __forceinline__ void collide_cell(const StepArgs& a, int x, int y, in
             } else {
                 B.uB[0] = B.uB[1] = B.uB[2] = 0.0f;
             }
-            B.sigma = a.sigma_band;
+            // hybrid non-equilibrium on the force cells only (sigma = 1 elsewhere)
+            B.sigma = (fl & FL_B) ? a.sigma_band : 1.0f;
 #pragma unroll
             for (int k = 0; k < 6; ++k) B.S[k] = 0.0f;
             if (a.wall_model && (fl & FL_W)) {
@@ -147,6 +148,12 @@ __device__ __forceinline__ void collide_cell(const StepArgs& a, int x, int y, in
 #pragma unroll
                 for (int k = 0; k < 6; ++k) B.S[k] = wm[(3 + k) * bc];
                 B.sigma = 0.0f;
+            } else if ((fl & FL_B) && a.sigma_band < 1.0f) {
+                // finite-difference strain of the band-strain kernel
+                const float* wm = R.wm + bi;
+                const long long bc = R.box_cells;
+#pragma unroll
+                for (int k = 0; k < 6; ++k) B.S[k] = wm[(3 + k) * bc];
             }
             rho = collide<Q, true>(g, B, a.tau_mo, a.Ksmag, u);
         } else if (D0) {
@@ -432,6 +439,54 @@ __global__ void __launch_bounds__(128) wall_kernel(const StepArgs a) {
         wm[8 * B] = gs * (th[1] * n[2] + n[1] * th[2]);
         R.active[bi] = 1;
         R.utau[bi] = utau;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// finite-difference strain across the band (Sec. 2.2, hybrid non-equilibrium
+// with sigma < 1): on the force cells off the wall set, S = (grad u +
+// grad u^T) / 2 by central differences of the pre-collision velocity of the
+// six axis neighbours, stored in rows 3..8 (xx yy zz xy xz yz) of the cell's
+// wall-model record, which the box collision reads
+// ---------------------------------------------------------------------------
+template <int Q, int S, int PH>
+__global__ void __launch_bounds__(128) band_strain_kernel(const StepArgs a) {
+    const RotorDev& R = a.rot[blockIdx.y];
+    int count = *((volatile int*)R.count);
+    if ((long long)count > R.box_cells) count = (int)R.box_cells;
+    const long long B = R.box_cells;
+    for (int idx = list_first(); idx < count; idx += list_stride()) {
+        const long long bi = R.list[idx];
+        if (a.wall_model && (R.flags[bi] & FL_W)) continue;
+        const int bx = (int)(bi % R.n[0]);
+        const long long r2 = bi / R.n[0];
+        const int by = (int)(r2 % R.n[1]);
+        const int bz = (int)(r2 / R.n[1]);
+        float* wm = R.wm + bi;
+        // the stencil must lie in the rotor box: the bulk launch updates every
+        // cell outside it at the same time
+        if (bx < 1 || by < 1 || bz < 1 || bx > R.n[0] - 2 || by > R.n[1] - 2 || bz > R.n[2] - 2) {
+            atomicOr(a.err, ERR_GEOMETRY);
+#pragma unroll
+            for (int k = 3; k < 9; ++k) wm[k * B] = 0.f;
+            continue;
+        }
+        const int x = R.lo[0] + bx, y = R.lo[1] + by, z = R.lo[2] + bz;
+        float gr[3][3];   // gr[m][b] = d u_b / d x_m
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            float up[3], um[3];
+            cell_velocity<Q, S, PH>(a, x + (m == 0), y + (m == 1), z + (m == 2), up);
+            cell_velocity<Q, S, PH>(a, x - (m == 0), y - (m == 1), z - (m == 2), um);
+#pragma unroll
+            for (int b = 0; b < 3; ++b) gr[m][b] = 0.5f * (up[b] - um[b]);
+        }
+        wm[3 * B] = gr[0][0];
+        wm[4 * B] = gr[1][1];
+        wm[5 * B] = gr[2][2];
+        wm[6 * B] = 0.5f * (gr[0][1] + gr[1][0]);
+        wm[7 * B] = 0.5f * (gr[0][2] + gr[2][0]);
+        wm[8 * B] = 0.5f * (gr[1][2] + gr[2][1]);
     }
 }
 
@@ -747,6 +802,15 @@ static cudaError_t launch_wall_t(const StepArgs& a, cudaStream_t s) {
 }
 
 template <int Q, int S>
+static cudaError_t launch_band_strain_t(const StepArgs& a, cudaStream_t s) {
+    if (a.nrot == 0 || !(a.sigma_band < 1.0f)) return cudaSuccess;
+    const dim3 grd(WALL_BLOCKS, a.nrot);
+    if (a.phase == 0) band_strain_kernel<Q, S, 0><<<grd, WALL_THREADS, 0, s>>>(a);
+    else band_strain_kernel<Q, S, 1><<<grd, WALL_THREADS, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int Q, int S>
 static cudaError_t launch_force_t(const StepArgs& a, cudaStream_t s) {
     if (a.nrot == 0) return cudaSuccess;
     const dim3 grd(FORCE_BLOCKS, a.nrot);
@@ -774,6 +838,9 @@ cudaError_t launch_band(int Q, int S, const StepArgs& a, cudaStream_t s) {
 }
 cudaError_t launch_wall(int Q, int S, const StepArgs& a, cudaStream_t s) {
     HL_DISPATCH(Q, S, launch_wall_t, a, s);
+}
+cudaError_t launch_band_strain(int Q, int S, const StepArgs& a, cudaStream_t s) {
+    HL_DISPATCH(Q, S, launch_band_strain_t, a, s);
 }
 cudaError_t launch_force(int Q, int S, const StepArgs& a, cudaStream_t s) {
     HL_DISPATCH(Q, S, launch_force_t, a, s);

@@ -29,7 +29,7 @@ class Lattice:
 
     def __init__(self, nx, ny, nz, q=19, storage="f32", flow_axis=2, open_boundaries=True,
                  tau_mo=0.5005, c_smag=0.1, u_in=0.05, eps_h=2.0, transition="smoothstep",
-                 wall_model=True, wm_E=9.8, wm_kappa=0.41, wm_ysample=2.0, wm_tol=1e-4,
+                 sigma_band=1.0, wall_model=True, wm_E=9.8, wm_kappa=0.41, wm_ysample=2.0, wm_tol=1e-4,
                  wm_maxit=10, modes=None, mass_check_every=100, mass_tol=0.05, overlap=True,
                  device=None, stream=None):
         import torch
@@ -45,6 +45,7 @@ class Lattice:
         cfg.open_boundaries = int(bool(open_boundaries))
         cfg.tau_mo, cfg.c_smag, cfg.u_in, cfg.eps_h = float(tau_mo), float(c_smag), float(u_in), float(eps_h)
         cfg.transition = 1 if transition == "linear" else 0
+        cfg.sigma_band = float(sigma_band)
         cfg.wall_model = int(bool(wall_model))
         cfg.wm_E, cfg.wm_kappa, cfg.wm_ysample = float(wm_E), float(wm_kappa), float(wm_ysample)
         cfg.wm_tol, cfg.wm_maxit = float(wm_tol), int(wm_maxit)
