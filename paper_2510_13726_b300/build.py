@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 SOURCES = [os.path.join(CSRC, f) for f in ("hl_kernels.cu", "hl_api.cu", "hl_grad.cu", "hl_noalloc.cu")]
-HEADERS = [os.path.join(CSRC, f) for f in ("hl_device.cuh", "hl_adjoint.cuh", "hl_internal.h", "hl_host.h")] + [
+HEADERS = [os.path.join(CSRC, f) for f in ("hl_device.cuh", "hl_adjoint.cuh", "hl_pair.cuh", "hl_internal.h", "hl_host.h")] + [
     os.path.join(ROOT, "include", "hlbm.h")]
 LIB = os.path.join(HERE, "libhlbm.so")
 NVCC = os.environ.get("NVCC", "nvcc")

@@ -63,6 +63,13 @@ void set_shifted_bases(StepArgs* a, int q, int esize) {
         a->rshift[s] = reinterpret_cast<const void*>(reinterpret_cast<uintptr_t>(a->slot[sbar]) - D * esize);
         a->wshift[s] = reinterpret_cast<void*>(reinterpret_cast<uintptr_t>(a->wslot[s]) + D * esize);
     }
+    // packed cell pairs need two-element alignment of every pair they touch:
+    // x even, and with nx (hence nx * ny) even a shift by c_s keeps the parity of c_x
+    bool pairs = a->n[0] % 2 == 0;
+    for (int s = 0; s < q; ++s)
+        pairs = pairs && reinterpret_cast<uintptr_t>(a->slot[s]) % (2 * esize) == 0 &&
+                reinterpret_cast<uintptr_t>(a->wslot[s]) % (2 * esize) == 0;
+    a->pairs = pairs ? 1 : 0;
 }
 
 StepArgs make_args(const hl_lattice* lat) {

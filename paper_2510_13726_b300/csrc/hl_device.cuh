@@ -341,11 +341,16 @@ __device__ __forceinline__ float blade_sample(const RotorDev& R, float pR, float
 
 // Signed distance of cell (x,y,z) to the rotor at pitch frames (cp, sp);
 // which = blade, or n_blades for the hub.
+// Component of (v0, v1, v2) along axis k (selects, no local-memory indexing).
+__device__ __forceinline__ float fsel3(int k, float v0, float v1, float v2) {
+    return k == 0 ? v0 : (k == 1 ? v1 : v2);
+}
+
 __device__ __forceinline__ float rotor_phi(const RotorDev& R, float cp, float sp, int x, int y, int z, int& which) {
-    const float rl[3] = {__fsub_rn((float)x, R.cf[0]), __fsub_rn((float)y, R.cf[1]),
-                         __fsub_rn((float)z, R.cf[2])};
-    const int a = R.axis, b = (a + 1) % 3, c = (a + 2) % 3;
-    const float rb = rl[b], rc = rl[c], ra = rl[a];
+    const float r0 = __fsub_rn((float)x, R.cf[0]), r1 = __fsub_rn((float)y, R.cf[1]),
+                r2l = __fsub_rn((float)z, R.cf[2]);
+    const int a = R.axis, b = a == 2 ? 0 : a + 1, c = a == 0 ? 2 : a - 1;
+    const float rb = fsel3(b, r0, r1, r2l), rc = fsel3(c, r0, r1, r2l), ra = fsel3(a, r0, r1, r2l);
     float best = __int_as_float(0x7f800000);
     which = -1;
     for (int k = 0; k < R.n_blades; ++k) {
@@ -369,10 +374,10 @@ __device__ __forceinline__ float rotor_phi(const RotorDev& R, float cp, float sp
 // current pitch frames, with the operations of rotor_phi: for the component
 // that attains the minimum the two agree bit for bit.
 __device__ __forceinline__ float component_phi(const RotorDev& R, int which, int x, int y, int z) {
-    const float rl[3] = {__fsub_rn((float)x, R.cf[0]), __fsub_rn((float)y, R.cf[1]),
-                         __fsub_rn((float)z, R.cf[2])};
-    const int a = R.axis, b = (a + 1) % 3, c = (a + 2) % 3;
-    const float rb = rl[b], rc = rl[c], ra = rl[a];
+    const float r0 = __fsub_rn((float)x, R.cf[0]), r1 = __fsub_rn((float)y, R.cf[1]),
+                r2l = __fsub_rn((float)z, R.cf[2]);
+    const int a = R.axis, b = a == 2 ? 0 : a + 1, c = a == 0 ? 2 : a - 1;
+    const float rb = fsel3(b, r0, r1, r2l), rc = fsel3(c, r0, r1, r2l), ra = fsel3(a, r0, r1, r2l);
     if (which >= R.n_blades) {
         const float r2 = __fmaf_rn(rb, rb, __fmaf_rn(rc, rc, __fmul_rn(ra, ra)));
         return __fsub_rn(__fsqrt_rn(r2), R.hub);

@@ -58,6 +58,7 @@ struct StepArgs {
     int part_rotor;
     const float* d0;         // [N] static porosity multiplier, null = 1
     int tangent;             // band kernel also writes d(porosity)/d(pitch) (reverse sweep)
+    int pairs;               // bulk launches take x-adjacent cell pairs (nx even, slot bases 2-element aligned)
     int nrot;
     RotorDev rot[MAXROT];
 };

@@ -20,6 +20,7 @@
 // buffer suffices and no synchronisation is needed inside the kernel.
 #include "hl_adjoint.cuh"
 #include "hl_internal.h"
+#include "hl_pair.cuh"
 
 namespace hl {
 
@@ -254,6 +255,74 @@ __global__ void __launch_bounds__(128) collide_kernel(const StepArgs a) {
     }
 }
 
+// Bulk launches with cell pairs: a thread takes cells x and x + 1 (x even).
+// A pair of plain bulk cells - outside every rotor box, off the inlet, the
+// outlet and the plane that feeds the outlet, and (odd phase) off the y and z
+// faces - takes the packed collision, with one access for both cells wherever
+// the pair is aligned (every slot in the even phase, slots with c_x = 0 in the
+// odd phase); any other pair runs the per-cell path.  The first and last pair
+// of an x row take the packed path too (their odd-phase neighbours across the
+// periodic x face are one row length away), so that no warp of a plain row
+// diverges into the per-cell path.
+template <int Q, int S, int PH>
+__global__ void __launch_bounds__(128) collide_pair_kernel(const StepArgs a) {
+    const int x = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (y >= a.n[1] || x >= a.n[0]) return;
+    bool plain = x + 1 < a.n[0];
+    for (int k = 0; k < a.nrot; ++k) {
+        const RotorDev& R = a.rot[k];
+        if ((unsigned)(y - R.lo[1]) < (unsigned)R.n[1] && (unsigned)(z - R.lo[2]) < (unsigned)R.n[2] &&
+            x + 1 >= R.lo[0] && x < R.lo[0] + R.n[0])
+            plain = false;
+    }
+    if (a.open) {
+        const int ca = sel3(a.flow_axis, x, y, z);
+        const int ca1 = ca + (a.flow_axis == 0 ? 1 : 0);
+        const int na = sel3(a.flow_axis, a.n[0], a.n[1], a.n[2]);
+        if (ca == 0 || ca1 >= na - 2) plain = false;
+    }
+    if (PH == 1 && !(y > 0 && y < a.n[1] - 1 && z > 0 && z < a.n[2] - 1)) plain = false;
+    if (!plain) {
+        collide_cell<Q, S, PH, false>(a, x, y, z);
+        if (x + 1 < a.n[0]) collide_cell<Q, S, PH, false>(a, x + 1, y, z);
+        return;
+    }
+    using T = typename Store<S>::T;
+    const int cell = (z * a.n[1] + y) * a.n[0] + x;
+    // odd phase, periodic x: the first cell's neighbour at x - 1 and the last
+    // cell's neighbour at x + 2 lie one row length away
+    const int lo_wrap = (PH == 1 && x == 0) ? a.n[0] : 0;
+    const int hi_wrap = (PH == 1 && x + 2 == a.n[0]) ? -a.n[0] : 0;
+    F2 g[Q];
+#pragma unroll
+    for (int s = 0; s < Q; ++s) {
+        const int cx = cslot(Q, s, 0);
+        const T* src = PH == 0 ? slot_ptr<Q, S>(a, s) + cell : static_cast<const T*>(a.rshift[s]) + cell;
+        if (PH == 0 || cx == 0) g[s] = Store2<S>::ld(src);
+        else if (cx > 0) g[s] = {make_float2(Store<S>::ld(src + lo_wrap), Store<S>::ld(src + 1))};
+        else g[s] = {make_float2(Store<S>::ld(src), Store<S>::ld(src + 1 + hi_wrap))};
+    }
+    F2 u[3];
+    const F2 rho = collide_pair<Q>(g, a.tau_mo, a.Ksmag, u);
+    if (!(fabsf(rho.v.x) < 1e30f) || !(fabsf(rho.v.y) < 1e30f)) atomicOr(a.err, ERR_NONFINITE);
+#pragma unroll
+    for (int s = 0; s < Q; ++s) {
+        T* dst = PH == 0 ? wslot_ptr<Q, S>(a, oslot(Q, s)) + cell : static_cast<T*>(a.wshift[s]) + cell;
+        const int cx = cslot(Q, s, 0);
+        if (PH == 0 || cx == 0) {
+            Store2<S>::st(dst, g[s]);
+        } else if (cx > 0) {
+            Store<S>::st(dst, g[s].v.x);
+            Store<S>::st(dst + 1 + hi_wrap, g[s].v.y);
+        } else {
+            Store<S>::st(dst + lo_wrap, g[s].v.x);
+            Store<S>::st(dst + 1, g[s].v.y);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // porosity embedding of the rotor boxes and the force / wall cell lists
 // ---------------------------------------------------------------------------
@@ -267,65 +336,71 @@ __device__ __forceinline__ int append(int* counter, bool take, int lane) {
     return start + __popc(mask & ((1u << lane) - 1u));
 }
 
+// One warp per box row (x contiguous, one 32-bit divide per row); rows are
+// strided over the grid's warps, so every ballot sees all 32 lanes.
 __global__ void __launch_bounds__(BAND_THREADS) band_kernel(const StepArgs a) {
     const RotorDev& R = a.rot[blockIdx.y];
-    const long long nbox = R.box_cells;
+    const int n0 = R.n[0], n1 = R.n[1];
+    const int rows = n1 * R.n[2];
+    const int nbox = (int)R.box_cells;
     const int lane = threadIdx.x & 31;
-    for (long long base = (long long)blockIdx.x * blockDim.x; base < nbox;
-         base += (long long)gridDim.x * blockDim.x) {
-        const long long bi = base + threadIdx.x;
-        bool isB = false, isW = false;
-        float phi = 0.f;
-        int which = -1;
-        if (bi < nbox) {
-            const int bx = (int)(bi % R.n[0]);
-            const long long r2 = bi / R.n[0];
-            const int by = (int)(r2 % R.n[1]);
-            const int bz = (int)(r2 / R.n[1]);
-            const int x = R.lo[0] + bx, y = R.lo[1] + by, z = R.lo[2] + bz;
-            uint8_t fl = 0;
-            float d = 1.0f;
-            // cells beyond the rotor's reach (every blade sample out of its grid,
-            // hub farther than eps/2 + 1) keep d = 1 without evaluating phi
-            const float rx = (float)x - R.cf[0], ry = (float)y - R.cf[1], rz = (float)z - R.cf[2];
-            const float ra = R.axis == 0 ? rx : (R.axis == 1 ? ry : rz);
-            const float rr = rx * rx + ry * ry + rz * rz - ra * ra;
-            float dd = 0.0f;
-            if (rr <= R.reach_plane2 && fabsf(ra) <= R.reach_axial) {
-                phi = rotor_phi(R, R.cpD, R.spD, x, y, z, which);
-                if (phi < a.eps_half) {
-                    fl |= FL_B;
-                    if (phi >= 0.0f) fl |= FL_W;
-                    // sets frozen: porosity and wall distance of the same component at the current pitch
-                    if (R.frozen) phi = component_phi(R, which, x, y, z);
-                    if (phi <= -a.eps_half) {
-                        d = 0.0f;
-                    } else if (phi < a.eps_half) {
-                        const float tt = phi * a.inv_eps + 0.5f;
-                        d = a.transition ? tt : tt * tt * (3.0f - 2.0f * tt);
-                        if (a.tangent) {
-                            float dphi;
-                            component_phi_tan(R, which, x, y, z, dphi);
-                            const float ds = a.transition ? a.inv_eps : 6.0f * tt * (1.0f - tt) * a.inv_eps;
-                            dd = ds * dphi;
+    const int wpb = blockDim.x >> 5;
+    for (int row = blockIdx.x * wpb + (threadIdx.x >> 5); row < rows; row += gridDim.x * wpb) {
+        const int by = row % n1, bz = row / n1;
+        const int y = R.lo[1] + by, z = R.lo[2] + bz;
+        const float ry = (float)y - R.cf[1], rz = (float)z - R.cf[2];
+        for (int x0 = 0; x0 < n0; x0 += 32) {
+            const int bx = x0 + lane;
+            const int bi = row * n0 + bx;
+            bool isB = false, isW = false;
+            float phi = 0.f;
+            int which = -1;
+            if (bx < n0) {
+                const int x = R.lo[0] + bx;
+                uint8_t fl = 0;
+                float d = 1.0f;
+                // cells beyond the rotor's reach (every blade sample out of its grid,
+                // hub farther than eps/2 + 1) keep d = 1 without evaluating phi
+                const float rx = (float)x - R.cf[0];
+                const float ra = R.axis == 0 ? rx : (R.axis == 1 ? ry : rz);
+                const float rr = rx * rx + ry * ry + rz * rz - ra * ra;
+                float dd = 0.0f;
+                if (rr <= R.reach_plane2 && fabsf(ra) <= R.reach_axial) {
+                    phi = rotor_phi(R, R.cpD, R.spD, x, y, z, which);
+                    if (phi < a.eps_half) {
+                        fl |= FL_B;
+                        if (phi >= 0.0f) fl |= FL_W;
+                        // sets frozen: porosity and wall distance of the same component at the current pitch
+                        if (R.frozen) phi = component_phi(R, which, x, y, z);
+                        if (phi <= -a.eps_half) {
+                            d = 0.0f;
+                        } else if (phi < a.eps_half) {
+                            const float tt = phi * a.inv_eps + 0.5f;
+                            d = a.transition ? tt : tt * tt * (3.0f - 2.0f * tt);
+                            if (a.tangent) {
+                                float dphi;
+                                component_phi_tan(R, which, x, y, z, dphi);
+                                const float ds = a.transition ? a.inv_eps : 6.0f * tt * (1.0f - tt) * a.inv_eps;
+                                dd = ds * dphi;
+                            }
                         }
                     }
                 }
+                R.d[bi] = d;
+                if (a.tangent) R.ddp[bi] = dd;
+                R.flags[bi] = fl;
+                isB = (fl & FL_B) != 0;
+                isW = a.wall_model && (fl & FL_W);
+                if (!isW) R.active[bi] = 0;
             }
-            R.d[bi] = d;
-            if (a.tangent) R.ddp[bi] = dd;
-            R.flags[bi] = fl;
-            isB = (fl & FL_B) != 0;
-            isW = a.wall_model && (fl & FL_W);
-            if (!isW) R.active[bi] = 0;
-        }
-        const int fslot = append(R.count, isB, lane);
-        if (isB && fslot < nbox) R.list[fslot] = (int)bi;
-        const int wslot = append(R.count + 1, isW, lane);
-        if (isW && wslot < nbox) {
-            R.wlist[wslot] = (int)bi;
-            R.wphi[wslot] = phi;
-            R.wwhich[wslot] = (signed char)which;
+            const int fslot = append(R.count, isB, lane);
+            if (isB && fslot < nbox) R.list[fslot] = bi;
+            const int wslot = append(R.count + 1, isW, lane);
+            if (isW && wslot < nbox) {
+                R.wlist[wslot] = bi;
+                R.wphi[wslot] = phi;
+                R.wwhich[wslot] = (signed char)which;
+            }
         }
     }
 }
@@ -768,6 +843,14 @@ static cudaError_t launch_collide_t(const StepArgs& a, cudaStream_t s) {
         }
         return cudaGetLastError();
     }
+    if (a.pairs && !a.d0) {
+        const int half = (n[0] + 1) / 2;
+        const dim3 pb = cell_block(half);
+        const dim3 pg((half + pb.x - 1) / pb.x, (n[1] + pb.y - 1) / pb.y, n[2]);
+        if (a.phase == 0) collide_pair_kernel<Q, S, 0><<<pg, pb, 0, s>>>(a);
+        else collide_pair_kernel<Q, S, 1><<<pg, pb, 0, s>>>(a);
+        return cudaGetLastError();
+    }
     constexpr int CPT = COLLIDE_CPT;
     const dim3 grd((n[0] + blk.x * CPT - 1) / (blk.x * CPT), (n[1] + blk.y - 1) / blk.y, n[2]);
     if (a.d0) {
@@ -783,9 +866,13 @@ static cudaError_t launch_collide_t(const StepArgs& a, cudaStream_t s) {
 template <int Q, int S>
 static cudaError_t launch_band_t(const StepArgs& a, cudaStream_t s) {
     if (a.nrot == 0) return cudaSuccess;
-    long long maxbox = 0;
-    for (int k = 0; k < a.nrot; ++k) maxbox = a.rot[k].box_cells > maxbox ? a.rot[k].box_cells : maxbox;
-    long long blocks = (maxbox + BAND_THREADS - 1) / BAND_THREADS;
+    long long maxrows = 0;
+    for (int k = 0; k < a.nrot; ++k) {
+        const long long r = (long long)a.rot[k].n[1] * a.rot[k].n[2];
+        maxrows = r > maxrows ? r : maxrows;
+    }
+    constexpr int WPB = BAND_THREADS / 32;
+    long long blocks = (maxrows + WPB - 1) / WPB;
     if (blocks > 148 * 16) blocks = 148 * 16;
     if (blocks < 1) blocks = 1;
     band_kernel<<<dim3((unsigned)blocks, a.nrot), BAND_THREADS, 0, s>>>(a);

@@ -234,7 +234,7 @@ def test_rotor_objective_autograd(P):
     ref = P.Lattice.from_workload(wl)
     ref.set_d0(torch.ones(wl.nz, wl.ny, wl.nx, device=ref.device))
     Jr, gpr, gdr = ref.grad(12, 6, [1.0], [-0.2], ckpt_every=4)
-    assert abs(float(T[0] - 0.2 * Qv[0]) - Jr) <= 1e-9 * abs(Jr)
+    assert abs(float((T[0] - 0.2 * Qv[0]).detach()) - Jr) <= 1e-9 * abs(Jr)
     assert abs(float(pitch.grad[0]) - gpr[0]) <= 1e-6 * abs(gpr[0])
     assert _rel_l2(d0.grad.cpu().numpy().astype(np.float64), gdr.cpu().numpy().astype(np.float64)) <= 1e-6
 
