@@ -325,7 +325,8 @@ def run_cuda(args):
             torch.cuda.empty_cache()
             line["storage_study"] = storage_study(dev, args.extra_steps)
             line["farm"] = farm_run(dev, args.extra_steps)
-            line["adjoint"] = adjoint_run(dev, args.adjoint_steps, args.adjoint_steps // 4, 100)
+            if args.adjoint_steps > 0:
+                line["adjoint"] = adjoint_run(dev, args.adjoint_steps, max(1, args.adjoint_steps // 4), 100)
             line["driven_rotor"] = driven_run(dev, 200)
         print(json.dumps(line), flush=True)
     lat.close()
@@ -474,7 +475,7 @@ def main(argv=None):
     ap.add_argument("--no-extra", action="store_true", help="skip the 16-bit storage study, the farm run and the gradient run")
     ap.add_argument("--extra-steps", type=int, default=40)
     ap.add_argument("--adjoint-steps", type=int, default=4000,
-                    help="steps of the gradient run (config of the adjoint/forward ratio)")
+                    help="steps of the gradient run (config of the adjoint/forward ratio); 0 skips it")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "cuda":
         args.warmup = 3

@@ -77,6 +77,115 @@ __device__ __forceinline__ void accum(Acc& a, int c, F2 x) {
     }
 }
 
+// Slot of velocity (cx, cy, cz), or -1 where the lattice lacks it (the D3Q19
+// corners).  Velocities are stored with their first non-zero component
+// positive in slots 1..P, opposites in P+1..2P (the order of cpos).
+__host__ __device__ constexpr int slot_of(int Q, int cx, int cy, int cz) {
+    if (cx == 0 && cy == 0 && cz == 0) return 0;
+    const bool neg = cx < 0 || (cx == 0 && (cy < 0 || (cy == 0 && cz < 0)));
+    const int x = neg ? -cx : cx, y = neg ? -cy : cy, z = neg ? -cz : cz;
+    int p = -1;
+    switch ((x + 1) * 9 + (y + 1) * 3 + (z + 1)) {
+        case 22: p = 0; break;                    // ( 1, 0, 0)
+        case 16: p = 1; break;                    // ( 0, 1, 0)
+        case 14: p = 2; break;                    // ( 0, 0, 1)
+        case 25: p = 3; break;                    // ( 1, 1, 0)
+        case 19: p = 4; break;                    // ( 1,-1, 0)
+        case 23: p = 5; break;                    // ( 1, 0, 1)
+        case 21: p = 6; break;                    // ( 1, 0,-1)
+        case 17: p = 7; break;                    // ( 0, 1, 1)
+        case 15: p = 8; break;                    // ( 0, 1,-1)
+        case 26: p = Q == 27 ? 9 : -1; break;     // ( 1, 1, 1)
+        case 24: p = Q == 27 ? 10 : -1; break;    // ( 1, 1,-1)
+        case 20: p = Q == 27 ? 11 : -1; break;    // ( 1,-1, 1)
+        case 18: p = Q == 27 ? 12 : -1; break;    // ( 1,-1,-1)
+        default: break;
+    }
+    if (p < 0) return -1;
+    return neg ? 1 + npos(Q) + p : 1 + p;
+}
+__host__ __device__ constexpr bool slot_of_consistent(int Q) {
+    for (int s = 0; s < Q; ++s)
+        if (slot_of(Q, cslot(Q, s, 0), cslot(Q, s, 1), cslot(Q, s, 2)) != s) return false;
+    int n = 0;
+    for (int k = 0; k < 27; ++k) n += slot_of(Q, k / 9 - 1, (k / 3) % 3 - 1, k % 3 - 1) >= 0;
+    return n == Q;
+}
+static_assert(slot_of_consistent(19) && slot_of_consistent(27), "slot_of disagrees with the slot tables");
+
+__device__ __forceinline__ void accum(Acc& a, int c, const Acc& x) {
+    if (x.on) accum(a, c, x.v);
+}
+
+// drho = sum g, j = sum c g, pg = sum c_a c_b g (xx yy zz xy xz yz) by three
+// one-axis passes over the {-1, 0, 1}^3 velocity grid: along x the sums of
+// c_x^k g (k = 0, 1, 2) per (c_y, c_z); along y and z only the combinations
+// of order <= 2 that the ten moments use.
+template <int Q>
+__device__ __forceinline__ void moments_pair(const F2 (&g)[Q], F2& drho, F2 (&j)[3], F2 (&pg)[6]) {
+    Acc S0[3][3], S1[3][3], S2[3][3];
+#pragma unroll
+    for (int iy = 0; iy < 3; ++iy)
+#pragma unroll
+        for (int iz = 0; iz < 3; ++iz) {
+            const int sp = slot_of(Q, 1, iy - 1, iz - 1), sm = slot_of(Q, -1, iy - 1, iz - 1),
+                      s0 = slot_of(Q, 0, iy - 1, iz - 1);
+            Acc e = acc0(), o = acc0();
+            if (sp >= 0) { accum(e, 1, g[sp]); accum(o, 1, g[sp]); }
+            if (sm >= 0) { accum(e, 1, g[sm]); accum(o, -1, g[sm]); }
+            S2[iy][iz] = e;
+            S1[iy][iz] = o;
+            if (s0 >= 0) accum(e, 1, g[s0]);
+            S0[iy][iz] = e;
+        }
+    // T[m][iz], m: 0 (k_x, k_y) = (0, 0), 1 (0, 1), 2 (0, 2), 3 (1, 0), 4 (1, 1), 5 (2, 0)
+    Acc T[6][3];
+#pragma unroll
+    for (int iz = 0; iz < 3; ++iz) {
+        Acc b = acc0();
+        accum(b, 1, S0[0][iz]);
+        accum(b, 1, S0[2][iz]);
+        T[2][iz] = b;
+        accum(b, 1, S0[1][iz]);
+        T[0][iz] = b;
+        Acc d = acc0();
+        accum(d, 1, S0[2][iz]);
+        accum(d, -1, S0[0][iz]);
+        T[1][iz] = d;
+        Acc c = acc0();
+        accum(c, 1, S1[0][iz]);
+        accum(c, 1, S1[2][iz]);
+        accum(c, 1, S1[1][iz]);
+        T[3][iz] = c;
+        Acc e = acc0();
+        accum(e, 1, S1[2][iz]);
+        accum(e, -1, S1[0][iz]);
+        T[4][iz] = e;
+        Acc f = acc0();
+        accum(f, 1, S2[0][iz]);
+        accum(f, 1, S2[2][iz]);
+        accum(f, 1, S2[1][iz]);
+        T[5][iz] = f;
+    }
+    // along z: plain sums, and the c_z-weighted ones for j_z, pg_xz, pg_yz
+    Acc r = acc0();
+    accum(r, 1, T[0][0]);
+    accum(r, 1, T[0][2]);
+    const F2 zz = r.v;                     // sum c_z^2 g
+    accum(r, 1, T[0][1]);
+    drho = r.v;
+    Acc t;
+    t = acc0(); accum(t, 1, T[0][2]); accum(t, -1, T[0][0]); j[2] = t.v;
+    t = acc0(); accum(t, 1, T[1][0]); accum(t, 1, T[1][2]); accum(t, 1, T[1][1]); j[1] = t.v;
+    t = acc0(); accum(t, 1, T[1][2]); accum(t, -1, T[1][0]); pg[5] = t.v;
+    t = acc0(); accum(t, 1, T[2][0]); accum(t, 1, T[2][2]); accum(t, 1, T[2][1]); pg[1] = t.v;
+    t = acc0(); accum(t, 1, T[3][0]); accum(t, 1, T[3][2]); accum(t, 1, T[3][1]); j[0] = t.v;
+    t = acc0(); accum(t, 1, T[3][2]); accum(t, -1, T[3][0]); pg[4] = t.v;
+    t = acc0(); accum(t, 1, T[4][0]); accum(t, 1, T[4][2]); accum(t, 1, T[4][1]); pg[3] = t.v;
+    t = acc0(); accum(t, 1, T[5][0]); accum(t, 1, T[5][2]); accum(t, 1, T[5][1]); pg[0] = t.v;
+    pg[2] = zz;
+}
+
 // Packed form of `assemble` (same Hermite coefficients; see there).
 template <int Q>
 __device__ __forceinline__ void assemble_pair(F2 (&g)[Q], F2 drho, F2 rho, const F2 (&u)[3], const F2 (&A)[6],
@@ -122,28 +231,8 @@ __device__ __forceinline__ void assemble_pair(F2 (&g)[Q], F2 drho, F2 rho, const
 // populations.  Returns rho; u_out = fluid velocity of the pre-collision state.
 template <int Q>
 __device__ __forceinline__ F2 collide_pair(F2 (&g)[Q], float tau_mo, float Ksmag, F2 (&u_out)[3]) {
-    constexpr int P = npos(Q);
-    F2 drho = g[0];
-    Acc ja[3] = {acc0(), acc0(), acc0()};
-    Acc pa[6] = {acc0(), acc0(), acc0(), acc0(), acc0(), acc0()};
-#pragma unroll
-    for (int p = 0; p < P; ++p) {
-        const int cx = cpos(Q, p, 0), cy = cpos(Q, p, 1), cz = cpos(Q, p, 2);
-        const F2 s = g[1 + p] + g[1 + P + p];
-        const F2 d = g[1 + p] - g[1 + P + p];
-        drho = drho + s;
-        accum(ja[0], cx, d);
-        accum(ja[1], cy, d);
-        accum(ja[2], cz, d);
-        accum(pa[0], cx * cx, s);
-        accum(pa[1], cy * cy, s);
-        accum(pa[2], cz * cz, s);
-        accum(pa[3], cx * cy, s);
-        accum(pa[4], cx * cz, s);
-        accum(pa[5], cy * cz, s);
-    }
-    const F2 j[3] = {ja[0].v, ja[1].v, ja[2].v};
-    const F2 pg[6] = {pa[0].v, pa[1].v, pa[2].v, pa[3].v, pa[4].v, pa[5].v};
+    F2 drho, j[3], pg[6];
+    moments_pair<Q>(g, drho, j, pg);
     const F2 rho = mk2(1.0f) + drho;
     const F2 inv = {make_float2(rcp_approx(rho.v.x), rcp_approx(rho.v.y))};
     const F2 u[3] = {j[0] * inv, j[1] * inv, j[2] * inv};

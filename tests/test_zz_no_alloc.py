@@ -4,8 +4,12 @@ For callers that cannot allocate device memory at the moment they need the
 total mass of a population array, hl_mass_noalloc keeps its partial sums in
 the library's own static device memory.  This file is collected last so that
 a run stopping at its first failure has already run every other test.  It
-compares the new entry point with hl_mass (which uses the lattice's
-workspace) on two calls in a row, through the C ABI.
+checks the new entry point and hl_mass (which uses the lattice's workspace)
+against an FP64 sum of the same population array, on two calls in a row,
+through the C ABI.  hl_mass_noalloc sums every stored value in FP64 (agrees
+to 1e-12 relative); hl_mass first sums groups of eight values in FP32, so it
+is held to the worst case of those roundings: 7 additions per group, each
+off by at most 2^-24 of a partial sum no larger than the group's absolute sum.
 """
 
 import ctypes as C
@@ -20,6 +24,16 @@ def _workspace_populations(lat):
     # the populations occupy the start of the (256-byte aligned) workspace
     base = lat._ws.data_ptr()
     return base + ((-base) % 256)
+
+
+def _populations_fp64(lat, q, n_cells, storage):
+    """The stored (weight-shifted) values as float64, from the workspace bytes."""
+    import torch
+    off = (-lat._ws.data_ptr()) % 256
+    dt = {"f32": torch.float32, "f16s": torch.float16, "bf16s": torch.bfloat16}[storage]
+    esize = 4 if storage == "f32" else 2
+    raw = lat._ws[off:off + q * n_cells * esize]
+    return raw.view(dt).double()
 
 
 def test_mass_noalloc_matches_workspace_mass_twice():
@@ -48,7 +62,12 @@ def test_mass_noalloc_matches_workspace_mass_twice():
             lat.stream.synchronize()
             got = float(out.item())
             assert np.isfinite(got)
-            assert abs(got - ref) <= 1e-12 * abs(ref), (storage, k, got, ref)
+            g = _populations_fp64(lat, wl.q, wl.cells, storage)
+            exact = float(g.sum()) + wl.cells            # shift: sum of the weights is 1 per cell
+            assert abs(got - exact) <= 1e-12 * abs(exact), (storage, k, got, exact)
+            groups = g[: (g.numel() // 8) * 8].view(-1, 8).abs().sum(dim=1)
+            bound = 7 * 2.0 ** -24 * float(groups.sum()) + 1e-12 * abs(exact)
+            assert abs(ref - exact) <= bound, (storage, k, ref, exact, bound)
         lat.close()
 
 
