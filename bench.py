@@ -181,18 +181,22 @@ def run_reference(args):
 # --------------------------------------------------------------------------
 # CUDA arm
 # --------------------------------------------------------------------------
-# DRAM traffic of one collide-and-stream launch of this workload from an ncu
-# capture, valid for the kernel source of the given hash (else reported null)
-# DRAM bytes (read + write) of one bulk collide launch of the rotor256 step, from
-# one ncu capture (profiles/collide_kernel_rotor256_traffic.md); reported only
-# while the kernel sources hash to the value they had at the capture
-NCU_TRAFFIC = {"source_sha": "5fe6e502e562a4f7", "bytes_per_launch": 4853547520}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one bulk collide
+# launch of the rotor256 step from one ncu capture; reported only while the
+# kernel sources hash to the value they had at the capture (else null)
+NCU_TRAFFIC = {"source_sha": "d27ce13086658809", "bytes_per_launch": 4871884288}
+
+
+def bulk_kernel_name(wl) -> str:
+    """The kernel of the bulk collide-and-stream launch: x-adjacent cell pairs
+    in packed FP32x2 arithmetic when nx is even, one cell per thread otherwise."""
+    return "collide_pair_kernel" if wl.nx % 2 == 0 else "collide_kernel"
 
 
 def kernel_source_sha():
     import hashlib
     h = hashlib.sha256()
-    for f in ("hl_device.cuh", "hl_kernels.cu", "hl_internal.h"):
+    for f in ("hl_device.cuh", "hl_pair.cuh", "hl_kernels.cu", "hl_internal.h"):
         with open(os.path.join(ROOT, "paper_2510_13726_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -303,7 +307,7 @@ def run_cuda(args):
                        "rotors": len(wl.rotors), "parallelism": f"replicas x{world}",
                        "l2": "no flush: the populations (%.2f GB) exceed the 126 MB L2" %
                              (wl.cells * wl.q * (4 if args.storage == "f32" else 2) / 1e9)},
-            "roofline": {"bound": "hbm", "kernel": "collide_kernel", "achieved": round(achieved, 1),
+            "roofline": {"bound": "hbm", "kernel": bulk_kernel_name(wl), "achieved": round(achieved, 1),
                          "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                          "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
                          else "fallback", "traffic": traffic,
