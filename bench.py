@@ -332,6 +332,8 @@ def run_cuda(args):
             if args.adjoint_steps > 0:
                 line["adjoint"] = adjoint_run(dev, args.adjoint_steps, max(1, args.adjoint_steps // 4), 100)
             line["driven_rotor"] = driven_run(dev, 200)
+            if args.farm_wake_steps > 0:
+                line["farm_wake"] = farm_wake(dev, args.farm_wake_steps)
         print(json.dumps(line), flush=True)
     lat.close()
     return 0
@@ -361,12 +363,14 @@ def timed_run(wl, storage, steps, warmup, dev):
     peak, _ = measured_peaks()
     gbs = collide_bytes(wl.q, storage, cells) / (c_ms / c_n / 1e3) / 1e9
     F, _ = lat.forces()
+    M, _ = lat.moments()
     lat.close()
     del lat
     torch.cuda.empty_cache()
     return {"MLUPS": round(wl.cells / ms / 1e3, 1), "ms_per_step": round(ms, 4),
             "collide_gbs": round(gbs, 1), "collide_frac": round(gbs / peak, 4),
-            "thrust_last": [round(float(f[wl.flow_axis]), 6) for f in F]}
+            "thrust_last": [round(float(f[wl.flow_axis]), 6) for f in F],
+            "torque_last": [round(float(m[wl.flow_axis]), 6) for m in M]}
 
 
 def storage_study(dev, steps):
@@ -388,6 +392,60 @@ def farm_run(dev, steps):
     r = timed_run(wl, "f32", steps, 5, dev)
     r["workload"] = "farm: 1536x512x1024 (805M cells) D3Q19 FP32, 6 rotors R=64, flow along x, 5% turbulence"
     return r
+
+
+def farm_wake(dev, steps, sample_every=50):
+    """Wind farm: per-rotor mean thrust and torque over the second half of
+    `steps` steps, and the time-averaged axial velocity there on lateral lines
+    (along z at hub height, +-1.5 D around the rotor centre, every D/8) 2 D and
+    4 D downstream of each rotor (D = 2 R)."""
+    import torch
+    import workloads as W
+    from paper_2510_13726_b300 import Lattice
+    wl = W.workload("farm")
+    lat = Lattice.from_workload(wl, device=dev)
+    half = steps // 2
+    lat.step(half)
+    lat.forces(reset_avg=True)
+    lines = []
+    for r in wl.rotors:
+        D = 2.0 * r.radius
+        cx, cy, cz = (int(round(v)) for v in r.center)
+        zs = [int(round(cz + k * D / 8)) for k in range(-12, 13)]
+        zs = [z for z in zs if 0 <= z < wl.nz]
+        xs = [int(round(cx + m * D)) for m in (2, 4)]
+        lines.append((cy, zs, xs))
+    acc = [torch.zeros(2, len(zs), dtype=torch.float64, device=dev) for (_, zs, _) in lines]
+    n = 0
+    done = 0
+    while done < steps - half:
+        k = min(sample_every, steps - half - done)
+        lat.step(k)
+        done += k
+        _, u = lat.fields()
+        for a, (cy, zs, xs) in zip(acc, lines):
+            zi = torch.tensor(zs, device=dev)
+            for j, x in enumerate(xs):
+                if 0 <= x < wl.nx:
+                    a[j] += u[0].index_select(0, zi)[:, cy, x].double()
+        n += 1
+        del u
+    _, Fa = lat.forces()
+    _, Ma = lat.moments()
+    out = {"workload": "farm: 1536x512x1024 D3Q19 FP32, 6 rotors R=64, flow along x, 5% turbulence",
+           "steps": steps, "averaged_steps": steps - half, "samples": n, "u_in": wl.u_in, "rotors": []}
+    for i, ((cy, zs, xs), a) in enumerate(zip(lines, acc)):
+        r = wl.rotors[i]
+        prof = (a / max(1, n)).cpu().numpy()
+        out["rotors"].append({
+            "center": [round(v, 2) for v in r.center], "thrust_mean": round(float(Fa[i, 0]), 6),
+            "torque_mean": round(float(Ma[i, 0]), 6), "z_offsets_D": [round((z - r.center[2]) / (2 * r.radius), 3) for z in zs],
+            "u_axial_2D": [round(float(v), 5) for v in prof[0]] if 0 <= xs[0] < wl.nx else None,
+            "u_axial_4D": [round(float(v), 5) for v in prof[1]] if 0 <= xs[1] < wl.nx else None})
+    lat.close()
+    del lat
+    torch.cuda.empty_cache()
+    return out
 
 
 def driven_run(dev, steps):
@@ -478,6 +536,9 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the 16-bit storage study, the farm run and the gradient run")
     ap.add_argument("--extra-steps", type=int, default=40)
+    ap.add_argument("--farm-wake-steps", type=int, default=0,
+                    help="steps of the wind-farm wake study (mean loads and axial-velocity lines 2 D and 4 D "
+                         "behind each rotor over the second half); 0 skips it")
     ap.add_argument("--adjoint-steps", type=int, default=4000,
                     help="steps of the gradient run (config of the adjoint/forward ratio); 0 skips it")
     args = ap.parse_args(argv)

@@ -55,11 +55,12 @@ def study_workload(radius: int, tsr: float = 6.0, u_in: float = 0.05, tau_ref: f
 
 
 def run_study(radii=(16, 32, 64, 128), revolutions_spinup: float = 3.0, revolutions_avg: float = 2.0,
-              device=None, progress=None):
+              device=None, progress=None, wall_model: bool = True):
     """C_T averaged over whole revolutions after a spin-up, at each resolution,
     on the GPU library.  Returns a dict with per-resolution results, the EOC
     against the finest grid and the GCI of the finest grid from the three
-    finest (constant refinement ratio)."""
+    finest (constant refinement ratio).  wall_model=False runs the porous
+    blades without the wall function (resolved HLBM only)."""
     import torch
     from paper_2510_13726_b300 import Lattice
     rows = []
@@ -69,7 +70,7 @@ def run_study(radii=(16, 32, 64, 128), revolutions_spinup: float = 3.0, revoluti
         steps_rev = 2.0 * math.pi / om
         n_spin = int(round(revolutions_spinup * steps_rev))
         n_avg = int(round(revolutions_avg * steps_rev))
-        lat = Lattice.from_workload(wl, device=device)
+        lat = Lattice.from_workload(wl, device=device, wall_model=wall_model)
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record(lat.stream)
@@ -88,7 +89,7 @@ def run_study(radii=(16, 32, 64, 128), revolutions_spinup: float = 3.0, revoluti
         lat.close()
         del lat
         torch.cuda.empty_cache()
-    out = {"resolutions": rows}
+    out = {"wall_model": bool(wall_model), "resolutions": rows}
     ct = [r["C_T"] for r in rows]
     if len(rows) >= 3:
         h = [1.0 / r["R"] for r in rows[:-1]]
@@ -110,8 +111,9 @@ if __name__ == "__main__":
     ap.add_argument("--radii", default="16,32,64,128")
     ap.add_argument("--spinup", type=float, default=3.0, help="revolutions before averaging")
     ap.add_argument("--average", type=float, default=2.0, help="revolutions averaged")
+    ap.add_argument("--no-wall-model", action="store_true", help="porous blades without the wall function")
     args = ap.parse_args()
     radii = tuple(int(v) for v in args.radii.split(","))
-    res = run_study(radii, args.spinup, args.average,
+    res = run_study(radii, args.spinup, args.average, wall_model=not args.no_wall_model,
                     progress=lambda row: print(json.dumps(row), file=sys.stderr, flush=True))
     print(json.dumps(res))

@@ -345,3 +345,50 @@ def test_16bit_precision_study_rotor256_q27(P):
     assert out["f32"][0] < 1e-3 and out["f32"][1] < 1e-3
     for s in ("f16s", "bf16s"):
         assert out[s][0] <= 0.01 and out[s][1] <= 0.01, (s, out[s])
+
+
+def _parity_run(P, wl, checkpoints):
+    lat = P.Lattice.from_workload(wl)
+    o = O.from_workload(wl)
+    rows = []
+    for t_target in checkpoints:
+        lat.step(t_target - lat.t)
+        o.step(t_target - o.t)
+        rg, ug = (a.cpu().numpy().astype(np.float64) for a in lat.fields())
+        ro, uo = o.fields()
+        a = wl.flow_axis
+        inner = [slice(None)] * 3
+        inner[2 - a] = slice(1, -1)          # fields are (nz, ny, nx): drop the open planes
+        inner = tuple(inner)
+        e_rho = float(np.linalg.norm((rg - ro)[inner]) / np.linalg.norm(ro[inner]))
+        e_u = _rel_l2(ug[(slice(None),) + inner], uo[(slice(None),) + inner])
+        rows.append((t_target, e_rho, e_u))
+    Fg, _ = lat.forces()
+    Fo, _, _, _ = o.forces()
+    return rows, float(np.abs(Fg - Fo).max() / np.abs(Fo).max())
+
+
+def test_flow_along_x_parity(P):
+    """Rotor and inflow along x (96x48x48, R = 12, TSR 6, 5 % turbulence): the
+    bulk launch takes x-adjacent cell pairs, so the inlet, the outlet and the
+    plane that feeds the outlet fall inside the pair rows."""
+    from workloads.configs import Workload, _single
+    wl = Workload("x96", 96, 48, 48, flow_axis=0, turbulence=0.05,
+                  rotors=_single(96, 48, 48, 12.0, 6.0, axis=0))
+    rows, eF = _parity_run(P, wl, (1, 50, 150))
+    print("t, rel L2 rho, rel L2 u:", rows, "forces", eF)
+    for t, e_rho, e_u in rows:
+        assert e_rho <= 1e-5 and e_u <= 1e-5, (t, e_rho, e_u)
+    assert eF <= 1e-3
+
+
+def test_odd_nx_runs_the_one_cell_kernel(P):
+    """nx odd (47x48x96): cell pairs would be misaligned, so the bulk launch
+    keeps one cell per thread; fields and forces against the oracle."""
+    from workloads.configs import Workload, _single
+    wl = Workload("odd47", 47, 48, 96, rotors=_single(47, 48, 96, 12.0, 6.0))
+    rows, eF = _parity_run(P, wl, (1, 50, 150))
+    print("t, rel L2 rho, rel L2 u:", rows, "forces", eF)
+    for t, e_rho, e_u in rows:
+        assert e_rho <= 1e-5 and e_u <= 1e-5, (t, e_rho, e_u)
+    assert eF <= 1e-3
