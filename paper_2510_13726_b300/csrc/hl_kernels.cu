@@ -264,11 +264,12 @@ __global__ void __launch_bounds__(128) collide_kernel(const StepArgs a) {
 // of an x row take the packed path too (their odd-phase neighbours across the
 // periodic x face are one row length away), so that no warp of a plain row
 // diverges into the per-cell path.
-// D3Q27: at most 64 registers (8 blocks of 128 per SM, 8-12 bytes of spill):
-// 2-3 % faster for 16-bit storage than the unbounded 72; 56 (9 blocks) spills
-// 60-100 bytes and is slower on every storage.
+// Register caps: D3Q27 at most 64 (8 blocks of 128 per SM, 8-12 bytes of
+// spill), 2-3 % faster for 16-bit storage than the unbounded 72 (56, 9 blocks,
+// spills 60-100 bytes and is slower on every storage); D3Q19 at most 48 (10
+// blocks), 3 % faster for 16-bit storage than the unbounded 56, FP32 unchanged.
 template <int Q, int S, int PH>
-__global__ void __launch_bounds__(128, Q == 27 ? 8 : 1) collide_pair_kernel(const StepArgs a) {
+__global__ void __launch_bounds__(128, Q == 27 ? 8 : 10) collide_pair_kernel(const StepArgs a) {
     const int x = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
