@@ -255,6 +255,16 @@ hl_status hl_debug_collide(int q, int n, const float* d_g_in, const float* d_d, 
  * force sets then relax towards rest with weight 1 - d0. */
 hl_status hl_set_d0(hl_lattice* lat, const float* d_d0);
 
+/* Inflow from the caller (a precursor run, measured data): d_plane is a
+ * device FP32 array [3][n_c][n_b] of inlet velocities (components x, y, z;
+ * (b, c) = the two axes after flow_axis in cyclic order, b fastest - the
+ * layout of the outlet plane), caller-owned and read by the inlet cells of
+ * every later step while set, so the caller may overwrite it between steps
+ * on the lattice's stream; NULL restores the synthetic inflow of the
+ * configuration (u_in and its Fourier modes, Sec. 4 inflow condition).
+ * HL_ERR_STATE without open boundaries; hl_grad rejects a set plane. */
+hl_status hl_set_inflow_plane(hl_lattice* lat, const float* d_plane);
+
 /* Change the pitch of rotor `rotor` (rad) for the following steps. */
 hl_status hl_set_pitch(hl_lattice* lat, int rotor, double pitch);
 
@@ -277,8 +287,9 @@ hl_status hl_grad_workspace_size(const hl_lattice* lat, int steps, int ckpt_ever
  * spacing (memory vs. one recomputed forward step per step).  d_work:
  * caller's device workspace of hl_grad_workspace_size bytes, 256-byte
  * aligned, overwritten.  Synchronises; HL_ERR_NONFINITE / HL_ERR_MASS as
- * hl_step; HL_ERR_STATE for a torque-driven rotor or sigma_band < 1 (the
- * derivative covers prescribed rotation and the local band collision). */
+ * hl_step; HL_ERR_STATE for a torque-driven rotor, sigma_band < 1 or a
+ * caller's inflow plane (the derivative covers prescribed rotation, the
+ * local band collision and the synthetic inflow). */
 hl_status hl_grad(hl_lattice* lat, int steps, int avg_last, int ckpt_every, const double* w_thrust,
                   const double* w_torque, double* J, double* dJ_dpitch, float* d_dJ_dd0, void* d_work,
                   size_t bytes);

@@ -83,6 +83,7 @@ StepArgs make_args(const hl_lattice* lat) {
         a.wslot[q] = a.slot[q];
     }
     a.d0 = lat->d0;
+    a.inflow_plane = lat->inflow;
     a.n[0] = c.nx; a.n[1] = c.ny; a.n[2] = c.nz;
     a.nxy = c.nx * c.ny;
     a.nplane = (int)plane_cells(c);

@@ -752,6 +752,8 @@ hl_status hl_grad(hl_lattice* lat, int steps, int avg_last, int ckpt_every, cons
             return fail(lat, HL_ERR_STATE, "hl_grad: gradients cover prescribed rotation only (rotor is torque-driven)");
     if (lat->cfg.sigma_band != 1.0)
         return fail(lat, HL_ERR_STATE, "hl_grad: gradients cover the local band collision only (sigma_band = 1)");
+    if (lat->inflow)
+        return fail(lat, HL_ERR_STATE, "hl_grad: the recompute cannot replay a caller's inflow planes (synthetic inflow only)");
     const int T = steps, K = ckpt_every, na = avg_last;
     const GradLayout G = grad_layout(lat, T, K);
     if (bytes < G.total) return fail(lat, HL_ERR_WORKSPACE, "hl_grad: workspace too small");
@@ -951,6 +953,13 @@ hl_status hl_grad(hl_lattice* lat, int steps, int avg_last, int ckpt_every, cons
 hl_status hl_set_d0(hl_lattice* lat, const float* d_d0) {
     if (!lat) return HL_ERR_ARG;
     lat->d0 = d_d0;
+    return HL_OK;
+}
+
+hl_status hl_set_inflow_plane(hl_lattice* lat, const float* d_plane) {
+    if (!lat) return HL_ERR_ARG;
+    if (d_plane && !lat->cfg.open_boundaries) return fail(lat, HL_ERR_STATE, "hl_set_inflow_plane: the lattice has no inlet");
+    lat->inflow = d_plane;
     return HL_OK;
 }
 

@@ -57,6 +57,7 @@ struct StepArgs {
     int part;                // collide cells: 0 all, 1 outside every rotor box, 2 the box of part_rotor
     int part_rotor;
     const float* d0;         // [N] static porosity multiplier, null = 1
+    const float* inflow_plane;  // [3][plane] caller's inflow velocity, null = the synthetic modes
     int tangent;             // band kernel also writes d(porosity)/d(pitch) (reverse sweep)
     int pairs;               // bulk launches take x-adjacent cell pairs (nx even, slot bases 2-element aligned)
     int nrot;

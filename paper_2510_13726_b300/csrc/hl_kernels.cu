@@ -196,7 +196,14 @@ __device__ __forceinline__ void collide_cell(const StepArgs& a, int x, int y, in
         }
         return;
     }
-    if (inlet) {
+    if (inlet && a.inflow_plane) {
+        // equilibrium inflow at the caller's plane velocity
+        const int nb = sel3(ax, a.n[1], a.n[2], a.n[0]);
+        const int cb = sel3(ax, y, z, x), cc = sel3(ax, z, x, y);
+        const int pl = cc * nb + cb;
+        const float u[3] = {a.inflow_plane[pl], a.inflow_plane[a.nplane + pl], a.inflow_plane[2 * a.nplane + pl]};
+        equilibrium<Q>(g, 0.0f, u);
+    } else if (inlet) {
         // equilibrium inflow: U a + sum_m a_m cos(k.x') + b_m sin(k.x'), x' = x - U t a
         float u[3] = {0.f, 0.f, 0.f};
         u[ax] = a.u_in;

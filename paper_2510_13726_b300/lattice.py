@@ -244,6 +244,28 @@ class Lattice:
         self._check(lib().hl_drive_state(self._h, int(k), C.byref(th), C.byref(om)))
         return th.value, om.value
 
+    def inflow_plane_shape(self):
+        """(3, n_c, n_b) of the inlet plane: (b, c) = the axes after flow_axis, b fastest."""
+        dims = (self.shape[2], self.shape[1], self.shape[0])
+        a = self.cfg.flow_axis
+        return (3, dims[(a + 2) % 3], dims[(a + 1) % 3])
+
+    def set_inflow_plane(self, plane):
+        """Inlet velocities from the caller: a device FP32 tensor of inflow_plane_shape(), read by
+        every later step while set (overwrite it in place between steps on the lattice stream);
+        None restores the synthetic inflow.  The tensor is kept alive by the lattice while set."""
+        import torch
+        if plane is None:
+            self._inflow = None
+            self._check(lib().hl_set_inflow_plane(self._h, None))
+            return
+        if not (isinstance(plane, torch.Tensor) and plane.is_cuda and plane.dtype == torch.float32
+                and plane.is_contiguous() and tuple(plane.shape) == self.inflow_plane_shape()):
+            raise ValueError(f"inflow plane must be a contiguous float32 device tensor of shape "
+                             f"{self.inflow_plane_shape()}")
+        self._inflow = plane
+        self._check(lib().hl_set_inflow_plane(self._h, plane.data_ptr()))
+
     # -- gradients ------------------------------------------------------------
     def set_d0(self, d0):
         """Static porosity multiplier d0 (device tensor of N or (nz, ny, nx) floats; None = 1).

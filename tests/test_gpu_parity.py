@@ -392,3 +392,38 @@ def test_odd_nx_runs_the_one_cell_kernel(P):
     for t, e_rho, e_u in rows:
         assert e_rho <= 1e-5 and e_u <= 1e-5, (t, e_rho, e_u)
     assert eF <= 1e-3
+
+
+def test_caller_inflow_plane_matches_synthetic_inflow(P):
+    """Inlet velocities supplied by the caller each step (the host evaluation
+    of the synthetic inflow, copied into the plane between steps) reproduce
+    the oracle's run with the Fourier modes; the gradient call and a lattice
+    without an inlet refuse a caller plane."""
+    import torch
+    from workloads.configs import Workload, _single
+    from workloads.turbulence import inflow_plane
+    wl = Workload("turb48", 48, 48, 96, turbulence=0.05, rotors=_single(48, 48, 96, 12.0, 6.0))
+    lat = P.Lattice.from_workload(wl)
+    o = O.from_workload(wl)
+    plane = torch.empty(lat.inflow_plane_shape(), dtype=torch.float32, device=lat.device)
+    lat.set_inflow_plane(plane)
+    modes = wl.modes()
+    for t in range(120):
+        host = torch.from_numpy(inflow_plane(modes, wl.shape, wl.flow_axis, wl.u_in, t).astype(np.float32))
+        with torch.cuda.stream(lat.stream):
+            plane.copy_(host.pin_memory(), non_blocking=True)
+        lat.step(1)
+    o.step(120)
+    rg, ug = (a.cpu().numpy().astype(np.float64) for a in lat.fields())
+    ro, uo = o.fields()
+    e_u = _rel_l2(ug[:, 1:-1], uo[:, 1:-1])
+    e_rho = float(np.linalg.norm((rg - ro)[1:-1]) / np.linalg.norm(ro[1:-1]))
+    print("caller plane vs oracle modes, 120 steps: rel L2 rho, u", e_rho, e_u)
+    assert e_rho <= 1e-5 and e_u <= 1e-5
+    with pytest.raises(P.HlError) as e:
+        lat.grad(4, 2, [1.0], [0.0], ckpt_every=2)
+    assert e.value.code == -5
+    lat.set_inflow_plane(None)
+    closed = P.Lattice(16, 16, 16, open_boundaries=False)
+    with pytest.raises(P.HlError):
+        closed.set_inflow_plane(torch.zeros(closed.inflow_plane_shape(), device=closed.device))

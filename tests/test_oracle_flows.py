@@ -200,3 +200,17 @@ def test_turbulent_inflow_statistics():
     rms = samples.reshape(-1, 3).std(0)
     assert np.all(np.abs(rms / (0.05 * U) - 1) < 0.35)
     assert abs(rms.mean() / (0.05 * U) - 1) < 0.2
+
+
+def test_inflow_plane_input_matches_oracle():
+    """The host evaluation of the synthetic inflow (input data for a caller's
+    inflow plane) equals the oracle's inlet velocities, flow along z and x."""
+    from workloads.turbulence import fourier_modes, inflow_plane
+    for shape, axis in (((12, 10, 20), 2), ((20, 12, 10), 0)):
+        modes = fourier_modes(3, 16, float(shape[axis]), 0.05, 0.05)
+        o = O.Oracle(*shape, flow_axis=axis, u_in=0.05, modes=modes)
+        for t in (0, 7, 31):
+            ref = o.inflow_plane(t)                     # (n_c, n_b, 3)
+            got = inflow_plane(modes, shape, axis, 0.05, t)
+            assert np.abs(got.transpose(1, 2, 0) - ref).max() <= 1e-15
+            assert np.abs(got - 0.05 * (np.arange(3) == axis)[:, None, None]).max() > 1e-4

@@ -15,6 +15,29 @@ from __future__ import annotations
 import numpy as np
 
 
+def inflow_plane(modes, shape, flow_axis: int, u_mean: float, t: int) -> np.ndarray:
+    """The synthetic inflow on the inlet plane (flow-axis coordinate 0) at
+    step t, as input data for a caller-supplied inflow:
+    u = u_mean a + sum_m a_m cos(k_m . x') + b_m sin(k_m . x'), x' = x - u_mean t a.
+    shape = (nx, ny, nz); returns float64 (3, n_c, n_b), (b, c) = the axes
+    after flow_axis in cyclic order, b fastest."""
+    b, c = (flow_axis + 1) % 3, (flow_axis + 2) % 3
+    nb, nc = shape[b], shape[c]
+    X = np.zeros((3, nc, nb))
+    X[b] = np.arange(nb)[None, :]
+    X[c] = np.arange(nc)[:, None]
+    X[flow_axis] = -u_mean * t
+    u = np.zeros((3, nc, nb))
+    u[flow_axis] = u_mean
+    if modes is not None:
+        for m in np.asarray(modes, dtype=np.float64).reshape(-1, 9):
+            ph = m[0] * X[0] + m[1] * X[1] + m[2] * X[2]
+            cs, sn = np.cos(ph), np.sin(ph)
+            for k in range(3):
+                u[k] += m[3 + k] * cs + m[6 + k] * sn
+    return u
+
+
 def fourier_modes(seed: int, n_modes: int = 64, length: float = 256.0,
                   u_mean: float = 0.05, intensity: float = 0.05,
                   kmax_wavelength: float = 4.0) -> np.ndarray:
