@@ -174,6 +174,14 @@ hl_status hl_check(hl_lattice* lat);
  * reset_avg != 0 restarts the mean after reading.  Synchronises. */
 hl_status hl_forces(hl_lattice* lat, double* F, double* F_avg, int reset_avg);
 
+/* Enqueue on the lattice's stream, without synchronising, a copy of the last
+ * enqueued step's loads into h_loads (host, [n_rotors][6] doubles: F(3) then
+ * M(3), as hl_forces / hl_moments report them; page-locked memory keeps the
+ * copy asynchronous).  The values are there once the stream has passed the
+ * copy (an event recorded after this call, or hl_check).  Lets a time loop
+ * read every step's thrust and torque while the next steps run. */
+hl_status hl_loads_async(hl_lattice* lat, double* h_loads);
+
 /* Torque about each rotor centre, [n_rotors][3], last step and mean. */
 hl_status hl_moments(hl_lattice* lat, double* M, double* M_avg);
 

@@ -611,6 +611,14 @@ static hl_status read_acc(hl_lattice* lat, std::vector<double>& acc) {
     return HL_OK;
 }
 
+hl_status hl_loads_async(hl_lattice* lat, double* h_loads) {
+    if (!lat || !h_loads) return HL_ERR_ARG;
+    for (int k = 0; k < lat->nrot; ++k)
+        HL_CUDA(lat, cudaMemcpyAsync(h_loads + 6 * k, lat->rot[k].dev.acc, 6 * sizeof(double),
+                                     cudaMemcpyDeviceToHost, lat->stream));
+    return HL_OK;
+}
+
 hl_status hl_forces(hl_lattice* lat, double* F, double* F_avg, int reset_avg) {
     if (!lat) return HL_ERR_ARG;
     std::vector<double> acc;

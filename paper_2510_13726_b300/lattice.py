@@ -166,6 +166,17 @@ class Lattice:
                                     Fa.ctypes.data_as(C.POINTER(C.c_double)), int(reset_avg)))
         return F[:self.nrot], Fa[:self.nrot]
 
+    def loads_async(self, out):
+        """Enqueue a copy of the last enqueued step's (F, M) per rotor into `out`, a pinned host
+        float64 tensor of (nrot, 6) values, on the lattice stream; no synchronisation (record an
+        event on self.stream after this call and wait for it before reading `out`)."""
+        import torch
+        if not (isinstance(out, torch.Tensor) and out.dtype == torch.float64 and not out.is_cuda
+                and out.is_contiguous() and out.numel() >= 6 * self.nrot):
+            raise ValueError("out must be a contiguous float64 host tensor of (nrot, 6) values")
+        with torch.cuda.device(self.device):
+            self._check(lib().hl_loads_async(self._h, out.data_ptr()))
+
     def moments(self):
         """(M, M_avg): torque about each rotor centre, (nrot, 3)."""
         M = np.zeros((max(1, self.nrot), 3))

@@ -427,3 +427,27 @@ def test_caller_inflow_plane_matches_synthetic_inflow(P):
     closed = P.Lattice(16, 16, 16, open_boundaries=False)
     with pytest.raises(P.HlError):
         closed.set_inflow_plane(torch.zeros(closed.inflow_plane_shape(), device=closed.device))
+
+
+def test_loads_async_matches_forces_and_moments(P):
+    """hl_loads_async copies each step's force and torque into pinned host
+    memory without synchronising; read after an event, they equal what
+    hl_forces and hl_moments report for the same step."""
+    import torch
+    wl = _wl48()
+    lat = P.Lattice.from_workload(wl)
+    ring = torch.zeros((3, 1, 6), dtype=torch.float64).pin_memory()
+    evs = [torch.cuda.Event() for _ in range(3)]
+    ref = []
+    for i in range(3):
+        lat.step_async(1)
+        lat.loads_async(ring[i])
+        evs[i].record(lat.stream)
+        lat.check()
+        F, _ = lat.forces()
+        M, _ = lat.moments()
+        ref.append(np.concatenate([F[0], M[0]]))
+    for i in range(3):
+        evs[i].synchronize()
+        assert np.array_equal(ring[i, 0].numpy(), ref[i]), (i, ring[i, 0].numpy(), ref[i])
+    assert not np.array_equal(ref[0], ref[2])
