@@ -1,16 +1,24 @@
 // Kernels of the HHRRLBM-LES rotor step on B300 (sm_103a).
 //
-// Per time step (listing "HHRRLBM-FSI", Sec. 3.2), on one stream:
-//   band_kernel     porosity embedding of the rotor boxes (Definition
-//                   "Lattice Porosity", Sec. 3.1): d, force/wall flags, and
-//                   compacted lists of force cells and wall cells
-//   wall_kernel     wall model on the wall-cell list (Sec. 2.2.1, 3.2)
-//   collide_kernel  fused collide-and-stream, single-buffer AA pattern,
-//                   bulk (RRLBM-LES) and band (HHRRLBM-LES) branches,
-//                   equilibrium inlet/outlet planes            (Eq. (hlbm))
-//   force_kernel    momentum exchange over the force cells, FP64 block
-//                   reduction, deterministic last-block combine (Sec. 2.2.2)
-//   mass_kernel     (every K steps) FP64 mass total + non-finite check
+// Per time step (listing "HHRRLBM-FSI", Sec. 3.2).  The bulk launch runs on
+// the lattice stream; the rotor-box chain (embedding, wall model, box
+// collision, force, evolve) runs beside it on a second stream:
+//   band_kernel         porosity embedding of the rotor boxes (Definition
+//                       "Lattice Porosity", Sec. 3.1): d, force/wall flags,
+//                       compacted lists of force cells and wall cells
+//   band_strain_kernel  (sigma < 1) finite-difference strain of the force
+//                       cells off the wall set (Sec. 2.2)
+//   wall_kernel         wall model on the wall-cell list (Sec. 2.2.1, 3.2)
+//   collide_pair_kernel fused collide-and-stream of the bulk cells, two
+//                       x-adjacent cells per thread in packed FP32x2
+//                       arithmetic (RRLBM-LES, Eq. (hlbm) with d = 1)
+//   collide_kernel      fused collide-and-stream, one cell per thread: the
+//                       rotor boxes (HHRRLBM-LES band branch), the pairs the
+//                       packed path does not take, equilibrium inlet/outlet
+//   force_kernel        momentum exchange over the force cells, FP64 block
+//                       reduction, deterministic last-block combine (Sec. 2.2.2)
+//   evolve_kernel       (torque-driven rotors) rotor angle and speed
+//   mass_kernel         (every K steps) FP64 mass total + non-finite check
 //
 // AA pattern: with phase p = t & 1 of the step,
 //   p = 0: f_i(x) is read from slot i of x, f*_i(x) written to slot ibar of x;
@@ -24,11 +32,6 @@
 
 namespace hl {
 
-// cells per thread of the bulk collide launch: one; two (half the blocks)
-// measured 5-7 % slower on every variant, with fewer loads in flight
-#ifndef COLLIDE_CPT
-#define COLLIDE_CPT 1
-#endif
 
 // periodic neighbour index contributions along x, y, z (-1, 0, +1)
 struct Offs {
@@ -241,11 +244,11 @@ __device__ __forceinline__ void collide_cell(const StepArgs& a, int x, int y, in
     }
 }
 
-// Bulk launches give each thread CPT cells blockDim.x apart along x; the box
-// launch spans one rotor box with one cell per thread.
-template <int Q, int S, int PH, bool D0, int CPT>
+// One cell per thread: the bulk launch when cell pairs are off (nx odd, a
+// static porosity field), or the box launch spanning one rotor box.
+template <int Q, int S, int PH, bool D0>
 __global__ void __launch_bounds__(128) collide_kernel(const StepArgs a) {
-    const int x = blockIdx.x * (blockDim.x * CPT) + threadIdx.x;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     if (a.part == 2) {
@@ -254,12 +257,8 @@ __global__ void __launch_bounds__(128) collide_kernel(const StepArgs a) {
         collide_cell<Q, S, PH, D0>(a, x + R.lo[0], y + R.lo[1], z + R.lo[2]);
         return;
     }
-    if (y >= a.n[1]) return;
-#pragma unroll
-    for (int k = 0; k < CPT; ++k) {
-        const int xk = x + k * (int)blockDim.x;
-        if (xk < a.n[0]) collide_cell<Q, S, PH, D0>(a, xk, y, z);
-    }
+    if (y >= a.n[1] || x >= a.n[0]) return;
+    collide_cell<Q, S, PH, D0>(a, x, y, z);
 }
 
 // Bulk launches with cell pairs: a thread takes cells x and x + 1 (x even).
@@ -846,11 +845,11 @@ static cudaError_t launch_collide_t(const StepArgs& a, cudaStream_t s) {
     if (a.part == 2) {
         const dim3 grd((n[0] + blk.x - 1) / blk.x, (n[1] + blk.y - 1) / blk.y, n[2]);
         if (a.d0) {
-            if (a.phase == 0) collide_kernel<Q, S, 0, true, 1><<<grd, blk, 0, s>>>(a);
-            else collide_kernel<Q, S, 1, true, 1><<<grd, blk, 0, s>>>(a);
+            if (a.phase == 0) collide_kernel<Q, S, 0, true><<<grd, blk, 0, s>>>(a);
+            else collide_kernel<Q, S, 1, true><<<grd, blk, 0, s>>>(a);
         } else {
-            if (a.phase == 0) collide_kernel<Q, S, 0, false, 1><<<grd, blk, 0, s>>>(a);
-            else collide_kernel<Q, S, 1, false, 1><<<grd, blk, 0, s>>>(a);
+            if (a.phase == 0) collide_kernel<Q, S, 0, false><<<grd, blk, 0, s>>>(a);
+            else collide_kernel<Q, S, 1, false><<<grd, blk, 0, s>>>(a);
         }
         return cudaGetLastError();
     }
@@ -862,14 +861,13 @@ static cudaError_t launch_collide_t(const StepArgs& a, cudaStream_t s) {
         else collide_pair_kernel<Q, S, 1><<<pg, pb, 0, s>>>(a);
         return cudaGetLastError();
     }
-    constexpr int CPT = COLLIDE_CPT;
-    const dim3 grd((n[0] + blk.x * CPT - 1) / (blk.x * CPT), (n[1] + blk.y - 1) / blk.y, n[2]);
+    const dim3 grd((n[0] + blk.x - 1) / blk.x, (n[1] + blk.y - 1) / blk.y, n[2]);
     if (a.d0) {
-        if (a.phase == 0) collide_kernel<Q, S, 0, true, CPT><<<grd, blk, 0, s>>>(a);
-        else collide_kernel<Q, S, 1, true, CPT><<<grd, blk, 0, s>>>(a);
+        if (a.phase == 0) collide_kernel<Q, S, 0, true><<<grd, blk, 0, s>>>(a);
+        else collide_kernel<Q, S, 1, true><<<grd, blk, 0, s>>>(a);
     } else {
-        if (a.phase == 0) collide_kernel<Q, S, 0, false, CPT><<<grd, blk, 0, s>>>(a);
-        else collide_kernel<Q, S, 1, false, CPT><<<grd, blk, 0, s>>>(a);
+        if (a.phase == 0) collide_kernel<Q, S, 0, false><<<grd, blk, 0, s>>>(a);
+        else collide_kernel<Q, S, 1, false><<<grd, blk, 0, s>>>(a);
     }
     return cudaGetLastError();
 }
