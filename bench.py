@@ -255,7 +255,7 @@ def run_cuda(args):
     dev = torch.device("cuda", local)
 
     wl = W.workload(args.workload)
-    lat = Lattice.from_workload(wl, storage=args.storage, device=dev)
+    lat = Lattice.from_workload(wl, storage=args.storage, layout=args.layout, device=dev)
     stream = lat.stream
     K, Wm = args.steps, args.warmup
     lat.step(Wm)
@@ -365,7 +365,7 @@ def run_cuda(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.storage == "f32" else "f32-math/" + args.storage,
             "data": "synthetic",
             "config": {"workload": WORKLOAD_DESC if args.workload == "rotor256" else wl.note,
-                       "name": args.workload, "cells": wl.cells, "q": wl.q, "storage": args.storage,
+                       "name": args.workload, "cells": wl.cells, "q": wl.q, "storage": args.storage, "layout": args.layout,
                        "rotors": len(wl.rotors), "parallelism": f"replicas x{world}",
                        "l2": "no flush: the populations (%.2f GB) exceed the 126 MB L2" %
                              (wl.cells * wl.q * (4 if args.storage == "f32" else 2) / 1e9)},
@@ -597,6 +597,8 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
     ap.add_argument("--workload", default="rotor256")
     ap.add_argument("--storage", default="f32", choices=["f32", "f16s", "bf16s"])
+    ap.add_argument("--layout", default="aa", choices=["aa", "esotwist"],
+                    help="population layout: AA pattern or esoteric twist")
     ap.add_argument("--cpu-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the 16-bit storage study, the farm run and the gradient run")

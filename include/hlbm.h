@@ -83,6 +83,12 @@ typedef int hl_status;
  *                  wall model, box collision and force reduction run on an
  *                  internal high-priority stream (ordered by events; same
  *                  results bit for bit); 0: everything on one stream
+ *  layout          population layout of the single buffer: 0 the AA pattern
+ *                  (even steps read and write each cell's own slots, odd
+ *                  steps its neighbours'), 1 the esoteric twist (every step
+ *                  a cell reads and writes the links to its +x/+y/+z
+ *                  neighbours, the slot of each link alternating with the
+ *                  step parity); same results, hl_grad needs 0
  */
 typedef struct hl_config {
     int nx, ny, nz;
@@ -101,6 +107,7 @@ typedef struct hl_config {
     int mass_check_every;
     double mass_tol;
     int overlap;
+    int layout;
 } hl_config;
 
 /* A rotor: n_blades copies of one blade grid plus a hub sphere (Sec. 3.1).

@@ -31,6 +31,7 @@ class HlConfig(C.Structure):
         ("wm_tol", C.c_double), ("wm_maxit", C.c_int),
         ("n_modes", C.c_int), ("modes", _dp),
         ("mass_check_every", C.c_int), ("mass_tol", C.c_double), ("overlap", C.c_int),
+        ("layout", C.c_int),
     ]
 
 

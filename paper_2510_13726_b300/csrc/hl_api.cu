@@ -42,6 +42,7 @@ bool valid_config(const hl_config* c) {
     if (c->n_modes < 0 || (c->n_modes > 0 && !c->modes)) return false;
     if (c->wm_maxit < 0 || c->wm_maxit > 1000 || !(c->wm_ysample > 0.0)) return false;
     if (c->mass_check_every < 0) return false;
+    if (c->layout < 0 || c->layout > 1) return false;
     return true;
 }
 
@@ -60,8 +61,24 @@ void set_shifted_bases(StepArgs* a, int q, int esize) {
         const int sbar = s == 0 ? 0 : (s <= P ? s + P : s - P);
         // integer arithmetic on the addresses: the shifted bases may lie
         // outside the buffer, every address formed from them lies inside
-        a->rshift[s] = reinterpret_cast<const void*>(reinterpret_cast<uintptr_t>(a->slot[sbar]) - D * esize);
-        a->wshift[s] = reinterpret_cast<void*>(reinterpret_cast<uintptr_t>(a->wslot[s]) + D * esize);
+        if (a->layout == 1) {
+            // esoteric twist: the link between x and x + c_s lives at cell
+            // x + max(c_s, 0); a cell reads f_s over the link to x - c_s (at
+            // x + max(-c_s, 0)) and writes f*_s onto the link to x + c_s, in
+            // slot s / sbar (reads) and sbar / s (writes) at even / odd steps
+            long long Dp = 0, Dn = 0;
+            const long long stride[3] = {1, a->n[0], a->nxy};
+            for (int k = 0; k < 3; ++k) {
+                Dp += (c[3 * s + k] > 0 ? 1 : 0) * stride[k];
+                Dn += (c[3 * s + k] < 0 ? 1 : 0) * stride[k];
+            }
+            const int rs = a->phase == 0 ? s : sbar, ws = a->phase == 0 ? sbar : s;
+            a->rshift[s] = reinterpret_cast<const void*>(reinterpret_cast<uintptr_t>(a->slot[rs]) + Dn * esize);
+            a->wshift[s] = reinterpret_cast<void*>(reinterpret_cast<uintptr_t>(a->wslot[ws]) + Dp * esize);
+        } else {
+            a->rshift[s] = reinterpret_cast<const void*>(reinterpret_cast<uintptr_t>(a->slot[sbar]) - D * esize);
+            a->wshift[s] = reinterpret_cast<void*>(reinterpret_cast<uintptr_t>(a->wslot[s]) + D * esize);
+        }
     }
     // packed cell pairs need two-element alignment of every pair they touch:
     // x even, and with nx (hence nx * ny) even a shift by c_s keeps the parity of c_x
@@ -88,6 +105,7 @@ StepArgs make_args(const hl_lattice* lat) {
     a.nxy = c.nx * c.ny;
     a.nplane = (int)plane_cells(c);
     a.phase = (int)(lat->t & 1);
+    a.layout = c.layout;
     a.t = lat->t;
     a.flow_axis = c.flow_axis;
     a.open = c.open_boundaries;

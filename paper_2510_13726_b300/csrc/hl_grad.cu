@@ -754,6 +754,8 @@ hl_status hl_grad(hl_lattice* lat, int steps, int avg_last, int ckpt_every, cons
         return fail(lat, HL_ERR_STATE, "hl_grad: gradients cover the local band collision only (sigma_band = 1)");
     if (lat->inflow)
         return fail(lat, HL_ERR_STATE, "hl_grad: the recompute cannot replay a caller's inflow planes (synthetic inflow only)");
+    if (lat->cfg.layout != 0)
+        return fail(lat, HL_ERR_STATE, "hl_grad: the reverse kernels address the AA layout (layout = 0)");
     const int T = steps, K = ckpt_every, na = avg_last;
     const GradLayout G = grad_layout(lat, T, K);
     if (bytes < G.total) return fail(lat, HL_ERR_WORKSPACE, "hl_grad: workspace too small");

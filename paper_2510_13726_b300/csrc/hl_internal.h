@@ -60,6 +60,7 @@ struct StepArgs {
     const float* inflow_plane;  // [3][plane] caller's inflow velocity, null = the synthetic modes
     int tangent;             // band kernel also writes d(porosity)/d(pitch) (reverse sweep)
     int pairs;               // bulk launches take x-adjacent cell pairs (nx even, slot bases 2-element aligned)
+    int layout;              // 0 AA pattern, 1 esoteric twist
     int nrot;
     RotorDev rot[MAXROT];
 };

@@ -60,14 +60,27 @@ __device__ __forceinline__ typename Store<S>::T* wslot_ptr(const StepArgs& a, in
     return static_cast<typename Store<S>::T*>(a.wslot[s]);
 }
 
+// Esoteric twist: the link between x and x + c lives at cell x + max(c, 0).
+// Cell index of the link a cell reads f_s over (towards x - c_s) or writes
+// f*_s onto (towards x + c_s), periodic wrap from the neighbour offsets.
+__device__ __forceinline__ int eso_read_node(const Offs& o, int cx, int cy, int cz) {
+    return o.x[1 + (cx < 0)] + o.y[1 + (cy < 0)] + o.z[1 + (cz < 0)];
+}
+__device__ __forceinline__ int eso_write_node(const Offs& o, int cx, int cy, int cz) {
+    return o.x[1 + (cx > 0)] + o.y[1 + (cy > 0)] + o.z[1 + (cz > 0)];
+}
+
 // pre-collision populations of a cell in the layout of phase PH (the
 // neighbour across an open face wraps: that value is undefined by the scheme
 // and only read for cells on an open boundary plane)
-template <int Q, int S, int PH>
+template <int Q, int S, int PH, int L>
 __device__ __forceinline__ void load_pre(const StepArgs& a, int cell, const Offs& o, float (&g)[Q]) {
 #pragma unroll
     for (int s = 0; s < Q; ++s) {
-        if (PH == 0) {
+        if (L == 1) {
+            const int cx = cslot(Q, s, 0), cy = cslot(Q, s, 1), cz = cslot(Q, s, 2);
+            g[s] = Store<S>::ld(slot_ptr<Q, S>(a, PH == 0 ? s : oslot(Q, s)) + eso_read_node(o, cx, cy, cz));
+        } else if (PH == 0) {
             g[s] = Store<S>::ld(slot_ptr<Q, S>(a, s) + cell);
         } else {
             const int cx = cslot(Q, s, 0), cy = cslot(Q, s, 1), cz = cslot(Q, s, 2);
@@ -92,7 +105,7 @@ __device__ __forceinline__ int sel3(int ax, int a0, int a1, int a2) { return ax 
 // ---------------------------------------------------------------------------
 // fused collide and stream
 // ---------------------------------------------------------------------------
-template <int Q, int S, int PH, bool D0>
+template <int Q, int S, int PH, bool D0, int L>
 __device__ __forceinline__ void collide_cell(const StepArgs& a, int x, int y, int z) {
     const int cell = (z * a.n[1] + y) * a.n[0] + x;
     const int ax = a.flow_axis;
@@ -100,9 +113,13 @@ __device__ __forceinline__ void collide_cell(const StepArgs& a, int x, int y, in
     const int na = sel3(ax, a.n[0], a.n[1], a.n[2]);
     const bool inlet = a.open && ca == 0;
     const bool outlet = a.open && ca == na - 1;
-    // odd steps away from the lattice faces: every population at one offset
-    // from a per-slot base (no neighbour index arithmetic)
-    const bool shifted = PH == 1 && x > 0 && x < a.n[0] - 1 && y > 0 && y < a.n[1] - 1 && z > 0 && z < a.n[2] - 1;
+    // every population at one offset from a per-slot base (no neighbour index
+    // arithmetic): AA odd steps away from the lattice faces; esoteric twist
+    // (links towards +x, +y, +z only) away from the upper faces
+    constexpr bool eso = L == 1;
+    const bool shifted = eso ? (x < a.n[0] - 1 && y < a.n[1] - 1 && z < a.n[2] - 1)
+                             : (PH == 1 && x > 0 && x < a.n[0] - 1 && y > 0 && y < a.n[1] - 1 && z > 0 &&
+                                z < a.n[2] - 1);
     Offs o;
     make_offs(a, x, y, z, o);
     float g[Q];
@@ -123,7 +140,7 @@ __device__ __forceinline__ void collide_cell(const StepArgs& a, int x, int y, in
 #pragma unroll
             for (int s = 0; s < Q; ++s) g[s] = Store<S>::ld(static_cast<const T*>(a.rshift[s]) + cell);
         } else {
-            load_pre<Q, S, PH>(a, cell, o, g);
+            load_pre<Q, S, PH, L>(a, cell, o, g);
         }
         float u[3];
         float rho;
@@ -190,10 +207,12 @@ __device__ __forceinline__ void collide_cell(const StepArgs& a, int x, int y, in
         }
 #pragma unroll
         for (int s = 0; s < Q; ++s) {
-            if (PH == 0) {
+            const int cx = cslot(Q, s, 0), cy = cslot(Q, s, 1), cz = cslot(Q, s, 2);
+            if (eso) {
+                Store<S>::st(wslot_ptr<Q, S>(a, PH == 0 ? oslot(Q, s) : s) + eso_write_node(o, cx, cy, cz), g[s]);
+            } else if (PH == 0) {
                 Store<S>::st(wslot_ptr<Q, S>(a, oslot(Q, s)) + cell, g[s]);
             } else {
-                const int cx = cslot(Q, s, 0), cy = cslot(Q, s, 1), cz = cslot(Q, s, 2);
                 Store<S>::st(wslot_ptr<Q, S>(a, s) + (o.x[1 + cx] + o.y[1 + cy] + o.z[1 + cz]), g[s]);
             }
         }
@@ -233,7 +252,12 @@ __device__ __forceinline__ void collide_cell(const StepArgs& a, int x, int y, in
     // boundary planes: populations that would leave through the open face are dropped
 #pragma unroll
     for (int s = 0; s < Q; ++s) {
-        if (PH == 0) {
+        if (eso) {
+            const int cx = cslot(Q, s, 0), cy = cslot(Q, s, 1), cz = cslot(Q, s, 2);
+            const int cas = sel3(ax, cx, cy, cz);
+            if ((inlet && cas < 0) || (outlet && cas > 0)) continue;
+            Store<S>::st(wslot_ptr<Q, S>(a, PH == 0 ? oslot(Q, s) : s) + eso_write_node(o, cx, cy, cz), g[s]);
+        } else if (PH == 0) {
             Store<S>::st(wslot_ptr<Q, S>(a, oslot(Q, s)) + cell, g[s]);
         } else {
             const int cx = cslot(Q, s, 0), cy = cslot(Q, s, 1), cz = cslot(Q, s, 2);
@@ -246,7 +270,7 @@ __device__ __forceinline__ void collide_cell(const StepArgs& a, int x, int y, in
 
 // One cell per thread: the bulk launch when cell pairs are off (nx odd, a
 // static porosity field), or the box launch spanning one rotor box.
-template <int Q, int S, int PH, bool D0>
+template <int Q, int S, int PH, bool D0, int L>
 __global__ void __launch_bounds__(128) collide_kernel(const StepArgs a) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -254,11 +278,11 @@ __global__ void __launch_bounds__(128) collide_kernel(const StepArgs a) {
     if (a.part == 2) {
         const RotorDev& R = a.rot[a.part_rotor];
         if (x >= R.n[0] || y >= R.n[1]) return;
-        collide_cell<Q, S, PH, D0>(a, x + R.lo[0], y + R.lo[1], z + R.lo[2]);
+        collide_cell<Q, S, PH, D0, L>(a, x + R.lo[0], y + R.lo[1], z + R.lo[2]);
         return;
     }
     if (y >= a.n[1] || x >= a.n[0]) return;
-    collide_cell<Q, S, PH, D0>(a, x, y, z);
+    collide_cell<Q, S, PH, D0, L>(a, x, y, z);
 }
 
 // Bulk launches with cell pairs: a thread takes cells x and x + 1 (x even).
@@ -274,7 +298,7 @@ __global__ void __launch_bounds__(128) collide_kernel(const StepArgs a) {
 // spill), 2-3 % faster for 16-bit storage than the unbounded 72 (56, 9 blocks,
 // spills 60-100 bytes and is slower on every storage); D3Q19 at most 48 (10
 // blocks), 3 % faster for 16-bit storage than the unbounded 56, FP32 unchanged.
-template <int Q, int S, int PH>
+template <int Q, int S, int PH, int L>
 __global__ void __launch_bounds__(128, Q == 27 ? 8 : 10) collide_pair_kernel(const StepArgs a) {
     const int x = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -293,22 +317,32 @@ __global__ void __launch_bounds__(128, Q == 27 ? 8 : 10) collide_pair_kernel(con
         const int na = sel3(a.flow_axis, a.n[0], a.n[1], a.n[2]);
         if (ca == 0 || ca1 >= na - 2) plain = false;
     }
-    if (PH == 1 && !(y > 0 && y < a.n[1] - 1 && z > 0 && z < a.n[2] - 1)) plain = false;
+    // the y and z neighbours the pair touches must lie inside the lattice
+    if (L == 0 && PH == 1 && !(y > 0 && y < a.n[1] - 1 && z > 0 && z < a.n[2] - 1)) plain = false;
+    if (L == 1 && !(y < a.n[1] - 1 && z < a.n[2] - 1)) plain = false;
     if (!plain) {
-        collide_cell<Q, S, PH, false>(a, x, y, z);
-        if (x + 1 < a.n[0]) collide_cell<Q, S, PH, false>(a, x + 1, y, z);
+        collide_cell<Q, S, PH, false, L>(a, x, y, z);
+        if (x + 1 < a.n[0]) collide_cell<Q, S, PH, false, L>(a, x + 1, y, z);
         return;
     }
     using T = typename Store<S>::T;
     const int cell = (z * a.n[1] + y) * a.n[0] + x;
-    // odd phase, periodic x: the first cell's neighbour at x - 1 and the last
-    // cell's neighbour at x + 2 lie one row length away
-    const int lo_wrap = (PH == 1 && x == 0) ? a.n[0] : 0;
-    const int hi_wrap = (PH == 1 && x + 2 == a.n[0]) ? -a.n[0] : 0;
+    // periodic x: the first cell's neighbour at x - 1 (AA odd steps) and the
+    // last cell's neighbour at x + 2 (AA odd steps, esoteric twist) lie one
+    // row length away
+    const int lo_wrap = (L == 0 && PH == 1 && x == 0) ? a.n[0] : 0;
+    const int hi_wrap = ((L == 1 || PH == 1) && x + 2 == a.n[0]) ? -a.n[0] : 0;
     F2 g[Q];
 #pragma unroll
     for (int s = 0; s < Q; ++s) {
         const int cx = cslot(Q, s, 0);
+        if (L == 1) {
+            // f_s over the link at x + max(-c_s, 0): one element off for c_x < 0
+            const T* src = static_cast<const T*>(a.rshift[s]) + cell;
+            if (cx >= 0) g[s] = Store2<S>::ld(src);
+            else g[s] = {make_float2(Store<S>::ld(src), Store<S>::ld(src + 1 + hi_wrap))};
+            continue;
+        }
         const T* src = PH == 0 ? slot_ptr<Q, S>(a, s) + cell : static_cast<const T*>(a.rshift[s]) + cell;
         if (PH == 0 || cx == 0) g[s] = Store2<S>::ld(src);
         else if (cx > 0) g[s] = {make_float2(Store<S>::ld(src + lo_wrap), Store<S>::ld(src + 1))};
@@ -319,8 +353,19 @@ __global__ void __launch_bounds__(128, Q == 27 ? 8 : 10) collide_pair_kernel(con
     if (!(fabsf(rho.v.x) < 1e30f) || !(fabsf(rho.v.y) < 1e30f)) atomicOr(a.err, ERR_NONFINITE);
 #pragma unroll
     for (int s = 0; s < Q; ++s) {
-        T* dst = PH == 0 ? wslot_ptr<Q, S>(a, oslot(Q, s)) + cell : static_cast<T*>(a.wshift[s]) + cell;
         const int cx = cslot(Q, s, 0);
+        if (L == 1) {
+            // f*_s onto the link at x + max(c_s, 0): one element off for c_x > 0
+            T* dst = static_cast<T*>(a.wshift[s]) + cell;
+            if (cx <= 0) {
+                Store2<S>::st(dst, g[s]);
+            } else {
+                Store<S>::st(dst, g[s].v.x);
+                Store<S>::st(dst + 1 + hi_wrap, g[s].v.y);
+            }
+            continue;
+        }
+        T* dst = PH == 0 ? wslot_ptr<Q, S>(a, oslot(Q, s)) + cell : static_cast<T*>(a.wshift[s]) + cell;
         if (PH == 0 || cx == 0) {
             Store2<S>::st(dst, g[s]);
         } else if (cx > 0) {
@@ -424,7 +469,8 @@ __device__ void cell_velocity(const StepArgs& a, int x, int y, int z, float u[3]
     make_offs(a, x, y, z, o);
     const int cell = (z * a.n[1] + y) * a.n[0] + x;
     float g[Q];
-    load_pre<Q, S, PH>(a, cell, o, g);
+    if (a.layout == 1) load_pre<Q, S, PH, 1>(a, cell, o, g);
+    else load_pre<Q, S, PH, 0>(a, cell, o, g);
     float drho, j[3];
     moments01<Q>(g, drho, j);
     const float inv = 1.0f / (1.0f + drho);
@@ -611,7 +657,12 @@ __global__ void __launch_bounds__(256) force_kernel(const StepArgs a) {
             const int o_s = oslot(Q, s);
             const int nbx = o.x[1 + c0] + o.y[1 + c1] + o.z[1 + c2];
             float out_s, in_o;   // f*_s(x) and f*_o(x + c_s)
-            if (PH == 0) {
+            if (a.layout == 1) {
+                // esoteric twist: both on the link between x and x + c_s
+                const int nl = eso_write_node(o, c0, c1, c2);
+                out_s = Store<S>::ld(wslot_ptr<Q, S>(a, PH == 0 ? o_s : s) + nl);
+                in_o = Store<S>::ld(wslot_ptr<Q, S>(a, PH == 0 ? s : o_s) + nl);
+            } else if (PH == 0) {
                 out_s = Store<S>::ld(wslot_ptr<Q, S>(a, o_s) + cell);
                 in_o = Store<S>::ld(wslot_ptr<Q, S>(a, s) + nbx);
             } else {
@@ -780,6 +831,16 @@ __global__ void init_kernel(const StepArgs a, const float* rho, const float* u, 
     if (u) { uu[0] = u[cell]; uu[1] = u[a.N + cell]; uu[2] = u[2 * a.N + cell]; }
     float g[Q];
     equilibrium<Q>(g, drho, uu);
+    if (a.layout == 1) {
+        // even-step layout of the esoteric twist: f_s on the link towards x - c_s
+        Offs o;
+        make_offs(a, x, y, z, o);
+#pragma unroll
+        for (int s = 0; s < Q; ++s)
+            Store<S>::st(slot_ptr<Q, S>(a, s) + eso_read_node(o, cslot(Q, s, 0), cslot(Q, s, 1), cslot(Q, s, 2)),
+                         g[s]);
+        return;
+    }
 #pragma unroll
     for (int s = 0; s < Q; ++s) Store<S>::st(slot_ptr<Q, S>(a, s) + cell, g[s]);
 }
@@ -794,7 +855,8 @@ __global__ void fields_kernel(const StepArgs a, float* rho, float* u) {
     Offs o;
     make_offs(a, x, y, z, o);
     float g[Q];
-    load_pre<Q, S, PH>(a, cell, o, g);
+    if (a.layout == 1) load_pre<Q, S, PH, 1>(a, cell, o, g);
+    else load_pre<Q, S, PH, 0>(a, cell, o, g);
     float drho, j[3];
     moments01<Q>(g, drho, j);
     const float r = 1.0f + drho;
@@ -838,38 +900,32 @@ static dim3 cell_block(int nx) {
     return dim3(bx, 128 / bx >= 1 ? 128 / bx : 1, 1);
 }
 
-template <int Q, int S>
-static cudaError_t launch_collide_t(const StepArgs& a, cudaStream_t s) {
+template <int Q, int S, int L>
+static cudaError_t launch_collide_l(const StepArgs& a, cudaStream_t s) {
     const int* n = a.part == 2 ? a.rot[a.part_rotor].n : a.n;
     const dim3 blk = cell_block(n[0]);
-    if (a.part == 2) {
-        const dim3 grd((n[0] + blk.x - 1) / blk.x, (n[1] + blk.y - 1) / blk.y, n[2]);
-        if (a.d0) {
-            if (a.phase == 0) collide_kernel<Q, S, 0, true><<<grd, blk, 0, s>>>(a);
-            else collide_kernel<Q, S, 1, true><<<grd, blk, 0, s>>>(a);
-        } else {
-            if (a.phase == 0) collide_kernel<Q, S, 0, false><<<grd, blk, 0, s>>>(a);
-            else collide_kernel<Q, S, 1, false><<<grd, blk, 0, s>>>(a);
-        }
-        return cudaGetLastError();
-    }
-    if (a.pairs && !a.d0) {
+    if (a.part != 2 && a.pairs && !a.d0) {
         const int half = (n[0] + 1) / 2;
         const dim3 pb = cell_block(half);
         const dim3 pg((half + pb.x - 1) / pb.x, (n[1] + pb.y - 1) / pb.y, n[2]);
-        if (a.phase == 0) collide_pair_kernel<Q, S, 0><<<pg, pb, 0, s>>>(a);
-        else collide_pair_kernel<Q, S, 1><<<pg, pb, 0, s>>>(a);
+        if (a.phase == 0) collide_pair_kernel<Q, S, 0, L><<<pg, pb, 0, s>>>(a);
+        else collide_pair_kernel<Q, S, 1, L><<<pg, pb, 0, s>>>(a);
         return cudaGetLastError();
     }
     const dim3 grd((n[0] + blk.x - 1) / blk.x, (n[1] + blk.y - 1) / blk.y, n[2]);
     if (a.d0) {
-        if (a.phase == 0) collide_kernel<Q, S, 0, true><<<grd, blk, 0, s>>>(a);
-        else collide_kernel<Q, S, 1, true><<<grd, blk, 0, s>>>(a);
+        if (a.phase == 0) collide_kernel<Q, S, 0, true, L><<<grd, blk, 0, s>>>(a);
+        else collide_kernel<Q, S, 1, true, L><<<grd, blk, 0, s>>>(a);
     } else {
-        if (a.phase == 0) collide_kernel<Q, S, 0, false><<<grd, blk, 0, s>>>(a);
-        else collide_kernel<Q, S, 1, false><<<grd, blk, 0, s>>>(a);
+        if (a.phase == 0) collide_kernel<Q, S, 0, false, L><<<grd, blk, 0, s>>>(a);
+        else collide_kernel<Q, S, 1, false, L><<<grd, blk, 0, s>>>(a);
     }
     return cudaGetLastError();
+}
+
+template <int Q, int S>
+static cudaError_t launch_collide_t(const StepArgs& a, cudaStream_t s) {
+    return a.layout == 1 ? launch_collide_l<Q, S, 1>(a, s) : launch_collide_l<Q, S, 0>(a, s);
 }
 
 template <int Q, int S>

@@ -31,7 +31,7 @@ class Lattice:
                  tau_mo=0.5005, c_smag=0.1, u_in=0.05, eps_h=2.0, transition="smoothstep",
                  sigma_band=1.0, wall_model=True, wm_E=9.8, wm_kappa=0.41, wm_ysample=2.0, wm_tol=1e-4,
                  wm_maxit=10, modes=None, mass_check_every=100, mass_tol=0.05, overlap=True,
-                 device=None, stream=None):
+                 layout="aa", device=None, stream=None):
         import torch
         self.device = torch.device(device if device is not None else "cuda")
         if self.device.index is None:
@@ -51,6 +51,7 @@ class Lattice:
         cfg.wm_tol, cfg.wm_maxit = float(wm_tol), int(wm_maxit)
         cfg.mass_check_every, cfg.mass_tol = int(mass_check_every), float(mass_tol)
         cfg.overlap = int(bool(overlap))
+        cfg.layout = {"aa": 0, "esotwist": 1}[layout] if isinstance(layout, str) else int(layout)
         self._modes = None
         if modes is not None and len(modes):
             self._modes = np.ascontiguousarray(modes, dtype=np.float64).reshape(-1, 9)
