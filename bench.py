@@ -186,7 +186,7 @@ def run_reference(args):
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one bulk collide
 # launch of the rotor256 step from one ncu capture; reported only while the
 # kernel sources hash to the value they had at the capture (else null)
-NCU_TRAFFIC = {"source_sha": "f4fc474f327b7ae9", "bytes_per_launch": 4872692224}
+NCU_TRAFFIC = {"source_sha": "a0dd7ef952cd55a9", "bytes_per_launch": 4872084480}
 
 
 def inflow_planes_pinned(wl, t0, n, dev):
