@@ -389,14 +389,19 @@ def run_cuda(args):
             "thrust_last": float(F[0, wl.flow_axis]) if lat.nrot else None,
             "cpu_baseline": cpu,
         }
-        if world == 1 and not args.no_extra:
+        extras = set() if args.no_extra else set(args.extras.split(","))
+        if world == 1 and extras:
             lat.close()
             torch.cuda.empty_cache()
-            line["storage_study"] = storage_study(dev, args.extra_steps)
-            line["farm"] = farm_run(dev, args.extra_steps)
-            if args.adjoint_steps > 0:
-                line["adjoint"] = adjoint_run(dev, args.adjoint_steps, max(1, args.adjoint_steps // 4), 100)
-            line["driven_rotor"] = driven_run(dev, 200)
+            if "storage" in extras:
+                line["storage_study"] = storage_study(dev, args.extra_steps)
+            if "farm" in extras:
+                line["farm"] = farm_run(dev, args.extra_steps)
+            if "adjoint" in extras and args.adjoint_steps > 0:
+                S = args.adjoint_steps
+                line["adjoint"] = adjoint_run(dev, S, max(1, S // 4), min(100, max(2, S // 2)))
+            if "driven" in extras:
+                line["driven_rotor"] = driven_run(dev, 200)
             if args.farm_wake_steps > 0:
                 line["farm_wake"] = farm_wake(dev, args.farm_wake_steps)
         print(json.dumps(line), flush=True)
@@ -602,6 +607,8 @@ def main(argv=None):
     ap.add_argument("--cpu-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the 16-bit storage study, the farm run and the gradient run")
+    ap.add_argument("--extras", default="storage,farm,adjoint,driven",
+                    help="comma-separated extra studies after the main line: storage, farm, adjoint, driven")
     ap.add_argument("--extra-steps", type=int, default=40)
     ap.add_argument("--farm-wake-steps", type=int, default=0,
                     help="steps of the wind-farm wake study (mean loads and axial-velocity lines 2 D and 4 D "
