@@ -2,7 +2,7 @@
 turbulent inflow), the 512x512x1024 D3Q27 rotor of the storage study (FP32)
 and the 1536x512x1024 wind farm (805M cells, 6 rotors), in the launch
 configuration the benchmark times, compared with the FP64 oracle at sampled
-cells.
+cells; and a lattice at the cell-count limit.
 
 After k steps a cell depends only on cells within a few lattice spacings
 (one cell per step for collide-and-stream, at most 4 per step where the wall
@@ -135,3 +135,46 @@ def test_fullsize_farm_sampled_parity():
     """Wind-farm scale on one GPU (1536x512x1024, 805M cells, 3x2 rotors, flow
     along x): sampled cells at every rotor and near the inlet."""
     _run_and_compare(W.workload("farm"))
+
+
+def test_maximum_size_lattice():
+    """Near the 2^31 - 1 cell limit: 1023 x 1024 x 2049 = 2,146,434,048 cells,
+    BF16 storage (81.6 GB).  A Taylor-Green field in (x, y), uniform in z,
+    evolves identically in every z slice; nx odd keeps one cell per thread, so
+    every cell runs the same arithmetic and the slices at the end of the index
+    range equal a 4-slice lattice bit for bit after steps of both parities."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("a CUDA device is required for the gpu-marked tests")
+    from paper_2510_13726_b300.build import build
+    build()
+    import paper_2510_13726_b300 as P
+    nx, ny, nz = 1023, 1024, 2049
+    assert nx * ny * nz < 2 ** 31 - 1
+    kw = dict(storage="bf16s", open_boundaries=False, tau_mo=0.8, c_smag=0.1, u_in=0.0, wall_model=False,
+              mass_check_every=0)
+
+    def tgv(n_z, dev):
+        x = torch.arange(nx, device=dev, dtype=torch.float32) * (2 * np.pi / nx)
+        y = torch.arange(ny, device=dev, dtype=torch.float32) * (2 * np.pi / ny)
+        ux = 0.03 * torch.sin(x)[None, :] * torch.cos(y)[:, None]
+        uy = -0.03 * torch.cos(x)[None, :] * torch.sin(y)[:, None]
+        u = torch.stack([ux, uy, torch.zeros_like(ux)])[:, None].expand(3, n_z, ny, nx)
+        return u.contiguous()
+
+    small = P.Lattice(nx, ny, 4, **kw)
+    small.init_fields(u=tgv(4, small.device))
+    small.step(5)
+    ref = small.fields()[1][:, 0].clone()
+    del small
+    big = P.Lattice(nx, ny, nz, **kw)
+    big.init_fields(u=tgv(nz, big.device))
+    m0 = big.mass()
+    big.step(5)
+    _, u = big.fields()
+    for z in (nz - 1, nz - 2, nz // 2, 0):
+        assert torch.equal(u[:, z], ref), z
+    del u
+    assert abs(big.mass() - m0) <= 1e-6 * m0
+    big.close()
+    torch.cuda.empty_cache()
