@@ -118,3 +118,26 @@ def test_snapshot_resume_and_gradient_refusal(P):
     with pytest.raises(P.HlError) as e:
         lat.grad(4, 2, [1.0], [0.0], ckpt_every=2)
     assert e.value.code == -5
+
+
+def test_porosity_field_hybrid_band_and_driven_rotor_bit_identical_to_aa(P):
+    """A static porosity field (the d0 collide instance), sigma < 1 (the
+    band-strain kernel reads neighbour velocities through the layout) and a
+    torque-driven rotor (forces read the post-collision links), one cell per
+    thread: interior fields, loads and the rotor state equal the AA layout's."""
+    import torch
+    wl = Workload("odd47", 47, 48, 96, turbulence=0.05, rotors=_single(47, 48, 96, 12.0, 6.0))
+    rng = np.random.default_rng(11)
+    d0 = torch.from_numpy((1.0 - 0.2 * rng.random((96, 48, 47))).astype(np.float32))
+    lats = []
+    for layout in ("aa", "esotwist"):
+        lat = P.Lattice.from_workload(wl, layout=layout, sigma_band=0.5)
+        lat.set_d0(d0.to(lat.device))
+        lat.step(3)
+        lat.set_drive(0, 5e3, k_gen=1.0)
+        lat.step(20)
+        lats.append(lat)
+    (ra, ua), (re, ue) = lats[0].fields(), lats[1].fields()
+    assert torch.equal(ra[1:-1], re[1:-1]) and torch.equal(ua[:, 1:-1], ue[:, 1:-1])
+    assert np.array_equal(lats[0].forces()[0], lats[1].forces()[0])
+    assert lats[0].drive_state(0) == lats[1].drive_state(0)
