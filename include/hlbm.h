@@ -253,6 +253,12 @@ hl_status hl_debug_collide(int q, int n, const float* d_g_in, const float* d_d, 
                            const float* d_sigma, const float* d_S, double tau_mo, double c_smag,
                            float* d_g_out, void* stream);
 
+/* As hl_debug_collide for the bulk branch, through the packed two-cell
+ * collision of the bulk launch (cells 2k and 2k+1 share a thread's FP32x2
+ * operations); n even (HL_ERR_ARG otherwise).  Runs on `stream`. */
+hl_status hl_debug_collide_pair(int q, int n, const float* d_g_in, double tau_mo, double c_smag, float* d_g_out,
+                                void* stream);
+
 /* ---- gradients (discrete adjoint of the step) ----
  *
  * Objective over the next `steps` steps from the current state:

@@ -80,6 +80,7 @@ SIGNATURES = {
     "hl_set_d0": (C.c_int, [_vp, _vp]),
     "hl_set_inflow_plane": (C.c_int, [_vp, _vp]),
     "hl_loads_async": (C.c_int, [_vp, _vp]),
+    "hl_debug_collide_pair": (C.c_int, [C.c_int, C.c_int, _vp, C.c_double, C.c_double, _vp, _vp]),
     "hl_set_pitch": (C.c_int, [_vp, C.c_int, C.c_double]),
     "hl_freeze_sets": (C.c_int, [_vp, C.c_int]),
     "hl_grad_workspace_size": (C.c_int, [_vp, C.c_int, C.c_int, C.POINTER(C.c_size_t)]),

@@ -27,6 +27,7 @@
 
 #include "hl_adjoint.cuh"
 #include "hl_host.h"
+#include "hl_pair.cuh"
 
 namespace hl {
 
@@ -559,6 +560,23 @@ cudaError_t launch_adj_box(int Q, int S, const StepArgs& a, const AdjArgs& j, bo
     HL_ADJ_DISPATCH(Q, S, launch_adj_box_t, a, j, force_on, s);
 }
 
+// unit check of the packed bulk collision: cells 2k and 2k+1 of [n][q] in one thread
+template <int Q>
+__global__ void debug_collide_pair_kernel(int n, const float* gin, float tau_mo, float Ksmag, float* gout) {
+    const int c = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (c + 1 >= n) return;
+    F2 g[Q];
+#pragma unroll
+    for (int s = 0; s < Q; ++s) g[s] = {make_float2(gin[(long long)c * Q + s], gin[(long long)(c + 1) * Q + s])};
+    F2 u[3];
+    collide_pair<Q>(g, tau_mo, Ksmag, u);
+#pragma unroll
+    for (int s = 0; s < Q; ++s) {
+        gout[(long long)c * Q + s] = g[s].v.x;
+        gout[(long long)(c + 1) * Q + s] = g[s].v.y;
+    }
+}
+
 }  // namespace
 }  // namespace hl
 
@@ -977,6 +995,18 @@ hl_status hl_freeze_sets(hl_lattice* lat, int on) {
     lat->frozen = on != 0;
     for (int k = 0; k < lat->nrot; ++k) lat->rot[k].pitch_sets = lat->rot[k].pitch;
     return HL_OK;
+}
+
+hl_status hl_debug_collide_pair(int q, int n, const float* d_g_in, double tau_mo, double c_smag, float* d_g_out,
+                                void* stream) {
+    if ((q != 19 && q != 27) || n < 0 || (n % 2) != 0 || (n > 0 && (!d_g_in || !d_g_out))) return HL_ERR_ARG;
+    if (n == 0) return HL_OK;
+    const float Ks = (float)(18.0 * std::sqrt(2.0) * c_smag * c_smag);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int blocks = (n / 2 + 127) / 128;
+    if (q == 19) debug_collide_pair_kernel<19><<<blocks, 128, 0, s>>>(n, d_g_in, (float)tau_mo, Ks, d_g_out);
+    else debug_collide_pair_kernel<27><<<blocks, 128, 0, s>>>(n, d_g_in, (float)tau_mo, Ks, d_g_out);
+    return cudaGetLastError() == cudaSuccess ? HL_OK : HL_ERR_CUDA;
 }
 
 hl_status hl_debug_collide_vjp(int q, int n, const float* d_g_in, const float* d_d, const float* d_uB,

@@ -92,6 +92,44 @@ def test_collision_unit_parity(P, q, branch):
     assert err.max() <= 2e-6, err.max()
 
 
+@pytest.mark.parametrize("q", [19, 27])
+def test_packed_collision_unit_parity(P, q):
+    """The packed two-cell bulk collision (FP32x2) against the oracle's
+    single-cell collision (2e-6 w_i, as the one-cell kernel) and against the
+    one-cell kernel itself (a few FP32 roundings), on random states and on
+    equilibrium-like states of fast flows (|u| up to 0.15)."""
+    import torch
+    c, w = P.velocity_set(q)
+    perm = _perm_to_oracle(q, P)
+    n = 8192
+    f = W.random_populations(31 + q, n, w, amplitude=0.1)
+    rng = np.random.default_rng(9)
+    u = rng.uniform(-0.15, 0.15, (n // 2, 3))
+    cu = u @ np.asarray(c, dtype=np.float64).T
+    feq = w * (1 + 3 * cu + 4.5 * cu ** 2 - 1.5 * (u ** 2).sum(1, keepdims=True))
+    f[n // 2:] = feq * (1 + 0.02 * rng.uniform(-1, 1, feq.shape))
+    g32 = (f - w).astype(np.float32)
+    fin = w + g32.astype(np.float64)
+    tau_mo, cs = 0.5005, 0.1
+    gin = torch.tensor(g32, device="cuda")
+    gp = torch.empty_like(gin)
+    gs = torch.empty_like(gin)
+    lib = P.lib()
+    st = torch.cuda.current_stream().cuda_stream
+    assert lib.hl_debug_collide_pair(q, n, gin.data_ptr(), tau_mo, cs, gp.data_ptr(), st) == 0
+    assert lib.hl_debug_collide(q, n, gin.data_ptr(), 0, 0, 0, 0, tau_mo, cs, gs.data_ptr(), st) == 0
+    assert lib.hl_debug_collide_pair(q, 3, gin.data_ptr(), tau_mo, cs, gp.data_ptr(), st) == -1   # n odd
+    torch.cuda.synchronize()
+    fpair = gp.cpu().numpy().astype(np.float64) + w
+    fone = gs.cpu().numpy().astype(np.float64) + w
+    inv = np.argsort(perm)
+    fo, _ = O.collide_cells(q, fin[:, inv], tau_mo=tau_mo, c_smag=cs)
+    fo = fo[:, perm]
+    err = np.abs(fpair - fo) / w
+    assert err.max() <= 2e-6, err.max()
+    assert (np.abs(fpair - fone) / w).max() <= 1e-6
+
+
 def _wl48():
     return W.workload("rotor48")
 
