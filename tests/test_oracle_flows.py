@@ -32,6 +32,22 @@ def _slab_grid(n, c, a, b, h=0.5):
                      hub_radius=0.0, chord_root=1.0, chord_tip=1.0)
 
 
+def _cylinder_grid(half, nz, cz, sign, radius, h=0.5):
+    """Axis-z cylinder as a blade-frame level set (one 'blade', no hub):
+    sign = +1 is solid inside r < radius, sign = -1 solid outside r > radius;
+    the grid spans +-half across the axis and the whole periodic length."""
+    lo = [-half, -half, -cz - 2]
+    hi = [half, half, nz - 1 - cz + 2]
+    g = [int(round((hi[k] - lo[k]) / h)) + 1 for k in range(3)]
+    R = lo[0] + h * np.arange(g[0])
+    T = lo[1] + h * np.arange(g[1])
+    A = lo[2] + h * np.arange(g[2])
+    _, TT, RR = np.meshgrid(A, T, R, indexing="ij")
+    sdf = (sign * (np.hypot(RR, TT) - radius)).astype(np.float32)
+    return BladeGrid(sdf=np.ascontiguousarray(sdf), origin=tuple(lo), spacing=h, radius=1.0,
+                     hub_radius=0.0, chord_root=1.0, chord_tip=1.0)
+
+
 def _tgv_viscosity_error(n, tau=0.8, U0=0.01):
     o = O.Oracle(n, n, 2, open_boundaries=False, tau_mo=tau, c_smag=0.0, u_in=0.0, wall_model=False)
     k = 2 * math.pi / n
@@ -158,6 +174,47 @@ def test_rotating_sphere_symmetry_and_torque_sign():
     assert M[0, 2] < 0
     assert np.abs(F[0]).max() < 1e-5 * abs(M[0, 2]) / 5.0
     assert np.abs(M[0, :2]).max() < 1e-4 * abs(M[0, 2])
+
+
+def test_circular_couette_profile_and_torque():
+    """Laminar flow between a porous cylinder of radius R1 spun at Omega (its
+    cells move with u^B = Omega a x (x - c), Sec. 2.2) and a fixed porous
+    outer wall at R2, periodic along the axis.  Steady state: the Navier-Stokes
+    solution u_theta = A r + B / r with u_theta(R1) = Omega R1, u_theta(R2) = 0
+    (walls at the d = 1/2 level sets), no radial flow, and a torque per unit
+    length 4 pi mu Omega R1^2 R2^2 / (R2^2 - R1^2) on each wall, opposite in
+    sign: the fluid resists the inner cylinder and drags the outer one.  The
+    diffuse interface (2 cells) and the staircase of a 12-cell gap leave a
+    few per cent; a wrong sign of u^B, a dropped (1 - d) u^B or a wrong lever
+    arm in the torque sum each fails by far more."""
+    n, nz, c = 48, 2, (23.5, 23.5, 0.5)
+    R1, R2, Om, tau = 8.0, 20.0, 0.0025, 0.8
+    inner = O.make_rotor(_cylinder_grid(R1 + 4, nz, c[2], 1, R1), center=c, axis=2, omega=Om, n_blades=1,
+                         hub_radius=0.0)
+    outer = O.make_rotor(_cylinder_grid(36.0, nz, c[2], -1, R2), center=c, axis=2, omega=0.0, n_blades=1,
+                         hub_radius=0.0)
+    o = O.Oracle(n, n, nz, open_boundaries=False, tau_mo=tau, c_smag=0.0, u_in=0.0, wall_model=False,
+                 rotors=[inner, outer])
+    o.step(1500)      # about ten e-folding times gap^2 / (pi^2 nu) of the spin-up
+    _, u = o.fields()
+    Y, X = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    dx, dy = X - c[0], Y - c[1]
+    r = np.hypot(dx, dy)
+    ut = (-dy * u[0, 0] + dx * u[1, 0]) / r
+    ur = (dx * u[0, 0] + dy * u[1, 0]) / r
+    A = -Om * R1**2 / (R2**2 - R1**2)
+    B = Om * R1**2 * R2**2 / (R2**2 - R1**2)
+    sel = (r >= R1 + 1) & (r <= R2 - 1)
+    assert np.abs(ut[sel] - (A * r[sel] + B / r[sel])).max() < 0.05 * Om * R1
+    assert np.abs(ur[sel]).max() < 0.01 * Om * R1
+    assert np.array_equal(u[:, 0], u[:, 1])                       # uniform along the axis
+    F, M, _, _ = o.forces()
+    nu = (tau - 0.5) / 3.0
+    Tq = 4.0 * math.pi * nu * Om * R1**2 * R2**2 / (R2**2 - R1**2) * nz
+    assert 0.97 < -M[0, 2] / Tq < 1.08
+    assert abs(M[0, 2] + M[1, 2]) < 1e-3 * Tq                   # steady: the fluid passes the torque on
+    assert np.abs(F).max() < 1e-6 * Tq / R1                       # no net force by symmetry
+    assert np.abs(M[:, :2]).max() < 1e-6 * Tq
 
 
 @pytest.mark.parametrize("wall_model", [False, True])
