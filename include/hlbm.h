@@ -310,7 +310,10 @@ hl_status hl_grad_workspace_size(const hl_lattice* lat, int steps, int ckpt_ever
  * aligned, overwritten.  Synchronises; HL_ERR_NONFINITE / HL_ERR_MASS as
  * hl_step; HL_ERR_STATE for a torque-driven rotor, sigma_band < 1 or a
  * caller's inflow plane (the derivative covers prescribed rotation, the
- * local band collision and the synthetic inflow). */
+ * local band collision and the synthetic inflow).  With the esoteric-twist
+ * layout the state is permuted into the AA layout of the same step for the
+ * sweep (the two layouts give the same trajectory; the copy lives in
+ * d_work) and back at the end, also when the sweep fails. */
 hl_status hl_grad(hl_lattice* lat, int steps, int avg_last, int ckpt_every, const double* w_thrust,
                   const double* w_torque, double* J, double* dJ_dpitch, float* d_dJ_dd0, void* d_work,
                   size_t bytes);

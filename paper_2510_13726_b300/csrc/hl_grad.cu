@@ -76,6 +76,34 @@ __device__ __forceinline__ void load_pre(const StepArgs& a, int cell, const Offs
     }
 }
 
+// Esoteric-twist state <-> AA state of the same step.  Each layout keeps
+// the pre-collision f_s(x) of a step at one place: AA, slot s at x (even
+// steps) or slot sbar at x - c_s (odd steps); esoteric twist, slot s (even)
+// or sbar (odd) at x + max(-c_s, 0); with periodic neighbour indices these
+// places cover the buffer once over all (x, s), so the change of layout is a
+// permutation of the stored values (raw storage words, no rounding).
+template <int Q, int S, int PH>
+__global__ void __launch_bounds__(128) relayout_kernel(const StepArgs a, const void* src, void* dst, int to_eso) {
+    using T = typename Store<S>::T;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
+    if (x >= a.n[0]) return;
+    Offs o;
+    make_offs(a, x, y, z, o);
+    const long long N = a.N;
+    const T* in = static_cast<const T*>(src);
+    T* out = static_cast<T*>(dst);
+#pragma unroll
+    for (int s = 0; s < Q; ++s) {
+        const int cx = cslot(Q, s, 0), cy = cslot(Q, s, 1), cz = cslot(Q, s, 2);
+        const long long base = (long long)(PH == 0 ? s : oslot(Q, s)) * N;
+        const long long aa = base + (PH == 0 ? o.x[1] + o.y[1] + o.z[1] : o.x[1 - cx] + o.y[1 - cy] + o.z[1 - cz]);
+        const long long es = base + (o.x[1 + (cx < 0)] + o.y[1 + (cy < 0)] + o.z[1 + (cz < 0)]);
+        if (to_eso) out[es] = in[aa];
+        else out[aa] = in[es];
+    }
+}
+
 // lam*_s(x) = lam_{t+1, s}(x + c_s); the adjoint is zero on the open planes,
 // so the periodic index of a neighbour across an open face reads a zero
 template <int Q>
@@ -560,6 +588,18 @@ cudaError_t launch_adj_box(int Q, int S, const StepArgs& a, const AdjArgs& j, bo
     HL_ADJ_DISPATCH(Q, S, launch_adj_box_t, a, j, force_on, s);
 }
 
+template <int Q, int S>
+cudaError_t launch_relayout_t(const StepArgs& a, const void* src, void* dst, bool to_eso, cudaStream_t s) {
+    const dim3 grd((a.n[0] + 127) / 128, a.n[1], a.n[2]);
+    if (a.phase == 0) relayout_kernel<Q, S, 0><<<grd, 128, 0, s>>>(a, src, dst, to_eso ? 1 : 0);
+    else relayout_kernel<Q, S, 1><<<grd, 128, 0, s>>>(a, src, dst, to_eso ? 1 : 0);
+    return cudaGetLastError();
+}
+cudaError_t launch_relayout(int Q, int S, const StepArgs& a, const void* src, void* dst, bool to_eso,
+                            cudaStream_t s) {
+    HL_ADJ_DISPATCH(Q, S, launch_relayout_t, a, src, dst, to_eso, s);
+}
+
 // unit check of the packed bulk collision: cells 2k and 2k+1 of [n][q] in one thread
 template <int Q>
 __global__ void debug_collide_pair_kernel(int n, const float* gin, float tau_mo, float Ksmag, float* gout) {
@@ -748,6 +788,15 @@ hl_status join_aux(hl_lattice* lat) {
     return HL_OK;
 }
 
+// the lattice state between the esoteric twist and the AA layout of the
+// current step, through a scratch buffer of the gradient workspace
+hl_status relayout_state(hl_lattice* lat, void* scratch, bool to_eso) {
+    const StepArgs a = make_args(lat);
+    HL_CUDA(lat, launch_relayout(lat->cfg.q, lat->cfg.storage, a, lat->f, scratch, to_eso, lat->stream));
+    HL_CUDA(lat, cudaMemcpyAsync(lat->f, scratch, (size_t)pop_bytes(lat), cudaMemcpyDeviceToDevice, lat->stream));
+    return HL_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -758,10 +807,11 @@ hl_status hl_grad_workspace_size(const hl_lattice* lat, int steps, int ckpt_ever
     return HL_OK;
 }
 
-hl_status hl_grad(hl_lattice* lat, int steps, int avg_last, int ckpt_every, const double* w_thrust,
-                  const double* w_torque, double* J, double* dJ_dpitch, float* d_dJ_dd0, void* d_work,
-                  size_t bytes) {
-    if (!lat) return HL_ERR_ARG;
+}  // extern "C"
+
+// arguments and lattice state hl_grad accepts
+static hl_status grad_check(hl_lattice* lat, int steps, int avg_last, int ckpt_every, const double* w_thrust,
+                            const double* w_torque, const void* d_work, size_t bytes) {
     if (steps < 1 || avg_last < 1 || avg_last > steps || ckpt_every < 1 || !w_thrust || !w_torque || !d_work)
         return fail(lat, HL_ERR_ARG, "hl_grad: invalid arguments");
     if (reinterpret_cast<size_t>(d_work) % ALIGN) return fail(lat, HL_ERR_ARG, "hl_grad: workspace not aligned");
@@ -772,18 +822,25 @@ hl_status hl_grad(hl_lattice* lat, int steps, int avg_last, int ckpt_every, cons
         return fail(lat, HL_ERR_STATE, "hl_grad: gradients cover the local band collision only (sigma_band = 1)");
     if (lat->inflow)
         return fail(lat, HL_ERR_STATE, "hl_grad: the recompute cannot replay a caller's inflow planes (synthetic inflow only)");
-    if (lat->cfg.layout != 0)
-        return fail(lat, HL_ERR_STATE, "hl_grad: the reverse kernels address the AA layout (layout = 0)");
+    if (bytes < grad_layout(lat, steps, ckpt_every).total)
+        return fail(lat, HL_ERR_WORKSPACE, "hl_grad: workspace too small");
+    return HL_OK;
+}
+
+// the sweep on a lattice in the AA layout
+static hl_status grad_aa(hl_lattice* lat, int steps, int avg_last, int ckpt_every, const double* w_thrust,
+                         const double* w_torque, double* J, double* dJ_dpitch, float* d_dJ_dd0, void* d_work,
+                         size_t bytes) {
+    hl_status rc = grad_check(lat, steps, avg_last, ckpt_every, w_thrust, w_torque, d_work, bytes);
+    if (rc != HL_OK) return rc;
     const int T = steps, K = ckpt_every, na = avg_last;
     const GradLayout G = grad_layout(lat, T, K);
-    if (bytes < G.total) return fail(lat, HL_ERR_WORKSPACE, "hl_grad: workspace too small");
     char* ws = static_cast<char*>(d_work);
     const int Q = lat->cfg.q, S = lat->cfg.storage;
     cudaStream_t st = lat->stream;
     const long long t0 = lat->t;
     const size_t ckb = ckpt_bytes(lat), smb = small_bytes(lat), pb = align_up((size_t)pop_bytes(lat));
     const size_t plb = sizeof(float) * 3 * plane_cells(lat->cfg);
-    hl_status rc;
 
     // per-rotor adjoint arrays
     struct RAdj { float *ddp, *gub, *gS; double *gut[2], *pacc, *accsnap; } ra[MAXROT];
@@ -968,6 +1025,32 @@ hl_status hl_grad(hl_lattice* lat, int steps, int avg_last, int ckpt_every, cons
         if (dJ_dpitch) dJ_dpitch[k] = s;
     }
     return read_error_word(lat);
+}
+
+extern "C" {
+
+hl_status hl_grad(hl_lattice* lat, int steps, int avg_last, int ckpt_every, const double* w_thrust,
+                  const double* w_torque, double* J, double* dJ_dpitch, float* d_dJ_dd0, void* d_work,
+                  size_t bytes) {
+    if (!lat) return HL_ERR_ARG;
+    if (lat->cfg.layout == 0)
+        return grad_aa(lat, steps, avg_last, ckpt_every, w_thrust, w_torque, J, dJ_dpitch, d_dJ_dd0, d_work, bytes);
+    // esoteric twist: the sweep runs on the AA form of the same state (the
+    // two layouts give the same trajectory); the adjoint arrays of the
+    // workspace, not yet or no longer in use, hold the permuted copy
+    hl_status rc = grad_check(lat, steps, avg_last, ckpt_every, w_thrust, w_torque, d_work, bytes);
+    if (rc != HL_OK) return rc;
+    void* scratch = static_cast<char*>(d_work) + grad_layout(lat, steps, ckpt_every).lam;
+    if ((rc = relayout_state(lat, scratch, false)) != HL_OK) return rc;
+    lat->cfg.layout = 0;
+    rc = grad_aa(lat, steps, avg_last, ckpt_every, w_thrust, w_torque, J, dJ_dpitch, d_dJ_dd0, d_work, bytes);
+    lat->cfg.layout = 1;
+    // back at the step the lattice ended on, also after a failed sweep
+    const hl_status rb = relayout_state(lat, scratch, true);
+    if (rc != HL_OK) return rc;
+    if (rb != HL_OK) return rb;
+    HL_CUDA(lat, cudaStreamSynchronize(lat->stream));
+    return HL_OK;
 }
 
 hl_status hl_set_d0(hl_lattice* lat, const float* d_d0) {
