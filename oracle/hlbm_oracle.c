@@ -1252,9 +1252,12 @@ size_t or_sizeof_rotor(void) { return sizeof(or_rotor); }
 /* cell sets (force cells, wall cells) frozen at their forward values. */
 /* Every local Jacobian is taken by complex-step differentiation       */
 /* (f(x + i h) = f(x) + i h f'(x) + O(h^2), h = 1e-30): derivatives to */
-/* rounding, with no hand-derived formula; the wall-model Newton roots */
-/* are differentiated by the implicit function theorem at the root,    */
-/* with complex-step partials of the residuals.                        */
+/* rounding, with no hand-derived formula; the two wall-model Newton   */
+/* solves are differentiated through the iterations they take (complex */
+/* step through the iterates, stopping rule and guard included).  The  */
+/* finite-difference strain of the sigma < 1 band is transposed by     */
+/* hand (it is linear in the neighbours' velocities), with            */
+/* du/df_i = (c_i - u) / rho.                                          */
 /* ================================================================== */
 
 typedef double complex cplx;
@@ -1696,7 +1699,6 @@ int or_adjoint(or_state* S, int T, int n_avg, const double* wT, const double* wQ
     if (T < 1 || n_avg < 1 || n_avg > T) return -1;
     for (int k = 0; k < S->nrot; ++k)
         if (S->rot[k].driven) return -3;   /* gradients cover prescribed rotation only */
-    if (P->sigma_band < 1.0) return -3;    /* and the local (sigma = 1) band collision */
     or_tape tp;
     tp.f = (double*)malloc(sizeof(double) * (size_t)T * q * N);
     tp.wm_ut = (double*)malloc(sizeof(double) * (size_t)T * N);
@@ -1889,6 +1891,45 @@ int or_adjoint(or_state* S, int T, int n_avg, const double* wT, const double* wQ
                     }
                     for (int i = 0; i < q; ++i) lam_new[(size_t)i * N + o] = lf[i];
                 }
+
+        /* adjoint of the finite-difference strain (sigma < 1): S^FD of a force
+           cell off the wall set is built by fd_strain from the pre-collision
+           velocities of its axis neighbours, g_ab = (u_b(x + e_a) - u_b(x - e_a)) / h_a
+           and S = (g + g^T) / 2; its transpose hands dJ/dg_ab = (gS_ab + gS_ba) / 2
+           to those velocities (to the cell itself where a one-sided difference
+           replaced a neighbour across an open face), and du/df_i = (c_i - u) / rho
+           to their populations */
+        if (P->sigma_band < 1.0)
+            for (int z = 0; z < P->nz; ++z)
+                for (int y = 0; y < P->ny; ++y)
+                    for (int x = 0; x < P->nx; ++x) {
+                        size_t o = cidx(S, x, y, z);
+                        if (!(S->flags[o] & FL_B) || (P->wall_model && (S->flags[o] & FL_W))) continue;
+                        double G[3][3];
+                        for (int a = 0; a < 3; ++a)
+                            for (int b = 0; b < 3; ++b) G[a][b] = 0.5 * (g_S[9 * o + 3 * a + b] + g_S[9 * o + 3 * b + a]);
+                        const int xi[3] = {x, y, z};
+                        for (int a = 0; a < 3; ++a) {
+                            int e[3] = {0, 0, 0};
+                            e[a] = 1;
+                            int xp[3], xm[3];
+                            const int okp = neighbour(S, xi, e, +1, xp), okm = neighbour(S, xi, e, -1, xm);
+                            const double h = (okp && okm) ? 2.0 : 1.0;
+                            const size_t cp = okp ? cidx(S, xp[0], xp[1], xp[2]) : o;
+                            const size_t cm = okm ? cidx(S, xm[0], xm[1], xm[2]) : o;
+                            for (int side = 0; side < 2; ++side) {
+                                const size_t cn = side == 0 ? cp : cm;
+                                const double sg = side == 0 ? 1.0 / h : -1.0 / h;
+                                double u[3], rho;
+                                cell_velocity(S, cn, u, &rho);
+                                for (int i = 0; i < q; ++i) {
+                                    double acc = 0.0;
+                                    for (int b = 0; b < 3; ++b) acc += sg * G[a][b] * (L->c[i][b] - u[b]);
+                                    lam_new[(size_t)i * N + cn] += acc / rho;
+                                }
+                            }
+                        }
+                    }
 
         /* adjoint of the wall model: corner velocities and pitch */
         if (P->wall_model) {
