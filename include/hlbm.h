@@ -66,7 +66,7 @@ typedef int hl_status;
  *                  Chapman-Enskog term of the finite-difference strain
  *                  (central differences of the pre-collision velocity of
  *                  the six axis neighbours); wall cells use sigma = 0 with
- *                  the wall model's strain; hl_grad needs sigma_band = 1
+ *                  the wall model's strain
  *  eps_h           width of the porosity transition (Definition "Lattice Porosity")
  *  transition      0 smoothstep t^2 (3 - 2t), 1 linear s = phi/eps + 1/2
  *  wall_model      1: Spalding wall function on the wall cells (Sec. 2.2.1)
@@ -308,9 +308,10 @@ hl_status hl_grad_workspace_size(const hl_lattice* lat, int steps, int ckpt_ever
  * spacing (memory vs. one recomputed forward step per step).  d_work:
  * caller's device workspace of hl_grad_workspace_size bytes, 256-byte
  * aligned, overwritten.  Synchronises; HL_ERR_NONFINITE / HL_ERR_MASS as
- * hl_step; HL_ERR_STATE for a torque-driven rotor, sigma_band < 1 or a
- * caller's inflow plane (the derivative covers prescribed rotation, the
- * local band collision and the synthetic inflow).  With the esoteric-twist
+ * hl_step; HL_ERR_STATE for a torque-driven rotor or a caller's inflow
+ * plane (the derivative covers prescribed rotation and the synthetic
+ * inflow; with sigma_band < 1 it includes the finite-difference strain of
+ * the band cells, transposed onto their neighbours' populations).  With the esoteric-twist
  * layout the state is permuted into the AA layout of the same step for the
  * sweep (the two layouts give the same trajectory; the copy lives in
  * d_work) and back at the end, also when the sweep fails. */

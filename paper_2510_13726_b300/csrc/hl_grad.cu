@@ -20,6 +20,8 @@
 //                           momentum exchange and the band parameters
 //   adj_wall_kernel         reverse pass of the wall model: corner populations,
 //                           pitch, the next step's Newton start
+//   adj_band_strain_kernel  (sigma < 1) reverse pass of the band strain: the
+//                           neighbours' populations
 // Memory: checkpoints of the full state every K steps, and the K states of a
 // segment recomputed out of place (read buffer j, write buffer j + 1).
 #include <cmath>
@@ -280,10 +282,12 @@ __global__ void __launch_bounds__(128) adj_box_kernel(const StepArgs a, const Ad
         } else {
             B.uB[0] = B.uB[1] = B.uB[2] = 0.0f;
         }
-        B.sigma = a.sigma_band;
+        // band parameters as the forward box collision takes them
+        B.sigma = (fl & FL_B) ? a.sigma_band : 1.0f;
 #pragma unroll
         for (int k = 0; k < 6; ++k) B.S[k] = 0.0f;
         const bool wall = a.wall_model && (fl & FL_W);
+        const bool hybrid = !wall && (fl & FL_B) && a.sigma_band < 1.0f;
         if (wall) {
             const float* wm = R.wm + bi;
             B.uB[0] += wm[0];
@@ -292,6 +296,11 @@ __global__ void __launch_bounds__(128) adj_box_kernel(const StepArgs a, const Ad
 #pragma unroll
             for (int k = 0; k < 6; ++k) B.S[k] = wm[(3 + k) * BC];
             B.sigma = 0.0f;
+        } else if (hybrid) {
+            // S^FD of the band-strain kernel (taped with the wall-model rows)
+            const float* wm = R.wm + bi;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) B.S[k] = wm[(3 + k) * BC];
         }
         float gd, guB[3], gS[6], u[3], rho;
         collide_vjp<Q, true>(g, B, a.tau_mo, a.Ksmag, ls, gd, guB, gS, u, rho);
@@ -301,6 +310,8 @@ __global__ void __launch_bounds__(128) adj_box_kernel(const StepArgs a, const Ad
             R.gub[bi] = guB[0];
             R.gub[BC + bi] = guB[1];
             R.gub[2 * BC + bi] = guB[2];
+        }
+        if (wall || hybrid) {
 #pragma unroll
             for (int k = 0; k < 6; ++k) R.gS[k * BC + bi] = gS[k];
         }
@@ -321,6 +332,69 @@ __global__ void __launch_bounds__(128) adj_box_kernel(const StepArgs a, const Ad
         if (t != 0.0) {
             const unsigned b = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
             atomicAdd(R.pacc + b % PACC_SLOTS, t);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// reverse pass of the band strain (sigma < 1, Sec. 2.2): S^FD of a force cell
+// off the wall set is (g + g^T) / 2 with g_mb = (u_b(x + e_m) - u_b(x - e_m)) / 2
+// from the neighbours' pre-collision populations; its adjoint (the six stored
+// components, from the box adjoint) goes to those velocities and through
+// du_b/df_s = (c_sb - u_b) / rho to the neighbours' population adjoints
+// (atomics: neighbouring band cells share neighbours)
+// ---------------------------------------------------------------------------
+template <int Q, int S, int PH>
+__global__ void __launch_bounds__(128) adj_band_strain_kernel(const StepArgs a, const AdjArgs j) {
+    const RotorDev& R = a.rot[blockIdx.y];
+    int count = *((volatile int*)R.count);
+    if ((long long)count > R.box_cells) count = (int)R.box_cells;
+    const long long N = a.N, BC = R.box_cells;
+    for (int idx = list_first(); idx < count; idx += list_stride()) {
+        const long long bi = R.list[idx];
+        if (a.wall_model && (R.flags[bi] & FL_W)) continue;
+        const int bx = (int)(bi % R.n[0]);
+        const long long r2 = bi / R.n[0];
+        const int by = (int)(r2 % R.n[1]);
+        const int bz = (int)(r2 / R.n[1]);
+        // the forward left S^FD = 0 where the stencil leaves the box
+        if (bx < 1 || by < 1 || bz < 1 || bx > R.n[0] - 2 || by > R.n[1] - 2 || bz > R.n[2] - 2) continue;
+        const int x = R.lo[0] + bx, y = R.lo[1] + by, z = R.lo[2] + bz;
+        float Sb[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) Sb[k] = R.gS[k * BC + bi];
+        // adjoint of g_mb (xx yy zz xy xz yz storage order of S)
+        const float G[3][3] = {{Sb[0], 0.5f * Sb[3], 0.5f * Sb[4]},
+                               {0.5f * Sb[3], Sb[1], 0.5f * Sb[5]},
+                               {0.5f * Sb[4], 0.5f * Sb[5], Sb[2]}};
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {
+                const int sg = side == 0 ? 1 : -1;
+                const int xn = x + (m == 0) * sg, yn = y + (m == 1) * sg, zn = z + (m == 2) * sg;
+                const int cn = (zn * a.n[1] + yn) * a.n[0] + xn;
+                Offs o;
+                make_offs(a, xn, yn, zn, o);
+                float g[Q];
+                load_pre<Q, S, PH>(a, cn, o, g);
+                float rho = 1.0f, jm[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+                for (int s = 0; s < Q; ++s) {
+                    rho += g[s];
+                    jm[0] += float(cslot(Q, s, 0)) * g[s];
+                    jm[1] += float(cslot(Q, s, 1)) * g[s];
+                    jm[2] += float(cslot(Q, s, 2)) * g[s];
+                }
+                const float inv = 1.0f / rho;
+                const float ub[3] = {0.5f * sg * G[m][0] * inv, 0.5f * sg * G[m][1] * inv, 0.5f * sg * G[m][2] * inv};
+                const float ubu = (ub[0] * jm[0] + ub[1] * jm[1] + ub[2] * jm[2]) * inv;
+#pragma unroll
+                for (int s = 0; s < Q; ++s)
+                    atomicAdd(j.lam + (long long)s * N + cn, float(cslot(Q, s, 0)) * ub[0] +
+                                                                 float(cslot(Q, s, 1)) * ub[1] +
+                                                                 float(cslot(Q, s, 2)) * ub[2] - ubu);
+            }
         }
     }
 }
@@ -566,6 +640,11 @@ cudaError_t launch_adj_box_t(const StepArgs& a, const AdjArgs& j, bool force_on,
         const dim3 grd(WALL_BLOCKS, a.nrot);
         if (a.phase == 0) adj_wall_kernel<Q, S, 0><<<grd, WALL_THREADS, 0, s>>>(a, j);
         else adj_wall_kernel<Q, S, 1><<<grd, WALL_THREADS, 0, s>>>(a, j);
+    }
+    if (a.nrot > 0 && a.sigma_band < 1.0f) {
+        const dim3 grd(WALL_BLOCKS, a.nrot);
+        if (a.phase == 0) adj_band_strain_kernel<Q, S, 0><<<grd, WALL_THREADS, 0, s>>>(a, j);
+        else adj_band_strain_kernel<Q, S, 1><<<grd, WALL_THREADS, 0, s>>>(a, j);
     }
     return cudaGetLastError();
 }
@@ -818,8 +897,6 @@ static hl_status grad_check(hl_lattice* lat, int steps, int avg_last, int ckpt_e
     for (int k = 0; k < lat->nrot; ++k)
         if (lat->rot[k].driven)
             return fail(lat, HL_ERR_STATE, "hl_grad: gradients cover prescribed rotation only (rotor is torque-driven)");
-    if (lat->cfg.sigma_band != 1.0)
-        return fail(lat, HL_ERR_STATE, "hl_grad: gradients cover the local band collision only (sigma_band = 1)");
     if (lat->inflow)
         return fail(lat, HL_ERR_STATE, "hl_grad: the recompute cannot replay a caller's inflow planes (synthetic inflow only)");
     if (bytes < grad_layout(lat, steps, ckpt_every).total)
@@ -841,6 +918,9 @@ static hl_status grad_aa(hl_lattice* lat, int steps, int avg_last, int ckpt_ever
     const long long t0 = lat->t;
     const size_t ckb = ckpt_bytes(lat), smb = small_bytes(lat), pb = align_up((size_t)pop_bytes(lat));
     const size_t plb = sizeof(float) * 3 * plane_cells(lat->cfg);
+    // the wall-model rows (u^B and S^WM of wall cells, S^FD of hybrid band
+    // cells) are taped per step when either is in use
+    const bool tape_wm = lat->cfg.wall_model || lat->cfg.sigma_band < 1.0;
 
     // per-rotor adjoint arrays
     struct RAdj { float *ddp, *gub, *gS; double *gut[2], *pacc, *accsnap; } ra[MAXROT];
@@ -944,11 +1024,12 @@ static hl_status grad_aa(hl_lattice* lat, int steps, int avg_last, int ckpt_ever
                 StepArgs a = args_at(lat, t, buf(jj), buf(jj));
                 a.part = 0;
                 HL_CUDA(lat, launch_band(Q, S, a, bs));
+                HL_CUDA(lat, launch_band_strain(Q, S, a, bs));
                 if (lat->cfg.wall_model) HL_CUDA(lat, launch_wall(Q, S, a, bs));
                 for (int k = 0; k < lat->nrot; ++k)
                     HL_CUDA(lat, cudaMemsetAsync(lat->rot[k].dev.count, 0, 2 * sizeof(int), bs));
             }
-            if (lat->nrot > 0 && lat->cfg.wall_model && (rc = wm_copy(lat, sm, true, bs)) != HL_OK) return rc;
+            if (lat->nrot > 0 && tape_wm && (rc = wm_copy(lat, sm, true, bs)) != HL_OK) return rc;
         }
         // both halves of the reverse step read states written by both halves
         // of the recomputation
@@ -982,7 +1063,7 @@ static hl_status grad_aa(hl_lattice* lat, int steps, int avg_last, int ckpt_ever
             // box stream: forward quantities of step t, then the box adjoint
             if (lat->nrot > 0) {
                 // the step's wall-model output from the tape (the linearisation point)
-                if (lat->cfg.wall_model && (rc = wm_copy(lat, sm, false, bs)) != HL_OK) return rc;
+                if (tape_wm && (rc = wm_copy(lat, sm, false, bs)) != HL_OK) return rc;
                 SmallOff so;
                 small_layout(lat, &so);
                 for (int k = 0; k < lat->nrot; ++k) {
