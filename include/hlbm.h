@@ -283,7 +283,10 @@ hl_status hl_set_d0(hl_lattice* lat, const float* d_d0);
  * every later step while set, so the caller may overwrite it between steps
  * on the lattice's stream; NULL restores the synthetic inflow of the
  * configuration (u_in and its Fourier modes, Sec. 4 inflow condition).
- * HL_ERR_STATE without open boundaries; hl_grad rejects a set plane. */
+ * HL_ERR_STATE without open boundaries.  hl_grad reads the plane in every
+ * step of its sweep (forward pass and recompute), so the inflow over the
+ * sweep is the plane's content at the call; the inlet equilibrium does not
+ * depend on the state, so the plane enters no derivative. */
 hl_status hl_set_inflow_plane(hl_lattice* lat, const float* d_plane);
 
 /* Change the pitch of rotor `rotor` (rad) for the following steps. */
@@ -308,10 +311,10 @@ hl_status hl_grad_workspace_size(const hl_lattice* lat, int steps, int ckpt_ever
  * spacing (memory vs. one recomputed forward step per step).  d_work:
  * caller's device workspace of hl_grad_workspace_size bytes, 256-byte
  * aligned, overwritten.  Synchronises; HL_ERR_NONFINITE / HL_ERR_MASS as
- * hl_step; HL_ERR_STATE for a torque-driven rotor or a caller's inflow
- * plane (the derivative covers prescribed rotation and the synthetic
- * inflow; with sigma_band < 1 it includes the finite-difference strain of
- * the band cells, transposed onto their neighbours' populations).  With the esoteric-twist
+ * hl_step; HL_ERR_STATE for a torque-driven rotor (the derivative covers
+ * prescribed rotation; with sigma_band < 1 it includes the finite-difference
+ * strain of the band cells, transposed onto their neighbours' populations;
+ * a caller's inflow plane is held at its content for the whole sweep).  With the esoteric-twist
  * layout the state is permuted into the AA layout of the same step for the
  * sweep (the two layouts give the same trajectory; the copy lives in
  * d_work) and back at the end, also when the sweep fails. */

@@ -897,8 +897,6 @@ static hl_status grad_check(hl_lattice* lat, int steps, int avg_last, int ckpt_e
     for (int k = 0; k < lat->nrot; ++k)
         if (lat->rot[k].driven)
             return fail(lat, HL_ERR_STATE, "hl_grad: gradients cover prescribed rotation only (rotor is torque-driven)");
-    if (lat->inflow)
-        return fail(lat, HL_ERR_STATE, "hl_grad: the recompute cannot replay a caller's inflow planes (synthetic inflow only)");
     if (bytes < grad_layout(lat, steps, ckpt_every).total)
         return fail(lat, HL_ERR_WORKSPACE, "hl_grad: workspace too small");
     return HL_OK;
