@@ -422,6 +422,15 @@ template <int NS>
 __device__ __forceinline__ Dual<NS> operator/(const Dual<NS>& x, const Dual<NS>& y) {
     Dual<NS> r;
     r.v = x.v / y.v;
+    if (isinf(y.v) && isfinite(x.v)) {
+        // a finite value over an infinite one is 0 in a whole neighbourhood
+        // (the Newton step of a wall-function solve whose exponential
+        // overflowed for a collapsed start value): zero derivatives, where
+        // the quotient rule would give 0 * inf
+#pragma unroll
+        for (int k = 0; k < NS; ++k) r.d[k] = 0.0;
+        return r;
+    }
     const double ry = 1.0 / y.v;
 #pragma unroll
     for (int k = 0; k < NS; ++k) r.d[k] = (x.d[k] - r.v * y.d[k]) * ry;

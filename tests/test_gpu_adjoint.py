@@ -385,3 +385,55 @@ def test_gradient_with_held_caller_inflow_plane(P):
     assert abs(gps[0] - fd) <= 1e-2 * abs(fd)
     print("synthetic-inflow sweep dJ/dpitch", gpr[0])
     assert abs(gpr[0] - fd) > 3e-2 * abs(fd)
+
+
+def test_gradient_parity_two_rotors(P):
+    """Two rotors in tandem with their own objective weights (the second in
+    the first's wake, other tip-speed ratio, phase and pitch): J, dJ/dpitch
+    of each rotor and dJ/dd0 against the oracle's adjoint."""
+    from workloads.configs import RotorSpec, Workload
+    wl = Workload("two48", 48, 48, 128, turbulence=0.05,
+                  rotors=[RotorSpec(center=(23.5, 23.5, 32.0), radius=10.0, tsr=6.0),
+                          RotorSpec(center=(23.5, 23.5, 88.0), radius=10.0, tsr=5.0, phase0=0.7, pitch=0.05)])
+    T, navg = 16, 8
+    wT, wQ = [1.0, 0.5], [-0.3, 0.2]
+    lat = P.Lattice.from_workload(wl)
+    Jg, gpg, gdg = lat.grad(T, navg, wT, wQ, ckpt_every=5)
+    gdg = gdg.cpu().numpy().astype(np.float64)
+    o = O.from_workload(wl)
+    Jo, gpo, gdo = o.adjoint(T, navg, wT, wQ)
+    print(f"two rotors: J {Jg:.8e} vs {Jo:.8e}; dJ/dpitch {list(gpg)} vs {list(gpo)}; "
+          f"dJ/dd0 rel L2 {_rel_l2(gdg, gdo):.2e}")
+    assert abs(Jg - Jo) <= 1e-5 * abs(Jo)
+    for k in range(2):
+        assert abs(gpg[k] - gpo[k]) <= 1e-4 * abs(gpo[k]), k
+    assert _rel_l2(gdg, gdo) <= 1e-4
+
+
+def test_gradient_through_a_collapsed_friction_velocity(P):
+    """A hub wall cell of the off-centre second rotor carries a friction
+    velocity of ~4e-7 from step to step (warm starts; |u_t| ~ 6e-4 near the
+    axis), so u+ ~ 1700: exp(kappa u+) ~ 1e304 and the Newton derivative f'
+    overflows to -inf, and the step is 0; its dual-number derivative must be
+    0 too (the quotient rule gave 0 * inf = NaN and poisoned the whole
+    gradient).  Gradients
+    are finite and match the oracle (complex division by an infinite value
+    also gives 0): pitch to 1e-4, dJ/dd0 to the 1e-3 gradient tolerance
+    (observed 7.5e-4: the cells around the collapsed one carry it, the
+    rest agree to 2e-4)."""
+    from workloads.configs import RotorSpec, Workload
+    wl = Workload("hub48", 48, 48, 128, turbulence=0.05,
+                  rotors=[RotorSpec(center=(23.5, 23.5, 32.0), radius=10.0, tsr=6.0),
+                          RotorSpec(center=(24.0, 23.0, 88.0), radius=10.0, tsr=5.0, phase0=0.7, pitch=0.05)])
+    T, navg = 16, 8
+    wT, wQ = [1.0, 0.5], [-0.3, 0.2]
+    lat = P.Lattice.from_workload(wl)
+    Jg, gpg, gdg = lat.grad(T, navg, wT, wQ, ckpt_every=5)
+    gdg = gdg.cpu().numpy().astype(np.float64)
+    assert np.isfinite(gpg).all() and np.isfinite(gdg).all()
+    o = O.from_workload(wl)
+    Jo, gpo, gdo = o.adjoint(T, navg, wT, wQ)
+    print(f"collapsed u_tau: dJ/dpitch {list(gpg)} vs {list(gpo)}; dJ/dd0 rel L2 {_rel_l2(gdg, gdo):.2e}")
+    for k in range(2):
+        assert abs(gpg[k] - gpo[k]) <= 1e-4 * abs(gpo[k]), k
+    assert _rel_l2(gdg, gdo) <= 1e-3
