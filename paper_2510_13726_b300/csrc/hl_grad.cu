@@ -408,7 +408,15 @@ __global__ void __launch_bounds__(128) adj_wall_kernel(const StepArgs a, const A
     int count = *((volatile int*)(R.count + 1));
     if ((long long)count > R.box_cells) count = (int)R.box_cells;
     const long long N = a.N, BC = R.box_cells;
-    for (int idx = list_first(); idx < count; idx += list_stride()) {
+    // four lanes per wall cell: corners m = sub and sub + 4 are gathered and
+    // scattered by lane sub, and lanes 0, 1, 2 (3 repeats 0) carry the
+    // derivative of the Newton solve along seed 0, 1, 2; each group of four
+    // takes the same list entries, so its branches are uniform
+    const int sub = threadIdx.x & 3;
+    const unsigned gm = 0xfu << (threadIdx.x & 28);
+    const int gbase = threadIdx.x & 28;
+    for (int idx = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 2); idx < count;
+         idx += (int)((gridDim.x * blockDim.x) >> 2)) {
         const long long bi = R.wlist[idx];
         const float phi = R.wphi[idx];
         const int which = R.wwhich[idx];
@@ -438,33 +446,47 @@ __global__ void __launch_bounds__(128) adj_wall_kernel(const StepArgs a, const A
                 if (i0[k] > a.n[k] - 2) { i0[k] = a.n[k] - 2; t[k] = 1.f; clamped[k] = true; }
             }
         }
-        R.gut_prev[bi] = 0.0;
+        if (sub == 0) R.gut_prev[bi] = 0.0;
         bool inside = true;
 #pragma unroll
         for (int k = 0; k < 3; ++k)
             inside = inside && i0[k] - R.lo[k] >= 0 && i0[k] + 1 - R.lo[k] < R.n[k];
         if (!inside) continue;   // the forward left this cell unmodelled (error word set)
-        int cidx[8];
-        float uc[8][3], irho[8];
-        float us[3] = {0.f, 0.f, 0.f};
-        for (int m = 0; m < 8; ++m) {
+        // this lane's corners h = 0, 1: m = sub + 4 h
+        int cidx[2];
+        float uc[2][3], irho[2], wc[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int m = sub + 4 * h;
             const int cx = m & 1, cy = (m >> 1) & 1, cz = m >> 2;
             int p[3] = {i0[0] + cx, i0[1] + cy, i0[2] + cz};
 #pragma unroll
             for (int k = 0; k < 3; ++k)
                 if (!(a.open && k == a.flow_axis)) p[k] = ((p[k] % a.n[k]) + a.n[k]) % a.n[k];
             const int c = (p[2] * a.n[1] + p[1]) * a.n[0] + p[0];
-            cidx[m] = c;
+            cidx[h] = c;
             Offs o;
             make_offs(a, p[0], p[1], p[2], o);
             float g[Q];
             load_pre<Q, S, PH>(a, c, o, g);
             float drho, jj[3];
             moments01<Q>(g, drho, jj);
-            irho[m] = 1.0f / (1.0f + drho);
-            uc[m][0] = jj[0] * irho[m]; uc[m][1] = jj[1] * irho[m]; uc[m][2] = jj[2] * irho[m];
+            irho[h] = 1.0f / (1.0f + drho);
+            uc[h][0] = jj[0] * irho[h]; uc[h][1] = jj[1] * irho[h]; uc[h][2] = jj[2] * irho[h];
             const float wgt = (cx ? t[0] : 1.f - t[0]) * (cy ? t[1] : 1.f - t[1]) * (cz ? t[2] : 1.f - t[2]);
-            us[0] += wgt * uc[m][0]; us[1] += wgt * uc[m][1]; us[2] += wgt * uc[m][2];
+            wc[h] = wgt;
+        }
+        // the trilinear sum in corner order 0..7 with the forward wall model's
+        // expression, so that the replayed Newton starts from the same |u_t|
+        float us[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            const int h = m >> 2, src = gbase + (m & 3);
+            const float wgt = __shfl_sync(gm, h ? wc[1] : wc[0], src);
+            const float u0 = __shfl_sync(gm, h ? uc[1][0] : uc[0][0], src);
+            const float u1 = __shfl_sync(gm, h ? uc[1][1] : uc[0][1], src);
+            const float u2 = __shfl_sync(gm, h ? uc[1][2] : uc[0][2], src);
+            us[0] += wgt * u0; us[1] += wgt * u1; us[2] += wgt * u2;
         }
         float usol[3];
         solid_vel(R, (float)x, (float)y, (float)z, usol);
@@ -478,15 +500,20 @@ __global__ void __launch_bounds__(128) adj_wall_kernel(const StepArgs a, const A
         const double ysamp = (double)y1 + (double)ys;
         const bool warm = R.tape_active[bi] != 0;
         const WallFn W = make_wallfn(a.wmE, a.wmK, a.nu, a.wmTol, a.wmMaxit);
-        // seeds: 0 = |u_t|, 1 = y_sample, 2 = Newton start value
-        Dual<3> guess;
+        // seeds: 0 = |u_t|, 1 = y_sample, 2 = Newton start value, one per lane
+        const int seed = sub == 3 ? 0 : sub;
+        Dual<1> guess;
         if (warm) {
-            guess = dual_seed<3>(R.tape_utau[bi], 2);
+            guess = seed == 2 ? dual_seed<1>(R.tape_utau[bi], 0) : dual_const<1>(R.tape_utau[bi]);
         } else {
             const double g0 = sqrt(a.nu * (double)utm / (double)ys);
-            guess = dual_seed<3>(g0, 0, a.nu / ((double)ys * 2.0 * g0));
+            guess = seed == 0 ? dual_seed<1>(g0, 0, a.nu / ((double)ys * 2.0 * g0)) : dual_const<1>(g0);
         }
-        const Dual<3> utau = wall_newton_t(dual_seed<3>((double)utm, 0), dual_seed<3>(ysamp, 1), guess, W);
+        const Dual<1> utau = wall_newton_t(seed == 0 ? dual_seed<1>((double)utm, 0) : dual_const<1>((double)utm),
+                                           seed == 1 ? dual_seed<1>(ysamp, 0) : dual_const<1>(ysamp), guess, W);
+        double utd[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) utd[q] = __shfl_sync(gm, utau.d[0], gbase + q);
         const double y1p = (double)y1 * utau.v * W.inv_nu;
         const Dual<1> up = spalding_uplus_t(dual_seed<1>(y1p, 0), W);
         const float uw = (float)(utau.v * up.v);
@@ -519,9 +546,9 @@ __global__ void __launch_bounds__(128) adj_wall_kernel(const StepArgs a, const A
         utaub += y1pb * (double)y1 * W.inv_nu;
         double y1b = y1pb * utau.v * W.inv_nu;
         // utau = Newton(|u_t|, y1 + y_s, start)
-        utmb += (float)(utaub * utau.d[0]);
-        y1b += utaub * utau.d[1];
-        R.gut_prev[bi] = warm ? utaub * utau.d[2] : 0.0;
+        utmb += (float)(utaub * utd[0]);
+        y1b += utaub * utd[1];
+        if (sub == 0) R.gut_prev[bi] = warm ? utaub * utd[2] : 0.0;
         // th = u_t / |u_t|
         const float td = thb[0] * th[0] + thb[1] * th[1] + thb[2] * th[2];
         float utb[3];
@@ -537,19 +564,21 @@ __global__ void __launch_bounds__(128) adj_wall_kernel(const StepArgs a, const A
         }
         // u_s = sum_m w_m u_m (trilinear at x_s = x + y_s n)
         float xsb[3] = {0.f, 0.f, 0.f};
-        for (int m = 0; m < 8; ++m) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int m = sub + 4 * h;
             const int cx = m & 1, cy = (m >> 1) & 1, cz = m >> 2;
             const float wx = cx ? t[0] : 1.f - t[0], wy = cy ? t[1] : 1.f - t[1], wz = cz ? t[2] : 1.f - t[2];
             const float wgt = wx * wy * wz;
             const float ucb[3] = {wgt * urb[0], wgt * urb[1], wgt * urb[2]};
-            const float dot = uc[m][0] * urb[0] + uc[m][1] * urb[1] + uc[m][2] * urb[2];
+            const float dot = uc[h][0] * urb[0] + uc[h][1] * urb[1] + uc[h][2] * urb[2];
             if (!clamped[0]) xsb[0] += (cx ? 1.f : -1.f) * wy * wz * dot;
             if (!clamped[1]) xsb[1] += (cy ? 1.f : -1.f) * wx * wz * dot;
             if (!clamped[2]) xsb[2] += (cz ? 1.f : -1.f) * wx * wy * dot;
             // u_m = j_m / rho_m: d u_m / d g_s = (c_s - u_m) / rho_m
-            const float ir = irho[m];
-            const float cu = (ucb[0] * uc[m][0] + ucb[1] * uc[m][1] + ucb[2] * uc[m][2]) * ir;
-            float* lp = j.lam + cidx[m];
+            const float ir = irho[h];
+            const float cu = (ucb[0] * uc[h][0] + ucb[1] * uc[h][1] + ucb[2] * uc[h][2]) * ir;
+            float* lp = j.lam + cidx[h];
 #pragma unroll
             for (int s = 0; s < Q; ++s) {
                 const int sx = cslot(Q, s, 0), sy = cslot(Q, s, 1), sz = cslot(Q, s, 2);
@@ -558,11 +587,15 @@ __global__ void __launch_bounds__(128) adj_wall_kernel(const StepArgs a, const A
             }
         }
 #pragma unroll
-        for (int k = 0; k < 3; ++k) nb[k] += ys * xsb[k];
+        for (int k = 0; k < 3; ++k) {
+            xsb[k] += __shfl_xor_sync(gm, xsb[k], 1);
+            xsb[k] += __shfl_xor_sync(gm, xsb[k], 2);
+            nb[k] += ys * xsb[k];
+        }
         // pitch: through the normal and the wall distance y1 = max(phi, 1/2)
         double pg = (double)(nb[0] * dn[0] + nb[1] * dn[1] + nb[2] * dn[2]);
         if (far) pg += y1b * (double)dphi;
-        atomicAdd(R.pacc + (unsigned)idx % PACC_SLOTS, pg);
+        if (sub == 0) atomicAdd(R.pacc + (unsigned)idx % PACC_SLOTS, pg);
     }
 }
 
