@@ -856,18 +856,14 @@ hl_status small_save(hl_lattice* lat, char* sm, long long t, cudaStream_t bs) {
     return HL_OK;
 }
 
-// the wall-model output of a step, saved after the step's wall model ran
-// (box stream) or put back for the step's reverse pass
-hl_status wm_copy(hl_lattice* lat, char* sm, bool save, cudaStream_t bs) {
-    const cudaMemcpyKind kd = cudaMemcpyDeviceToDevice;
+// the wall-model rows of a step (u^B and S^WM of wall cells, S^FD of hybrid
+// band cells) live in the step's tape entry: the recompute's wall model and
+// band strain write them there and its box collision reads them there, and
+// the reverse step reads them in place (no copies)
+void wm_rows_in_tape(hl_lattice* lat, StepArgs& a, char* sm) {
     SmallOff so;
     small_layout(lat, &so);
-    for (int k = 0; k < lat->nrot; ++k) {
-        RotorDev& D = lat->rot[k].dev;
-        const size_t b = sizeof(float) * 9 * D.box_cells;
-        HL_CUDA(lat, save ? cudaMemcpyAsync(sm + so.wm[k], D.wm, b, kd, bs) : cudaMemcpyAsync(D.wm, sm + so.wm[k], b, kd, bs));
-    }
-    return HL_OK;
+    for (int k = 0; k < lat->nrot; ++k) a.rot[k].wm = reinterpret_cast<float*>(sm + so.wm[k]);
 }
 
 // arguments of step t with explicit read / write population buffers
@@ -1048,11 +1044,13 @@ static hl_status grad_aa(hl_lattice* lat, int steps, int avg_last, int ckpt_ever
             if ((rc = small_save(lat, sm, t, bs)) != HL_OK) return rc;
             if (jj < L - 1) {
                 StepArgs a = args_at(lat, t, buf(jj), buf(jj + 1));
+                if (tape_wm) wm_rows_in_tape(lat, a, sm);
                 if ((rc = issue_step(lat, a, false)) != HL_OK) return rc;
             } else if (lat->nrot > 0) {
                 // the segment's last state is not advanced: run its embedding and
                 // wall model alone
                 StepArgs a = args_at(lat, t, buf(jj), buf(jj));
+                if (tape_wm) wm_rows_in_tape(lat, a, sm);
                 a.part = 0;
                 HL_CUDA(lat, launch_band(Q, S, a, bs));
                 HL_CUDA(lat, launch_band_strain(Q, S, a, bs));
@@ -1060,7 +1058,6 @@ static hl_status grad_aa(hl_lattice* lat, int steps, int avg_last, int ckpt_ever
                 for (int k = 0; k < lat->nrot; ++k)
                     HL_CUDA(lat, cudaMemsetAsync(lat->rot[k].dev.count, 0, 2 * sizeof(int), bs));
             }
-            if (lat->nrot > 0 && tape_wm && (rc = wm_copy(lat, sm, true, bs)) != HL_OK) return rc;
         }
         // both halves of the reverse step read states written by both halves
         // of the recomputation
@@ -1093,8 +1090,8 @@ static hl_status grad_aa(hl_lattice* lat, int steps, int avg_last, int ckpt_ever
             if (two) HL_CUDA(lat, cudaEventRecord(ev_bulk[p], st));
             // box stream: forward quantities of step t, then the box adjoint
             if (lat->nrot > 0) {
-                // the step's wall-model output from the tape (the linearisation point)
-                if (tape_wm && (rc = wm_copy(lat, sm, false, bs)) != HL_OK) return rc;
+                // the step's wall-model output is read from the tape (the linearisation point)
+                if (tape_wm) wm_rows_in_tape(lat, a, sm);
                 SmallOff so;
                 small_layout(lat, &so);
                 for (int k = 0; k < lat->nrot; ++k) {
