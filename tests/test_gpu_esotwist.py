@@ -117,8 +117,8 @@ def test_snapshot_resume(P):
     assert torch.equal(u1, lat.fields()[1])
 
 
-@pytest.mark.parametrize("start,storage", [(4, "f32"), (5, "f32"), (5, "bf16s")])
-def test_gradient_matches_aa(P, start, storage):
+@pytest.mark.parametrize("start,storage,q", [(4, "f32", 19), (5, "f32", 19), (5, "bf16s", 19), (5, "f32", 27)])
+def test_gradient_matches_aa(P, start, storage, q):
     """hl_grad on an esoteric-twist lattice (state permuted into the AA layout
     of the same step for the sweep and back) gives the AA lattice's objective
     and gradients, and leaves the lattice where hl_step would: the interior
@@ -127,7 +127,7 @@ def test_gradient_matches_aa(P, start, storage):
     step parities at entry and exit; one cell per thread (nx odd), so both
     layouts run the same arithmetic."""
     import torch
-    wl = Workload("odd47", 47, 48, 96, turbulence=0.05, rotors=_single(47, 48, 96, 12.0, 6.0))
+    wl = Workload("odd47", 47, 48, 96, q=q, turbulence=0.05, rotors=_single(47, 48, 96, 12.0, 6.0))
     out = []
     for layout in ("aa", "esotwist"):
         lat = P.Lattice.from_workload(wl, layout=layout, storage=storage)

@@ -107,8 +107,8 @@ def test_overlap_schedule_bit_identical_with_hybrid_band(P):
     assert np.allclose(Fa, Fb, rtol=1e-12, atol=0)
 
 
-@pytest.mark.parametrize("wall_model", [False, True])
-def test_gradient_parity_with_oracle(P, wall_model):
+@pytest.mark.parametrize("wall_model,q", [(False, 19), (True, 19), (False, 27)])
+def test_gradient_parity_with_oracle(P, wall_model, q):
     """hl_grad with sigma = 0.5 (the box adjoint hands the strain sensitivity
     of the hybrid band cells to adj_band_strain_kernel, which passes it to
     the neighbours' populations) against the oracle's adjoint: J, dJ/dpitch
@@ -117,6 +117,7 @@ def test_gradient_parity_with_oracle(P, wall_model):
     it."""
     import torch
     wl = W.workload("rotor48_adj")
+    wl.q = q
     T, navg, wT, wQ = 16, 8, 1.0, -0.3
     lat = P.Lattice.from_workload(wl, wall_model=wall_model, sigma_band=0.5)
     Jg, gpg, gdg = lat.grad(T, navg, [wT], [wQ], ckpt_every=5)
