@@ -482,7 +482,15 @@ __global__ void __launch_bounds__(128) wall_kernel(const StepArgs a) {
     const RotorDev& R = a.rot[blockIdx.y];
     int count = *((volatile int*)(R.count + 1));
     if ((long long)count > R.box_cells) count = (int)R.box_cells;
-    for (int idx = list_first(); idx < count; idx += list_stride()) {
+    // four lanes per wall cell: lane sub gathers the velocities of sample
+    // corners sub and sub + 4; every lane of the group then runs the same
+    // Newton solve and lane 0 stores the result (the group takes the same
+    // list entries, so its branches are uniform)
+    const int sub = threadIdx.x & 3;
+    const unsigned gm = 0xfu << (threadIdx.x & 28);
+    const int gbase = threadIdx.x & 28;
+    for (int idx = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 2); idx < count;
+         idx += (int)((gridDim.x * blockDim.x) >> 2)) {
         const long long bi = R.wlist[idx];
         const float phi = R.wphi[idx];
         const int which = R.wwhich[idx];
@@ -517,26 +525,38 @@ __global__ void __launch_bounds__(128) wall_kernel(const StepArgs a) {
         const long long B = R.box_cells;
         float* wm = R.wm + bi;
         if (!inside) {
-            atomicOr(a.err, ERR_GEOMETRY);
+            if (sub == 0) {
+                atomicOr(a.err, ERR_GEOMETRY);
 #pragma unroll
-            for (int k = 0; k < 9; ++k) wm[k * B] = 0.f;
-            R.active[bi] = 0;
-            R.utau[bi] = 0.0;
+                for (int k = 0; k < 9; ++k) wm[k * B] = 0.f;
+                R.active[bi] = 0;
+                R.utau[bi] = 0.0;
+            }
             continue;
         }
-        float us[3] = {0.f, 0.f, 0.f};
-        for (int cz = 0; cz < 2; ++cz)
-            for (int cy = 0; cy < 2; ++cy)
-                for (int cx = 0; cx < 2; ++cx) {
-                    int p[3] = {i0[0] + cx, i0[1] + cy, i0[2] + cz};
+        float wc[2], uc[2][3];
 #pragma unroll
-                    for (int k = 0; k < 3; ++k)
-                        if (!(a.open && k == a.flow_axis)) p[k] = ((p[k] % a.n[k]) + a.n[k]) % a.n[k];
-                    const float wgt = (cx ? t[0] : 1.f - t[0]) * (cy ? t[1] : 1.f - t[1]) * (cz ? t[2] : 1.f - t[2]);
-                    float uc[3];
-                    cell_velocity<Q, S, PH>(a, p[0], p[1], p[2], uc);
-                    us[0] += wgt * uc[0]; us[1] += wgt * uc[1]; us[2] += wgt * uc[2];
-                }
+        for (int h = 0; h < 2; ++h) {
+            const int m = sub + 4 * h;
+            const int cx = m & 1, cy = (m >> 1) & 1, cz = m >> 2;
+            int p[3] = {i0[0] + cx, i0[1] + cy, i0[2] + cz};
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                if (!(a.open && k == a.flow_axis)) p[k] = ((p[k] % a.n[k]) + a.n[k]) % a.n[k];
+            wc[h] = (cx ? t[0] : 1.f - t[0]) * (cy ? t[1] : 1.f - t[1]) * (cz ? t[2] : 1.f - t[2]);
+            cell_velocity<Q, S, PH>(a, p[0], p[1], p[2], uc[h]);
+        }
+        // the trilinear sum in corner order 0..7 (m = cx + 2 cy + 4 cz)
+        float us[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            const int h = m >> 2, src = gbase + (m & 3);
+            const float wgt = __shfl_sync(gm, h ? wc[1] : wc[0], src);
+            const float u0 = __shfl_sync(gm, h ? uc[1][0] : uc[0][0], src);
+            const float u1 = __shfl_sync(gm, h ? uc[1][1] : uc[0][1], src);
+            const float u2 = __shfl_sync(gm, h ? uc[1][2] : uc[0][2], src);
+            us[0] += wgt * u0; us[1] += wgt * u1; us[2] += wgt * u2;
+        }
         float usol[3];
         solid_velocity(R, x, y, z, usol);
         const float ur[3] = {us[0] - usol[0], us[1] - usol[1], us[2] - usol[2]};
@@ -544,21 +564,27 @@ __global__ void __launch_bounds__(128) wall_kernel(const StepArgs a) {
         const float ut[3] = {ur[0] - un * n[0], ur[1] - un * n[1], ur[2] - un * n[2]};
         const float utm = sqrtf(ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2]);
         if (!(utm >= 1e-12f)) {
+            if (sub == 0) {
 #pragma unroll
-            for (int k = 0; k < 9; ++k) wm[k * B] = 0.f;
-            R.active[bi] = 0;
-            R.utau[bi] = 0.0;
+                for (int k = 0; k < 9; ++k) wm[k * B] = 0.f;
+                R.active[bi] = 0;
+                R.utau[bi] = 0.0;
+            }
             continue;
         }
         const float th[3] = {ut[0] / utm, ut[1] / utm, ut[2] / utm};
         const double ysamp = (double)y1 + (double)a.wmYs;
         // Eq. (guess): previous value if the wall function was active last step
-        const double guess = R.active[bi] ? R.utau[bi] : sqrt(a.nu * (double)utm / (double)a.wmYs);
+        // (read by lane 0, which alone writes the new value below)
+        double guess = 0.0;
+        if (sub == 0) guess = R.active[bi] ? R.utau[bi] : sqrt(a.nu * (double)utm / (double)a.wmYs);
+        guess = __shfl_sync(gm, guess, gbase);
         const WallFn W = make_wallfn(a.wmE, a.wmK, a.nu, a.wmTol, a.wmMaxit);
         const double utau = wall_newton_t<double>((double)utm, ysamp, guess, W);
         const double up = spalding_uplus_t<double>((double)y1 * utau * W.inv_nu, W);
         const float uw = (float)(utau * up);
         const float gs = (float)(0.5 * ((double)utm - utau * up) / (double)a.wmYs);
+        if (sub != 0) continue;
         wm[0] = uw * th[0];
         wm[B] = uw * th[1];
         wm[2 * B] = uw * th[2];
