@@ -672,7 +672,7 @@ cudaError_t launch_adj_box_t(const StepArgs& a, const AdjArgs& j, bool force_on,
         }
     }
     if (a.nrot > 0 && a.wall_model) {
-        const dim3 grd(WALL_BLOCKS, a.nrot);
+        const dim3 grd(WALL_GROUP_BLOCKS, a.nrot);
         if (a.phase == 0) adj_wall_kernel<Q, S, 0><<<grd, WALL_THREADS, 0, s>>>(a, j);
         else adj_wall_kernel<Q, S, 1><<<grd, WALL_THREADS, 0, s>>>(a, j);
     }

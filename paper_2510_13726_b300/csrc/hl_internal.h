@@ -11,6 +11,9 @@ namespace hl {
 constexpr int FORCE_BLOCKS = 296;    // blocks per rotor in the force reduction (2 x 148 SMs)
 constexpr int WALL_BLOCKS = 148;     // blocks per rotor in the wall model
 constexpr int WALL_THREADS = 128;    // four warps per block
+// the wall-model kernels take four lanes per wall cell: up to 37,888 wall
+// cells per rotor in one pass (blocks whose lanes find no entry exit at once)
+constexpr int WALL_GROUP_BLOCKS = 148 * 8;
 
 // Cell lists (force cells, wall cells): consecutive entries (neighbouring
 // cells) go to consecutive threads, so each warp's gathers share cache lines

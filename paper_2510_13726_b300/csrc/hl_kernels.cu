@@ -973,7 +973,7 @@ static cudaError_t launch_band_t(const StepArgs& a, cudaStream_t s) {
 template <int Q, int S>
 static cudaError_t launch_wall_t(const StepArgs& a, cudaStream_t s) {
     if (a.nrot == 0 || !a.wall_model) return cudaSuccess;
-    const dim3 grd(WALL_BLOCKS, a.nrot);
+    const dim3 grd(WALL_GROUP_BLOCKS, a.nrot);
     if (a.phase == 0) wall_kernel<Q, S, 0><<<grd, WALL_THREADS, 0, s>>>(a);
     else wall_kernel<Q, S, 1><<<grd, WALL_THREADS, 0, s>>>(a);
     return cudaGetLastError();
