@@ -14,6 +14,9 @@ constexpr int WALL_THREADS = 128;    // four warps per block
 // the wall-model kernels take four lanes per wall cell: up to 37,888 wall
 // cells per rotor in one pass (blocks whose lanes find no entry exit at once)
 constexpr int WALL_GROUP_BLOCKS = 148 * 8;
+// rotor boxes up to this many cells take four lanes per wall cell in the
+// forward wall model (the 128x128x256 rotor's box: 0.26M cells; rotor256's: 1.3M)
+constexpr long long WALL_SMALL_BOX = 1LL << 20;
 
 // Cell lists (force cells, wall cells): consecutive entries (neighbouring
 // cells) go to consecutive threads, so each warp's gathers share cache lines

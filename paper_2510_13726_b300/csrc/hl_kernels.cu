@@ -477,20 +477,21 @@ __device__ void cell_velocity(const StepArgs& a, int x, int y, int z, float u[3]
     u[0] = j[0] * inv; u[1] = j[1] * inv; u[2] = j[2] * inv;
 }
 
-template <int Q, int S, int PH>
+template <int Q, int S, int PH, int LN>
 __global__ void __launch_bounds__(128) wall_kernel(const StepArgs a) {
     const RotorDev& R = a.rot[blockIdx.y];
     int count = *((volatile int*)(R.count + 1));
     if ((long long)count > R.box_cells) count = (int)R.box_cells;
-    // four lanes per wall cell: lane sub gathers the velocities of sample
-    // corners sub and sub + 4; every lane of the group then runs the same
-    // Newton solve and lane 0 stores the result (the group takes the same
-    // list entries, so its branches are uniform)
-    const int sub = threadIdx.x & 3;
-    const unsigned gm = 0xfu << (threadIdx.x & 28);
+    // LN lanes per wall cell (1 or 4): lane sub gathers the velocities of the
+    // sample corners m = sub (mod LN); every lane of the group then runs the
+    // same Newton solve and lane 0 stores the result (the group takes the
+    // same list entries, so its branches are uniform)
+    static_assert(LN == 1 || LN == 4, "one or four lanes per wall cell");
+    const int sub = LN == 1 ? 0 : (int)(threadIdx.x & 3);
+    const unsigned gm = LN == 1 ? 0u : 0xfu << (threadIdx.x & 28);
     const int gbase = threadIdx.x & 28;
-    for (int idx = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 2); idx < count;
-         idx += (int)((gridDim.x * blockDim.x) >> 2)) {
+    for (int idx = (int)((blockIdx.x * blockDim.x + threadIdx.x) / LN); idx < count;
+         idx += (int)((gridDim.x * blockDim.x) / LN)) {
         const long long bi = R.wlist[idx];
         const float phi = R.wphi[idx];
         const int which = R.wwhich[idx];
@@ -534,10 +535,11 @@ __global__ void __launch_bounds__(128) wall_kernel(const StepArgs a) {
             }
             continue;
         }
-        float wc[2], uc[2][3];
+        constexpr int NH = 8 / LN;
+        float wc[NH], uc[NH][3];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int m = sub + 4 * h;
+        for (int h = 0; h < NH; ++h) {
+            const int m = sub + LN * h;
             const int cx = m & 1, cy = (m >> 1) & 1, cz = m >> 2;
             int p[3] = {i0[0] + cx, i0[1] + cy, i0[2] + cz};
 #pragma unroll
@@ -550,11 +552,16 @@ __global__ void __launch_bounds__(128) wall_kernel(const StepArgs a) {
         float us[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
-            const int h = m >> 2, src = gbase + (m & 3);
-            const float wgt = __shfl_sync(gm, h ? wc[1] : wc[0], src);
-            const float u0 = __shfl_sync(gm, h ? uc[1][0] : uc[0][0], src);
-            const float u1 = __shfl_sync(gm, h ? uc[1][1] : uc[0][1], src);
-            const float u2 = __shfl_sync(gm, h ? uc[1][2] : uc[0][2], src);
+            float wgt, u0, u1, u2;
+            if constexpr (LN == 1) {
+                wgt = wc[m]; u0 = uc[m][0]; u1 = uc[m][1]; u2 = uc[m][2];
+            } else {
+                const int h = m >> 2, src = gbase + (m & 3);
+                wgt = __shfl_sync(gm, h ? wc[1] : wc[0], src);
+                u0 = __shfl_sync(gm, h ? uc[1][0] : uc[0][0], src);
+                u1 = __shfl_sync(gm, h ? uc[1][1] : uc[0][1], src);
+                u2 = __shfl_sync(gm, h ? uc[1][2] : uc[0][2], src);
+            }
             us[0] += wgt * u0; us[1] += wgt * u1; us[2] += wgt * u2;
         }
         float usol[3];
@@ -578,7 +585,7 @@ __global__ void __launch_bounds__(128) wall_kernel(const StepArgs a) {
         // (read by lane 0, which alone writes the new value below)
         double guess = 0.0;
         if (sub == 0) guess = R.active[bi] ? R.utau[bi] : sqrt(a.nu * (double)utm / (double)a.wmYs);
-        guess = __shfl_sync(gm, guess, gbase);
+        if constexpr (LN > 1) guess = __shfl_sync(gm, guess, gbase);
         const WallFn W = make_wallfn(a.wmE, a.wmK, a.nu, a.wmTol, a.wmMaxit);
         const double utau = wall_newton_t<double>((double)utm, ysamp, guess, W);
         const double up = spalding_uplus_t<double>((double)y1 * utau * W.inv_nu, W);
@@ -973,9 +980,20 @@ static cudaError_t launch_band_t(const StepArgs& a, cudaStream_t s) {
 template <int Q, int S>
 static cudaError_t launch_wall_t(const StepArgs& a, cudaStream_t s) {
     if (a.nrot == 0 || !a.wall_model) return cudaSuccess;
-    const dim3 grd(WALL_GROUP_BLOCKS, a.nrot);
-    if (a.phase == 0) wall_kernel<Q, S, 0><<<grd, WALL_THREADS, 0, s>>>(a);
-    else wall_kernel<Q, S, 1><<<grd, WALL_THREADS, 0, s>>>(a);
+    // small rotor boxes (few wall cells): four lanes per cell, so the corner
+    // gathers of a short list spread over more SMs; large boxes: one lane per
+    // cell (four lanes would repeat each FP64 Newton solve four times)
+    long long box = 0;
+    for (int k = 0; k < a.nrot; ++k) box = a.rot[k].box_cells > box ? a.rot[k].box_cells : box;
+    if (box <= WALL_SMALL_BOX) {
+        const dim3 grd(WALL_GROUP_BLOCKS, a.nrot);
+        if (a.phase == 0) wall_kernel<Q, S, 0, 4><<<grd, WALL_THREADS, 0, s>>>(a);
+        else wall_kernel<Q, S, 1, 4><<<grd, WALL_THREADS, 0, s>>>(a);
+    } else {
+        const dim3 grd(WALL_BLOCKS, a.nrot);
+        if (a.phase == 0) wall_kernel<Q, S, 0, 1><<<grd, WALL_THREADS, 0, s>>>(a);
+        else wall_kernel<Q, S, 1, 1><<<grd, WALL_THREADS, 0, s>>>(a);
+    }
     return cudaGetLastError();
 }
 
