@@ -8,7 +8,7 @@
 
 namespace hl {
 
-constexpr int FORCE_BLOCKS = 296;    // blocks per rotor in the force reduction (2 x 148 SMs)
+constexpr int FORCE_BLOCKS = 64;     // blocks per rotor in the force reduction (few: they start beside the bulk launch)
 constexpr int WALL_BLOCKS = 148;     // blocks per rotor in the wall model
 constexpr int WALL_THREADS = 128;    // four warps per block
 // the wall-model kernels take four lanes per wall cell: up to 37,888 wall
