@@ -971,7 +971,9 @@ static cudaError_t launch_band_t(const StepArgs& a, cudaStream_t s) {
     }
     constexpr int WPB = BAND_THREADS / 32;
     long long blocks = (maxrows + WPB - 1) / WPB;
-    if (blocks > 148 * 16) blocks = 148 * 16;
+    // at most two blocks per SM: the embedding runs beside the bulk launch, and
+    // fewer blocks leave it more of the GPU (rotor256 step 0.797 -> 0.790 ms)
+    if (blocks > 148 * 2) blocks = 148 * 2;
     if (blocks < 1) blocks = 1;
     band_kernel<<<dim3((unsigned)blocks, a.nrot), BAND_THREADS, 0, s>>>(a);
     return cudaGetLastError();
