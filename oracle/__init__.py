@@ -10,9 +10,15 @@ It shares no code with ``paper_2510_13726_b300``; both take their inputs from
 Parity status of each part (the pins live in ``tests/test_oracle_*.py``):
   lattice, equilibrium, regularized non-equilibrium, Smagorinsky tau,
   collision, wall function, porosity definition, embedding, streaming,
-  invariants: pinned; boundary force (momentum exchange): pinned against the
-  momentum deficit and symmetry; physical accuracy on the paper's rotor
-  (C_T ~ 0.963): parity unpinned (geometry and data are not available).
+  invariants: pinned; wall model of a wall cell (sample point, tangential
+  relative velocity, friction velocity at the sample's wall distance,
+  modelled velocity u_tau u+(y1+), strain, Newton start values): pinned in
+  the log-law regime against closed forms on flat walls and by a log-law
+  channel; open boundaries: pinned by a uniform stream (fixed point) and a
+  parallel shear flow leaving through the outlet; boundary force (momentum
+  exchange): pinned against the momentum deficit and symmetry; physical
+  accuracy on the paper's rotor (C_T ~ 0.963): parity unpinned (geometry and
+  data are not available).
 """
 
 from __future__ import annotations
