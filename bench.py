@@ -10,9 +10,12 @@ every 100 steps.  Workload: the 256x256x512 D3Q19 rotor (FP32 populations,
 single-buffer AA pattern, R = 64 NACA 4412 three-bladed rotor at TSR 6,
 5 % synthetic turbulent inflow).  Prints one JSON line (rank 0).
 
-Under torchrun (N > 1) every rank advances its own replica of the workload
-on its own GPU (the path has no exchange step in this configuration); the
-timed region is bracketed by barriers and the max over ranks is reported.
+Under torchrun (N > 1) the lattice is decomposed along the flow axis (the
+paper's weak scaling, one rotor per GPU): a row of N rotor256 domains,
+256x256x(512 N) cells with a rotor every 512 planes, one slab of 512 planes
+per rank; every odd step exchanges the halo planes between neighbouring
+ranks (NCCL point-to-point) and the per-rotor loads are reduced.  The timed
+region is bracketed by barriers and the max over ranks is reported.
 """
 
 from __future__ import annotations
@@ -40,7 +43,7 @@ WORKLOAD_DESC = ("rotor256: 256x256x512 cells (33.5M), D3Q19, FP32 weight-shifte
 
 
 # --------------------------------------------------------------------------
-# distributed helpers (replicas; barrier + max over ranks)
+# distributed helpers (barrier + max over ranks)
 # --------------------------------------------------------------------------
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -243,6 +246,99 @@ def measured_peaks():
     return 6400.0, "fallback"
 
 
+def chain_workload(base, n):
+    """A row of n copies of a workload along its flow axis z (rotor k at the
+    base rotor's position plus k lengths): the weak-scaling lattice."""
+    import dataclasses
+    from workloads.configs import RotorSpec
+    rot = [dataclasses.replace(r, center=(r.center[0], r.center[1], r.center[2] + k * base.nz))
+           for k in range(n) for r in base.rotors]
+    return dataclasses.replace(base, nz=base.nz * n, rotors=rot, name=f"{base.name}_row{n}",
+                               note=f"{n} x {base.name} along the flow axis, one slab per rank")
+
+
+def run_cuda_slabs(args, world, rank, local, dev):
+    """N > 1: one slab of the rotor row per rank, halo exchange every odd step."""
+    import torch
+    import torch.distributed as dist
+    import workloads as W
+    from paper_2510_13726_b300.slabs import SlabDomain
+
+    base = W.workload(args.workload)
+    if base.flow_axis != 2:
+        raise SystemExit("the multi-GPU run decomposes along z: choose a workload that flows along z")
+    wl = chain_workload(base, world)
+    cuts = [k * base.nz for k in range(world + 1)]
+    dom = SlabDomain.from_workload(wl, cuts=cuts, held=[rank], rank_of=list(range(world)),
+                                   group=dist.group.WORLD, storage=args.storage, device=dev)
+    lat = dom.engines[rank]
+    K, Wm = args.steps, args.warmup
+    dom.step(Wm)
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    lat.profile_begin(4 * K + 16)
+    e0.record(lat.stream)
+    dom.step(K)
+    e1.record(lat.stream)
+    e1.synchronize()
+    prof = lat.profile_end()
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    barrier()
+    elapsed = e0.elapsed_time(e1) / 1e3
+    cells_rank = wl.nx * wl.ny * (cuts[rank + 1] - cuts[rank])
+    value, t_max = aggregate(elapsed, cells_rank, K, world, device=dev)
+    # end to end: every step the inlet slab takes the step's inflow plane from
+    # pinned host memory, and every rank reads the reduced loads of every rotor
+    K2 = max(1, min(K, 200))
+    plane = None
+    if rank == 0:
+        host_planes = inflow_planes_pinned(base, lat.t, K2, dev)
+        plane = torch.empty(lat.inflow_plane_shape(), dtype=torch.float32, device=dev)
+        lat.set_inflow_plane(plane)
+    torch.cuda.synchronize(dev)
+    barrier()
+    t0 = time.perf_counter()
+    for i in range(K2):
+        if plane is not None:
+            with torch.cuda.stream(lat.stream):
+                plane.copy_(host_planes[i], non_blocking=True)
+        dom.step(1)
+        F, Fa, M, Ma = dom.loads()
+    t_e2e = time.perf_counter() - t0
+    e2e_value, _ = aggregate(t_e2e, cells_rank, K2, world, device=dev)
+    launches = sum(n for _, n in prof.values())
+    kernels = {k: {"launches": n, "ms_per_launch": round(ms / n, 4) if n else None} for k, (ms, n) in prof.items()}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": Wm, "ms_per_step": round(1e3 * t_max / K, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.storage == "f32" else "f32-math/" + args.storage, "data": "synthetic",
+            "config": {"workload": f"{world} x rotor256 along the flow axis: 256x256x{wl.nz} cells, "
+                                   f"{world} rotors 512 planes apart (one per rank); " + WORKLOAD_DESC,
+                       "name": wl.name, "cells": wl.cells, "cells_per_rank": cells_rank, "q": wl.q,
+                       "storage": args.storage, "layout": "aa",
+                       "parallelism": f"slabs x{world} along z (halo exchange every odd step, NCCL p2p)",
+                       "l2": "no flush: the populations exceed the 126 MB L2"},
+            "kernels_rank0": kernels, "gpu_launches": launches, "clocks": clk,
+            "e2e": {"value": round(e2e_value, 1), "unit": UNIT,
+                    "h2d_bytes_per_step": plane.numel() * 4, "d2h_bytes_per_step": 12 * 8 * len(wl.rotors) * world,
+                    "steps": K2, "per_step": "inflow plane to the inlet slab from pinned host memory, one step "
+                                             "of every slab with its halo exchange, the reduced loads of every "
+                                             "rotor to the host on every rank"},
+            "thrust": [float(v) for v in F[:, 2]],
+            "cpu_baseline": None,
+        }
+        print(json.dumps(line), flush=True)
+    dom.close()
+    return 0
+
+
 def run_cuda(args):
     import torch
     import workloads as W
@@ -253,6 +349,8 @@ def run_cuda(args):
     torch.cuda.set_device(local)
     dist_init("nccl")
     dev = torch.device("cuda", local)
+    if world > 1:
+        return run_cuda_slabs(args, world, rank, local, dev)
 
     wl = W.workload(args.workload)
     lat = Lattice.from_workload(wl, storage=args.storage, layout=args.layout, device=dev)
@@ -366,7 +464,7 @@ def run_cuda(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD_DESC if args.workload == "rotor256" else wl.note,
                        "name": args.workload, "cells": wl.cells, "q": wl.q, "storage": args.storage, "layout": args.layout,
-                       "rotors": len(wl.rotors), "parallelism": f"replicas x{world}",
+                       "rotors": len(wl.rotors), "parallelism": "single GPU",
                        "l2": "no flush: the populations (%.2f GB) exceed the 126 MB L2" %
                              (wl.cells * wl.q * (4 if args.storage == "f32" else 2) / 1e9)},
             "roofline": {"bound": "hbm", "kernel": bulk_kernel_name(wl), "achieved": round(achieved, 1),

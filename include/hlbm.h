@@ -89,6 +89,19 @@ typedef int hl_status;
  *                  a cell reads and writes the links to its +x/+y/+z
  *                  neighbours, the slot of each link alternating with the
  *                  step parity); same results, hl_grad needs 0
+ *  halo_lo, halo_hi  slab of a lattice decomposed along z (the domain
+ *                  decomposition of the paper's multi-GPU runs, Sec. 5): 1
+ *                  makes the plane z = 0 (halo_lo) or z = nz - 1 (halo_hi) a
+ *                  halo plane that stands for the neighbouring slab's
+ *                  boundary plane.  Halo planes are never collided, take no
+ *                  part in the mass total, and their fields are undefined;
+ *                  with flow_axis 2 the open face on that side is absent (the
+ *                  inlet belongs to the first slab, the outlet to the last).
+ *                  Every odd step is bracketed by hl_halo_export /
+ *                  hl_halo_import of each halo face (see there).  Needs
+ *                  layout 0; hl_grad rejects slabs (HL_ERR_STATE).
+ *  z_offset        global z index of local plane 0 (the synthetic inflow is
+ *                  evaluated at global coordinates); 0 for a whole lattice
  */
 typedef struct hl_config {
     int nx, ny, nz;
@@ -108,6 +121,8 @@ typedef struct hl_config {
     double mass_tol;
     int overlap;
     int layout;
+    int halo_lo, halo_hi;
+    int z_offset;
 } hl_config;
 
 /* A rotor: n_blades copies of one blade grid plus a hub sphere (Sec. 3.1).
@@ -200,7 +215,8 @@ hl_status hl_fields(hl_lattice* lat, float* d_rho, float* d_u);
  * d_u[3][N] (either may be NULL: rho = 1, u = 0); resets t to 0. */
 hl_status hl_init_fields(hl_lattice* lat, const float* d_rho, const float* d_u);
 
-/* FP64 total mass sum_x sum_i f_i of the stored populations.  Synchronises. */
+/* FP64 total mass sum_x sum_i f_i of the stored populations (every stored
+ * value converted to FP64 before it is added).  Synchronises. */
 hl_status hl_mass(hl_lattice* lat, double* mass);
 
 /* Number of steps taken since init (or since the loaded state's time). */
@@ -345,6 +361,41 @@ hl_status hl_debug_collide_vjp(int q, int n, const float* d_g_in, const float* d
 hl_status hl_profile_begin(hl_lattice* lat, int capacity);
 hl_status hl_profile_end(hl_lattice* lat, double* ms, long long* launches);
 
+/* ---- slabs: halo exchange of a lattice decomposed along z ----
+ *
+ * In the AA pattern only odd steps move populations between cells.  A slab's
+ * boundary cells then read and write the populations with c_z = -1 (lower
+ * face) or c_z = +1 (upper face) on the adjacent halo plane, 5 slots on D3Q19
+ * and 9 on D3Q27.  Before an odd step the halo plane must hold the
+ * neighbour's values of those slots, and after it the values the slab wrote
+ * there belong to the neighbour.  So around every odd step, for each halo
+ * face, the caller moves one message from each slab to its neighbour:
+ *   t odd (before the step):  hl_halo_export(A, 1) -> hl_halo_import(B, 0) and
+ *                             hl_halo_export(B, 0) -> hl_halo_import(A, 1);
+ *   then the step of every slab;
+ *   t even (after the odd step): the same two exchanges again;
+ * A the slab below B (its upper neighbour; with z periodic the last slab is
+ * below the first).  The library picks the plane and the slot set from the
+ * face and the parity of t.  A message is [nslots][nx * ny] stored values
+ * (storage type, hl_halo_size bytes); the caller carries it (a device copy
+ * on one GPU, a send/receive between ranks).  hl_step on a slab advances one
+ * step per call and returns HL_ERR_STATE if a halo face has not imported at
+ * the current t (t > 0). */
+
+/* Bytes of one halo message of this lattice (HL_ERR_ARG without halo planes). */
+hl_status hl_halo_size(const hl_lattice* lat, size_t* bytes);
+
+/* Copy the outgoing message of face `face` (0 lower, 1 upper; must be a halo
+ * face, HL_ERR_ARG otherwise) into the caller's device buffer d_buf
+ * (hl_halo_size bytes).  Asynchronous on the lattice stream. */
+hl_status hl_halo_export(hl_lattice* lat, int face, void* d_buf);
+
+/* Store the neighbour's message for face `face` (d_buf, device, as written
+ * by the neighbour's hl_halo_export of the opposite face at the same t) and
+ * record that the face is up to date at the current t.  Asynchronous on the
+ * lattice stream: the caller orders it after the neighbour's export. */
+hl_status hl_halo_import(hl_lattice* lat, int face, const void* d_buf);
+
 /* Total mass of a population array, without allocating anything.
  * The paper has no counterpart: this is a service for callers that cannot
  * allocate device memory when they need the total (code inside a memory pool
@@ -363,7 +414,9 @@ hl_status hl_profile_end(hl_lattice* lat, double* ms, long long* launches);
  * address (once per device, with that device current), so make that first
  * call before any stream capture.  All calls share the one array: calls that
  * overlap on the GPU (two streams, or two threads) race and must be ordered
- * by the caller. */
+ * by the caller.  An error still pending on the calling thread from earlier
+ * CUDA work is reported as HL_ERR_CUDA before anything is launched (reading
+ * it clears it, as for any CUDA runtime call). */
 hl_status hl_mass_noalloc(int q, int storage, const void* d_f, long long n_cells, double* d_mass,
                           void* stream);
 

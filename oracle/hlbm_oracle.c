@@ -274,9 +274,19 @@ static double wf_residual(double ut, double u, double y, double nu, double E, do
     return spalding_yplus(u / ut, E, kappa) - y * ut / nu;
 }
 
-static double wf_derivative(double ut, double u, double y, double nu, double E, double kappa)
+/* The Newton step f/f' of Eq. (implicitWF) at u_tau = ut, with numerator and
+   denominator both multiplied by exp(-kappa u+) before the division: the
+   same quotient, but neither factor overflows when the iterate lies far
+   below the root (f and f' both grow like exp(kappa u+); f' leaves the FP64
+   range for kappa u+ above ~700, where the plain quotient would be 0 and
+   the iterate would stop moving).  There the step tends to -ut/(kappa u+). */
+static double wf_step(double ut, double u, double y, double nu, double E, double kappa)
 {
-    return -spalding_dyplus(u / ut, E, kappa) * u / (ut * ut) - y / nu;
+    double up = u / ut, k = kappa * up, s = exp(-k);
+    double P2 = 1.0 + k + 0.5 * k * k, P3 = P2 + k * k * k / 6.0;
+    double fs = (up - y * ut / nu) * s + (1.0 - P3 * s) / E;
+    double fps = -(s + kappa / E * (1.0 - P2 * s)) * up / ut - y / nu * s;
+    return fs / fps;
 }
 
 /* Newton-Raphson for u_tau (Sec. 2.2.1): iterate until the residual changes by
@@ -289,8 +299,7 @@ static double wf_newton(double u, double y, double nu, double guess, double E, d
     double fv = wf_residual(ut, u, y, nu, E, kappa);
     int it = 0;
     while (it < maxit) {
-        double fp = wf_derivative(ut, u, y, nu, E, kappa);
-        double un = ut - fv / fp;
+        double un = ut - wf_step(ut, u, y, nu, E, kappa);
         if (!(un > 0.0)) un = 0.5 * ut;
         double fn = wf_residual(un, u, y, nu, E, kappa);
         ut = un;
@@ -1556,11 +1565,14 @@ static cplx wf_newton_c(cplx u, cplx y, double nu, cplx guess, double E, double 
     cplx fv = spalding_yplus_c(u / ut, E, kappa) - y * ut / nu;
     int it = 0;
     while (it < maxit) {
-        cplx r = u / ut;
-        cplx k = kappa * r;
-        cplx dyp = 1.0 + kappa / E * (cexp(k) - 1.0 - k - 0.5 * k * k);
-        cplx fp = -dyp * u / (ut * ut) - y / nu;
-        cplx un = ut - fv / fp;
+        /* the step of wf_step: f/f' with both scaled by exp(-kappa u+) */
+        cplx up = u / ut;
+        cplx k = kappa * up;
+        cplx sc = cexp(-k);
+        cplx P2 = 1.0 + k + 0.5 * k * k, P3 = P2 + k * k * k / 6.0;
+        cplx fs = (up - y * ut / nu) * sc + (1.0 - P3 * sc) / E;
+        cplx fps = -(sc + kappa / E * (1.0 - P2 * sc)) * up / ut - y / nu * sc;
+        cplx un = ut - fs / fps;
         if (!(creal(un) > 0.0)) un = 0.5 * ut;
         cplx fn = spalding_yplus_c(u / un, E, kappa) - y * un / nu;
         ut = un;

@@ -31,7 +31,7 @@ class HlConfig(C.Structure):
         ("wm_tol", C.c_double), ("wm_maxit", C.c_int),
         ("n_modes", C.c_int), ("modes", _dp),
         ("mass_check_every", C.c_int), ("mass_tol", C.c_double), ("overlap", C.c_int),
-        ("layout", C.c_int),
+        ("layout", C.c_int), ("halo_lo", C.c_int), ("halo_hi", C.c_int), ("z_offset", C.c_int),
     ]
 
 
@@ -90,6 +90,9 @@ SIGNATURES = {
     "hl_profile_begin": (C.c_int, [_vp, C.c_int]),
     "hl_profile_end": (C.c_int, [_vp, _dp, C.POINTER(C.c_longlong)]),
     "hl_mass_noalloc": (C.c_int, [C.c_int, C.c_int, _vp, C.c_longlong, _vp, _vp]),
+    "hl_halo_size": (C.c_int, [_vp, C.POINTER(C.c_size_t)]),
+    "hl_halo_export": (C.c_int, [_vp, C.c_int, _vp]),
+    "hl_halo_import": (C.c_int, [_vp, C.c_int, _vp]),
     "hl_last_error": (C.c_char_p, [_vp]),
     "hl_destroy": (None, [_vp]),
 }

@@ -42,20 +42,33 @@ def gci(f1: float, f2: float, r: float, p: float, fs: float = 1.25) -> float:
 
 
 def study_workload(radius: int, tsr: float = 6.0, u_in: float = 0.05, tau_ref: float = 0.5005,
-                   radius_ref: int = 32):
+                   radius_ref: int = 32, ladder: str = "reynolds"):
     """The synthetic rotor at resolution `radius` (cells per rotor radius):
     lattice 4R x 4R x 8R, rotor a quarter of the length downstream of the
-    inlet, uniform inflow.  Reynolds number and tip-speed ratio are those of
-    the reference resolution: nu scales with R (tau - 1/2 = (tau_ref - 1/2) R / R_ref)."""
+    inlet, uniform inflow, tip-speed ratio `tsr` at every resolution.
+
+    ladder "reynolds": the Reynolds number of the reference resolution at
+    every R (nu scales with R: tau - 1/2 = (tau_ref - 1/2) R / R_ref), so the
+    wall-normal spacing in wall units, and with it the first cell's y+,
+    falls as the grid is refined.  ladder "yplus": the lattice viscosity of
+    the reference (tau = tau_ref) at every R, so y+ of the first cell (its
+    distance in cells times u_tau / nu) stays the same while the Reynolds
+    number U R / nu grows with R: the refinement of a wall-modelled LES,
+    which resolves the outer flow ever finer and models the same inner layer."""
     from workloads.configs import Workload, _single
     n = 4 * radius
-    tau = 0.5 + (tau_ref - 0.5) * radius / radius_ref
-    return Workload(f"convergence_R{radius}", n, n, 2 * n, steps=0, tau_mo=tau, u_in=u_in,
+    if ladder == "reynolds":
+        tau = 0.5 + (tau_ref - 0.5) * radius / radius_ref
+    elif ladder == "yplus":
+        tau = tau_ref
+    else:
+        raise ValueError("ladder is 'reynolds' or 'yplus'")
+    return Workload(f"convergence_R{radius}_{ladder}", n, n, 2 * n, steps=0, tau_mo=tau, u_in=u_in,
                     rotors=_single(n, n, 2 * n, float(radius), tsr))
 
 
 def run_study(radii=(16, 32, 64, 128), revolutions_spinup: float = 3.0, revolutions_avg: float = 2.0,
-              device=None, progress=None, wall_model: bool = True):
+              device=None, progress=None, wall_model: bool = True, ladder: str = "reynolds"):
     """C_T averaged over whole revolutions after a spin-up, at each resolution,
     on the GPU library.  Returns a dict with per-resolution results, the EOC
     against the finest grid and the GCI of the finest grid from the three
@@ -65,7 +78,7 @@ def run_study(radii=(16, 32, 64, 128), revolutions_spinup: float = 3.0, revoluti
     from paper_2510_13726_b300 import Lattice
     rows = []
     for R in radii:
-        wl = study_workload(R)
+        wl = study_workload(R, ladder=ladder)
         om = wl.rotors[0].omega(wl.u_in)
         steps_rev = 2.0 * math.pi / om
         n_spin = int(round(revolutions_spinup * steps_rev))
@@ -82,14 +95,22 @@ def run_study(radii=(16, 32, 64, 128), revolutions_spinup: float = 3.0, revoluti
         _, Fa = lat.forces()
         T = float(Fa[0, wl.flow_axis])
         ms = t0.elapsed_time(t1)
-        rows.append({"R": R, "cells": wl.cells, "tau": wl.tau_mo, "steps": n_spin + n_avg,
-                     "thrust": T, "C_T": thrust_coefficient(T, R, wl.u_in), "seconds": round(ms / 1e3, 2)})
+        band = lat.rotor_band(0)
+        wall = (band["flags"] & 2) > 0
+        ut = band["utau"][wall]
+        nu = (wl.tau_mo - 0.5) / 3.0
+        rows.append({"R": R, "cells": wl.cells, "tau": wl.tau_mo, "Re": wl.u_in * R / nu,
+                     "steps": n_spin + n_avg, "thrust": T, "C_T": thrust_coefficient(T, R, wl.u_in),
+                     # wall units per lattice spacing, u_tau / nu, of the last step: median over the wall
+                     # cells (a wall cell sits 0.5 to 1 spacing from the wall)
+                     "yplus_per_cell_median": float(torch.median(ut / nu).item()) if ut.numel() else None,
+                     "seconds": round(ms / 1e3, 2)})
         if progress:
             progress(rows[-1])
         lat.close()
         del lat
         torch.cuda.empty_cache()
-    out = {"wall_model": bool(wall_model), "resolutions": rows}
+    out = {"wall_model": bool(wall_model), "ladder": ladder, "resolutions": rows}
     ct = [r["C_T"] for r in rows]
     if len(rows) >= 3:
         h = [1.0 / r["R"] for r in rows[:-1]]
@@ -112,8 +133,10 @@ if __name__ == "__main__":
     ap.add_argument("--spinup", type=float, default=3.0, help="revolutions before averaging")
     ap.add_argument("--average", type=float, default=2.0, help="revolutions averaged")
     ap.add_argument("--no-wall-model", action="store_true", help="porous blades without the wall function")
+    ap.add_argument("--ladder", default="reynolds", choices=["reynolds", "yplus"],
+                    help="hold the Reynolds number (reynolds) or the first cell's y+ (yplus) across R")
     args = ap.parse_args()
     radii = tuple(int(v) for v in args.radii.split(","))
-    res = run_study(radii, args.spinup, args.average, wall_model=not args.no_wall_model,
+    res = run_study(radii, args.spinup, args.average, wall_model=not args.no_wall_model, ladder=args.ladder,
                     progress=lambda row: print(json.dumps(row), file=sys.stderr, flush=True))
     print(json.dumps(res))

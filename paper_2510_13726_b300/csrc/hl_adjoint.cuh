@@ -371,25 +371,25 @@ __device__ inline void rotor_normal_tan(const RotorDev& R, int which, int x, int
 }
 
 // ---------------------------------------------------------------------------
-// FP64 forward-mode duals for the two Newton solves of the wall function
+// FP32 forward-mode duals for the two Newton solves of the wall function
 // (wall_newton_t / spalding_uplus_t instantiated on Dual<NS>): the value and
 // its derivatives along NS seeds
 // ---------------------------------------------------------------------------
 template <int NS>
 struct Dual {
-    double v, d[NS];
+    float v, d[NS];
 };
 
 template <int NS>
-__device__ __forceinline__ Dual<NS> dual_const(double v) {
+__device__ __forceinline__ Dual<NS> dual_const(float v) {
     Dual<NS> r;
     r.v = v;
 #pragma unroll
-    for (int k = 0; k < NS; ++k) r.d[k] = 0.0;
+    for (int k = 0; k < NS; ++k) r.d[k] = 0.0f;
     return r;
 }
 template <int NS>
-__device__ __forceinline__ Dual<NS> dual_seed(double v, int k, double dv = 1.0) {
+__device__ __forceinline__ Dual<NS> dual_seed(float v, int k, float dv = 1.0f) {
     Dual<NS> r = dual_const<NS>(v);
     r.d[k] = dv;
     return r;
@@ -428,16 +428,16 @@ __device__ __forceinline__ Dual<NS> operator/(const Dual<NS>& x, const Dual<NS>&
         // overflowed for a collapsed start value): zero derivatives, where
         // the quotient rule would give 0 * inf
 #pragma unroll
-        for (int k = 0; k < NS; ++k) r.d[k] = 0.0;
+        for (int k = 0; k < NS; ++k) r.d[k] = 0.0f;
         return r;
     }
-    const double ry = 1.0 / y.v;
+    const float ry = 1.0f / y.v;
 #pragma unroll
     for (int k = 0; k < NS; ++k) r.d[k] = (x.d[k] - r.v * y.d[k]) * ry;
     return r;
 }
 template <int NS>
-__device__ __forceinline__ Dual<NS> operator*(double s, const Dual<NS>& x) {
+__device__ __forceinline__ Dual<NS> operator*(float s, const Dual<NS>& x) {
     Dual<NS> r;
     r.v = s * x.v;
 #pragma unroll
@@ -445,23 +445,23 @@ __device__ __forceinline__ Dual<NS> operator*(double s, const Dual<NS>& x) {
     return r;
 }
 template <int NS>
-__device__ __forceinline__ Dual<NS> operator*(const Dual<NS>& x, double s) {
+__device__ __forceinline__ Dual<NS> operator*(const Dual<NS>& x, float s) {
     return s * x;
 }
 template <int NS>
-__device__ __forceinline__ Dual<NS> operator+(double s, const Dual<NS>& x) {
+__device__ __forceinline__ Dual<NS> operator+(float s, const Dual<NS>& x) {
     Dual<NS> r = x;
     r.v = s + x.v;
     return r;
 }
 template <int NS>
-__device__ __forceinline__ Dual<NS> operator-(const Dual<NS>& x, double s) {
+__device__ __forceinline__ Dual<NS> operator-(const Dual<NS>& x, float s) {
     Dual<NS> r = x;
     r.v = x.v - s;
     return r;
 }
 template <int NS>
-__device__ __forceinline__ Dual<NS> operator-(double s, const Dual<NS>& x) {
+__device__ __forceinline__ Dual<NS> operator-(float s, const Dual<NS>& x) {
     Dual<NS> r;
     r.v = s - x.v;
 #pragma unroll
@@ -469,13 +469,13 @@ __device__ __forceinline__ Dual<NS> operator-(double s, const Dual<NS>& x) {
     return r;
 }
 template <int NS>
-__device__ __forceinline__ double wf_val(const Dual<NS>& x) {
+__device__ __forceinline__ float wf_val(const Dual<NS>& x) {
     return x.v;
 }
 template <int NS>
 __device__ __forceinline__ Dual<NS> wf_exp(const Dual<NS>& x) {
     Dual<NS> r;
-    r.v = exp(x.v);
+    r.v = expf(x.v);
 #pragma unroll
     for (int k = 0; k < NS; ++k) r.d[k] = r.v * x.d[k];
     return r;
@@ -483,8 +483,8 @@ __device__ __forceinline__ Dual<NS> wf_exp(const Dual<NS>& x) {
 template <int NS>
 __device__ __forceinline__ Dual<NS> wf_log(const Dual<NS>& x) {
     Dual<NS> r;
-    r.v = log(x.v);
-    const double rx = 1.0 / x.v;
+    r.v = logf(x.v);
+    const float rx = 1.0f / x.v;
 #pragma unroll
     for (int k = 0; k < NS; ++k) r.d[k] = x.d[k] * rx;
     return r;
@@ -492,8 +492,8 @@ __device__ __forceinline__ Dual<NS> wf_log(const Dual<NS>& x) {
 template <int NS>
 __device__ __forceinline__ Dual<NS> wf_rcp(const Dual<NS>& x) {
     Dual<NS> r;
-    r.v = 1.0 / x.v;
-    const double m = -r.v * r.v;
+    r.v = 1.0f / x.v;
+    const float m = -r.v * r.v;
 #pragma unroll
     for (int k = 0; k < NS; ++k) r.d[k] = m * x.d[k];
     return r;

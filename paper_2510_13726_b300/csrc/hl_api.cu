@@ -43,6 +43,9 @@ bool valid_config(const hl_config* c) {
     if (c->wm_maxit < 0 || c->wm_maxit > 1000 || !(c->wm_ysample > 0.0)) return false;
     if (c->mass_check_every < 0) return false;
     if (c->layout < 0 || c->layout > 1) return false;
+    if (c->halo_lo < 0 || c->halo_lo > 1 || c->halo_hi < 0 || c->halo_hi > 1 || c->z_offset < 0) return false;
+    if ((c->halo_lo || c->halo_hi) && c->layout != 0) return false;   // slabs use the AA pattern
+    if (c->nz - c->halo_lo - c->halo_hi < 1) return false;
     return true;
 }
 
@@ -109,6 +112,12 @@ StepArgs make_args(const hl_lattice* lat) {
     a.t = lat->t;
     a.flow_axis = c.flow_axis;
     a.open = c.open_boundaries;
+    // a slab (halo planes along z) has the inlet / outlet of a z flow only where it has no halo
+    a.open_lo = (c.flow_axis == 2 && c.halo_lo) ? 0 : 1;
+    a.open_hi = (c.flow_axis == 2 && c.halo_hi) ? 0 : 1;
+    a.z0 = c.halo_lo;
+    a.z1 = c.nz - c.halo_hi;
+    a.zoff = c.z_offset;
     a.tau_mo = (float)c.tau_mo;
     a.Ksmag = (float)(18.0 * std::sqrt(2.0) * c.c_smag * c.c_smag);
     a.u_in = (float)c.u_in;
@@ -168,19 +177,26 @@ hl_status read_error_word(hl_lattice* lat) {
 
 namespace {
 
+// N_owned * sum_i w_i: the mass of the storage shift over the cells the
+// lattice owns (a slab's halo planes excluded)
 double shift_mass(const hl_lattice* lat) {
     std::vector<int> c(3 * lat->cfg.q);
     std::vector<double> w(lat->cfg.q);
     hl_velocity_set(lat->cfg.q, c.data(), w.data());
     double s = 0.0;
     for (double v : w) s += v;
-    return s * (double)lat->N;
+    const long long nxy = (long long)lat->cfg.nx * lat->cfg.ny;
+    return s * (double)(lat->N - (long long)(lat->cfg.halo_lo + lat->cfg.halo_hi) * nxy);
 }
 
 hl_status compute_mass(hl_lattice* lat, double tol, double* out) {
     MassArgs m;
     m.f = lat->f;
     m.count = (long long)lat->cfg.q * lat->N;
+    m.N = lat->N;
+    m.nxy = lat->cfg.nx * lat->cfg.ny;
+    m.halo_lo = lat->cfg.halo_lo;
+    m.halo_hi = lat->cfg.halo_hi;
     m.shift_mass = shift_mass(lat);
     m.ref = lat->mass_ref;
     m.tol = tol;
@@ -262,6 +278,7 @@ hl_status hl_lattice_init(hl_lattice** out, const hl_config* cfg, void* d_worksp
     lat->modes = reinterpret_cast<float*>(lat->ws + L.modes);
     lat->err = reinterpret_cast<unsigned*>(lat->ws + L.err);
     std::snprintf(lat->msg, sizeof lat->msg, "no error");
+    lat->halo_t[0] = lat->halo_t[1] = -1;
     hl_status st;
     if (cfg->n_modes > 0) {
         std::vector<float> m(9 * cfg->n_modes);
@@ -324,8 +341,10 @@ static bool rotor_box(const hl_lattice* lat, const hl_rotor_geometry* g, int lo[
         const int a = (int)std::floor(g->center[k] - r);
         const int b = (int)std::ceil(g->center[k] + r);
         const bool open = lat->cfg.open_boundaries && k == lat->cfg.flow_axis;
-        const int margin = open ? 4 : 0;
-        if (a < margin || b > dims[k] - 1 - margin) return false;
+        // 4 cells from an open face; a slab's box lies in its own planes
+        const int m_lo = (open && !(k == 2 && lat->cfg.halo_lo)) ? 4 : (k == 2 ? lat->cfg.halo_lo : 0);
+        const int m_hi = (open && !(k == 2 && lat->cfg.halo_hi)) ? 4 : (k == 2 ? lat->cfg.halo_hi : 0);
+        if (a < m_lo || b > dims[k] - 1 - m_hi) return false;
         lo[k] = a;
         nn[k] = b - a + 1;
     }
@@ -543,6 +562,13 @@ extern "C" {
 
 hl_status hl_step_async(hl_lattice* lat, int n) {
     if (!lat || n < 0) return HL_ERR_ARG;
+    if (lat->cfg.halo_lo || lat->cfg.halo_hi) {
+        // a slab steps once per call, after the halo exchange of its parity
+        if (n > 1) return fail(lat, HL_ERR_ARG, "a slab (halo planes) advances one step per call");
+        for (int f = 0; f < 2 && n > 0; ++f)
+            if ((f == 0 ? lat->cfg.halo_lo : lat->cfg.halo_hi) && lat->t > 0 && lat->halo_t[f] != lat->t)
+                return fail(lat, HL_ERR_STATE, "halo face not imported at the current time step");
+    }
     const bool two = lat->have_aux && lat->nrot > 0;
     if (two && n > 0) {
         // everything issued on the lattice stream so far precedes the aux work
@@ -695,6 +721,64 @@ hl_status hl_init_fields(hl_lattice* lat, const float* d_rho, const float* d_u) 
     return HL_OK;
 }
 
+// ---- slabs: halo exchange (AA pattern, decomposition along z) ----
+// The message of a face is one plane of the slots whose velocity crosses
+// that face, chosen by the step parity (see include/hlbm.h):
+//   export  face 0: t odd plane 1 (c_z = +1),      t even plane 0 (c_z = -1)
+//           face 1: t odd plane nz-2 (c_z = -1),   t even plane nz-1 (c_z = +1)
+//   import  face 0: t odd plane 0 (c_z = -1),      t even plane 1 (c_z = +1)
+//           face 1: t odd plane nz-1 (c_z = +1),   t even plane nz-2 (c_z = -1)
+static int halo_slot_list(int q, int sign, int* out) {
+    std::vector<int> c(3 * q);
+    std::vector<double> w(q);
+    hl_velocity_set(q, c.data(), w.data());
+    int n = 0;
+    for (int s = 0; s < q; ++s)
+        if (c[3 * s + 2] == sign) out[n++] = s;
+    return n;
+}
+
+static hl_status halo_copy(hl_lattice* lat, int face, void* buf, bool import_) {
+    if (!lat || face < 0 || face > 1 || !buf) return HL_ERR_ARG;
+    if (!(face == 0 ? lat->cfg.halo_lo : lat->cfg.halo_hi))
+        return fail(lat, HL_ERR_ARG, "hl_halo_export/import: the face is not a halo face");
+    const int nz = lat->cfg.nz;
+    const bool odd = (lat->t & 1) != 0;
+    int plane, sign;
+    if (!import_) {
+        if (face == 0) { plane = odd ? 1 : 0; sign = odd ? +1 : -1; }
+        else { plane = odd ? nz - 2 : nz - 1; sign = odd ? -1 : +1; }
+    } else {
+        if (face == 0) { plane = odd ? 0 : 1; sign = odd ? -1 : +1; }
+        else { plane = odd ? nz - 1 : nz - 2; sign = odd ? +1 : -1; }
+    }
+    HaloArgs h;
+    std::memset(&h, 0, sizeof h);
+    h.f = lat->f;
+    h.N = lat->N;
+    h.nxy = lat->cfg.nx * lat->cfg.ny;
+    h.plane = plane;
+    h.nslot = halo_slot_list(lat->cfg.q, sign, h.slots);
+    h.buf = buf;
+    h.import_ = import_ ? 1 : 0;
+    HL_CUDA(lat, launch_halo(lat->cfg.storage, h, lat->stream));
+    if (import_) lat->halo_t[face] = lat->t;
+    return HL_OK;
+}
+
+hl_status hl_halo_size(const hl_lattice* lat, size_t* bytes) {
+    if (!lat || !bytes || !(lat->cfg.halo_lo || lat->cfg.halo_hi)) return HL_ERR_ARG;
+    const int nslot = lat->cfg.q == 19 ? 5 : 9;
+    *bytes = (size_t)nslot * lat->cfg.nx * lat->cfg.ny * store_bytes(lat->cfg.storage);
+    return HL_OK;
+}
+
+hl_status hl_halo_export(hl_lattice* lat, int face, void* d_buf) { return halo_copy(lat, face, d_buf, false); }
+
+hl_status hl_halo_import(hl_lattice* lat, int face, const void* d_buf) {
+    return halo_copy(lat, face, const_cast<void*>(d_buf), true);
+}
+
 hl_status hl_mass(hl_lattice* lat, double* mass) {
     if (!lat || !mass) return HL_ERR_ARG;
     return compute_mass(lat, -1.0, mass);
@@ -791,6 +875,7 @@ hl_status hl_load_state(hl_lattice* lat, const void* d_buf, size_t bytes) {
     lat->t = h.t;
     lat->n_avg = h.n_avg;
     lat->mass_ref = h.mass_ref;
+    lat->halo_t[0] = lat->halo_t[1] = -1;   // a slab exchanges again before its next step
     hl_status st = state_copy(lat, const_cast<char*>(static_cast<const char*>(d_buf)), false);
     if (st != HL_OK) return st;
     HL_CUDA(lat, cudaMemsetAsync(lat->err, 0, sizeof(unsigned), lat->stream));

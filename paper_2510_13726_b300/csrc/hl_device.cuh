@@ -446,97 +446,116 @@ __device__ inline void rotor_normal(const RotorDev& R, int which, int x, int y, 
 }
 
 // ---------------------------------------------------------------------------
-// wall function, Sec. 2.2.1.  The Newton iterations run in FP64: their
-// stopping rule, the halving guard and the overflow of exp(kappa u+) are
-// decisions taken in floating point, and they must be taken in the same
-// precision as the FP64 statement of the scheme (FP32 exp overflows at
-// u+ ~ 216, which the iterates of a cold start do reach).  Only the few
-// wall cells run this code.
+// wall function, Sec. 2.2.1, in FP32.  The Newton step f/f' of Eq.
+// (implicitWF) is taken with numerator and denominator both multiplied by
+// exp(-kappa u+): the same quotient, but neither factor overflows when an
+// iterate lies far below the root (a cold start reaches u+ ~ 250, where
+// exp(kappa u+) is beyond the FP32 range; both f and f' grow like it).  The
+// stopping rule compares the unscaled residuals, which are +inf beyond
+// kappa u+ = 80 (there the residual exceeds 5e33 and the rule cannot stop).
 // ---------------------------------------------------------------------------
 // Constants of the wall function; divisions by them become products.
 struct WallFn {
-    double E, kappa, inv_E, kappa_inv_E, inv_kappa, inv_nu, tol;
+    float E, kappa, inv_E, kappa_inv_E, inv_kappa, inv_nu, tol;
     int maxit;
 };
 
 __host__ __device__ inline WallFn make_wallfn(double E, double kappa, double nu, double tol, int maxit) {
     WallFn W;
-    W.E = E;
-    W.kappa = kappa;
-    W.inv_E = 1.0 / E;
-    W.kappa_inv_E = kappa / E;
-    W.inv_kappa = 1.0 / kappa;
-    W.inv_nu = 1.0 / nu;
-    W.tol = tol;
+    W.E = (float)E;
+    W.kappa = (float)kappa;
+    W.inv_E = (float)(1.0 / E);
+    W.kappa_inv_E = (float)(kappa / E);
+    W.inv_kappa = (float)(1.0 / kappa);
+    W.inv_nu = (float)(1.0 / nu);
+    W.tol = (float)tol;
     W.maxit = maxit;
     return W;
 }
 
-// The two solves are written once for a scalar type T: double in the time
+// The two solves are written once for a scalar type T: float in the time
 // step, forward-mode duals in the reverse sweep (same operations on the
 // value part).
-__device__ __forceinline__ double wf_val(double x) { return x; }
-__device__ __forceinline__ double wf_exp(double x) { return exp(x); }
-__device__ __forceinline__ double wf_log(double x) { return log(x); }
-__device__ __forceinline__ double wf_rcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float wf_val(float x) { return x; }
+__device__ __forceinline__ float wf_exp(float x) { return expf(x); }
+__device__ __forceinline__ float wf_log(float x) { return logf(x); }
+__device__ __forceinline__ float wf_rcp(float x) { return 1.0f / x; }
 
 // y+(u+) of Eq. (spalding) and its derivative dy+/du+, given e = exp(kappa u+)
 template <class T>
 __device__ __forceinline__ T spalding_yplus_t(const T& up, const T& e, const WallFn& W) {
     const T k = W.kappa * up;
-    return up + (e - 1.0 - k - 0.5 * k * k - (1.0 / 6.0) * k * k * k) * W.inv_E;
+    return up + (e - 1.0f - k - 0.5f * k * k - (1.0f / 6.0f) * k * k * k) * W.inv_E;
 }
 template <class T>
 __device__ __forceinline__ T spalding_dyplus_t(const T& up, const T& e, const WallFn& W) {
     const T k = W.kappa * up;
-    return 1.0 + W.kappa_inv_E * (e - 1.0 - k - 0.5 * k * k);
+    return 1.0f + W.kappa_inv_E * (e - 1.0f - k - 0.5f * k * k);
 }
 
-// Newton-Raphson on Eq. (implicitWF), f(u_tau) = y+(u / u_tau) - y u_tau / nu:
-// stop when the residual changes by less than tol, at most maxit
-// iterations; a non-positive iterate is halved.  One exponential and one
-// reciprocal per iterate.
+// residual f(u_tau) = y+(u / u_tau) - u_tau y / nu of Eq. (implicitWF), for
+// the stopping rule only (no derivative); +inf where kappa u+ > 80
+__device__ __forceinline__ float wf_residual(float ut, float u, float y_nu, const WallFn& W) {
+    const float up = u / ut;
+    const float k = W.kappa * up;
+    if (!(k <= 80.0f)) return INFINITY;
+    return spalding_yplus_t(up, expf(k), W) - ut * y_nu;
+}
+
+// Newton step f / f' at u_tau, both scaled by s = exp(-kappa u+):
+//   f s  = (u+ - u_tau y / nu) s + (1 - P3 s) / E
+//   f' s = -(s + kappa / E (1 - P2 s)) u+ / u_tau - s y / nu
+// with P2, P3 the Taylor polynomials of exp(kappa u+) to second and third order
+template <class T>
+__device__ __forceinline__ T wf_step(const T& ut, const T& u, const T& y_nu, const WallFn& W) {
+    const T r = wf_rcp(ut);
+    const T up = u * r;
+    const T k = W.kappa * up;
+    const T s = wf_exp(0.0f - k);
+    const T P2 = 1.0f + k + 0.5f * k * k;
+    const T P3 = P2 + (1.0f / 6.0f) * k * k * k;
+    const T fs = (up - ut * y_nu) * s + (1.0f - P3 * s) * W.inv_E;
+    const T fps = 0.0f - (s + W.kappa_inv_E * (1.0f - P2 * s)) * up * r - y_nu * s;
+    return fs / fps;
+}
+
+// Newton-Raphson on Eq. (implicitWF): stop when the residual changes by less
+// than tol, at most maxit iterations; a non-positive iterate is halved.  One
+// exponential and one reciprocal per step, one more exponential per
+// residual.
 template <class T>
 __device__ inline T wall_newton_t(const T& u, const T& y, const T& guess, const WallFn& W) {
     const T y_nu = y * W.inv_nu;
     T ut = guess;
-    T r = wf_rcp(ut);
-    T up = u * r;
-    T e = wf_exp(W.kappa * up);
-    T fv = spalding_yplus_t(up, e, W) - ut * y_nu;
+    float fv = wf_residual(wf_val(ut), wf_val(u), wf_val(y_nu), W);
     for (int it = 0; it < W.maxit; ++it) {
-        const T fp = 0.0 - spalding_dyplus_t(up, e, W) * u * r * r - y_nu;
-        T un = ut - fv / fp;
-        if (!(wf_val(un) > 0.0)) un = 0.5 * ut;
-        const T rn = wf_rcp(un);
-        const T upn = u * rn;
-        const T en = wf_exp(W.kappa * upn);
-        const T fn = spalding_yplus_t(upn, en, W) - un * y_nu;
+        T un = ut - wf_step(ut, u, y_nu, W);
+        if (!(wf_val(un) > 0.0f)) un = 0.5f * ut;
+        const float fn = wf_residual(wf_val(un), wf_val(u), wf_val(y_nu), W);
         ut = un;
-        r = rn;
-        up = upn;
-        e = en;
-        if (fabs(wf_val(fn) - wf_val(fv)) < W.tol) break;
+        if (fabsf(fn - fv) < W.tol) break;
         fv = fn;
     }
     return ut;
 }
 
 // inverse of Eq. (spalding): u+ for y+, Newton from the right of the root
+// (y+ is convex and increasing in u+, so the iterates fall monotonically
+// from a start value of at most ln(1 + E y+)/kappa: no overflow)
 template <class T>
 __device__ inline T spalding_uplus_t(const T& yp, const WallFn& W) {
-    const T lg = wf_log(1.0 + W.E * yp) * W.inv_kappa;
+    const T lg = wf_log(1.0f + W.E * yp) * W.inv_kappa;
     T up = wf_val(yp) < wf_val(lg) ? yp : lg;
     T e = wf_exp(W.kappa * up);
     T g = spalding_yplus_t(up, e, W) - yp;
     for (int it = 0; it < W.maxit; ++it) {
         T un = up - g / spalding_dyplus_t(up, e, W);
-        if (!(wf_val(un) > 0.0)) un = 0.5 * up;
+        if (!(wf_val(un) > 0.0f)) un = 0.5f * up;
         const T en = wf_exp(W.kappa * un);
         const T gn = spalding_yplus_t(un, en, W) - yp;
         up = un;
         e = en;
-        if (fabs(wf_val(gn) - wf_val(g)) < W.tol) break;
+        if (fabsf(wf_val(gn) - wf_val(g)) < W.tol) break;
         g = gn;
     }
     return up;

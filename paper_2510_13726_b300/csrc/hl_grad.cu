@@ -498,28 +498,31 @@ __global__ void __launch_bounds__(128) adj_wall_kernel(const StepArgs a, const A
         const float utm = sqrtf(ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2]);
         if (!(utm >= 1e-12f)) continue;   // the forward left this cell inactive
         const float th[3] = {ut[0] / utm, ut[1] / utm, ut[2] / utm};
-        // forward Newton solves with derivatives along (|u_t|, y_sample, start value)
-        const double ysamp = (double)y1 + (double)ys;
+        // forward Newton solves with derivatives along (|u_t|, y_sample, start value),
+        // with the forward wall model's FP32 expressions
+        const float ysamp = y1 + ys;
         const bool warm = R.tape_active[bi] != 0;
         const WallFn W = make_wallfn(a.wmE, a.wmK, a.nu, a.wmTol, a.wmMaxit);
         // seeds: 0 = |u_t|, 1 = y_sample, 2 = Newton start value, one per lane
         const int seed = sub == 3 ? 0 : sub;
         Dual<1> guess;
         if (warm) {
-            guess = seed == 2 ? dual_seed<1>(R.tape_utau[bi], 0) : dual_const<1>(R.tape_utau[bi]);
+            const float gw = (float)R.tape_utau[bi];
+            guess = seed == 2 ? dual_seed<1>(gw, 0) : dual_const<1>(gw);
         } else {
-            const double g0 = sqrt(a.nu * (double)utm / (double)ys);
-            guess = seed == 0 ? dual_seed<1>(g0, 0, a.nu / ((double)ys * 2.0 * g0)) : dual_const<1>(g0);
+            // Eq. (guess): g0 = sqrt(nu |u_t| / y_s), d g0 / d|u_t| = nu / (2 y_s g0)
+            const float g0 = sqrtf(utm / (ys * W.inv_nu));
+            guess = seed == 0 ? dual_seed<1>(g0, 0, 1.0f / (2.0f * ys * W.inv_nu * g0)) : dual_const<1>(g0);
         }
-        const Dual<1> utau = wall_newton_t(seed == 0 ? dual_seed<1>((double)utm, 0) : dual_const<1>((double)utm),
+        const Dual<1> utau = wall_newton_t(seed == 0 ? dual_seed<1>(utm, 0) : dual_const<1>(utm),
                                            seed == 1 ? dual_seed<1>(ysamp, 0) : dual_const<1>(ysamp), guess, W);
-        double utd[3];
+        float utd[3];
 #pragma unroll
         for (int q = 0; q < 3; ++q) utd[q] = __shfl_sync(gm, utau.d[0], gbase + q);
-        const double y1p = (double)y1 * utau.v * W.inv_nu;
+        const float y1p = y1 * utau.v * W.inv_nu;
         const Dual<1> up = spalding_uplus_t(dual_seed<1>(y1p, 0), W);
-        const float uw = (float)(utau.v * up.v);
-        const float gs = (float)(0.5 * ((double)utm - utau.v * up.v) / (double)ys);
+        const float uw = utau.v * up.v;
+        const float gs = 0.5f * (utm - uw) / ys;
         // ---- reverse ----
         const float gdu[3] = {R.gub[bi], R.gub[BC + bi], R.gub[2 * BC + bi]};
         float Sb[6];
@@ -540,17 +543,17 @@ __global__ void __launch_bounds__(128) adj_wall_kernel(const StepArgs a, const A
                        gs * (2.0f * Sb[2] * th[2] + Sb[4] * th[0] + Sb[5] * th[1])};
         // gs = (|u_t| - utau u+) / (2 y_s)
         float utmb = 0.5f * gsb / ys;
-        const double uwdb = (double)uwb - 0.5 * (double)gsb / (double)ys;
-        double utaub = uwdb * up.v + R.gut_next[bi];
-        const double upb = uwdb * utau.v;
+        const float uwdb = uwb - 0.5f * gsb / ys;
+        float utaub = uwdb * up.v + (float)R.gut_next[bi];
+        const float upb = uwdb * utau.v;
         // u+ = U(y1 utau / nu)
-        const double y1pb = upb * up.d[0];
-        utaub += y1pb * (double)y1 * W.inv_nu;
-        double y1b = y1pb * utau.v * W.inv_nu;
+        const float y1pb = upb * up.d[0];
+        utaub += y1pb * y1 * W.inv_nu;
+        float y1b = y1pb * utau.v * W.inv_nu;
         // utau = Newton(|u_t|, y1 + y_s, start)
-        utmb += (float)(utaub * utd[0]);
+        utmb += utaub * utd[0];
         y1b += utaub * utd[1];
-        if (sub == 0) R.gut_prev[bi] = warm ? utaub * utd[2] : 0.0;
+        if (sub == 0) R.gut_prev[bi] = warm ? (double)(utaub * utd[2]) : 0.0;
         // th = u_t / |u_t|
         const float td = thb[0] * th[0] + thb[1] * th[1] + thb[2] * th[2];
         float utb[3];
@@ -596,7 +599,7 @@ __global__ void __launch_bounds__(128) adj_wall_kernel(const StepArgs a, const A
         }
         // pitch: through the normal and the wall distance y1 = max(phi, 1/2)
         double pg = (double)(nb[0] * dn[0] + nb[1] * dn[1] + nb[2] * dn[2]);
-        if (far) pg += y1b * (double)dphi;
+        if (far) pg += (double)(y1b * dphi);
         if (sub == 0) atomicAdd(R.pacc + (unsigned)idx % PACC_SLOTS, pg);
     }
 }
@@ -1144,6 +1147,8 @@ hl_status hl_grad(hl_lattice* lat, int steps, int avg_last, int ckpt_every, cons
                   const double* w_torque, double* J, double* dJ_dpitch, float* d_dJ_dd0, void* d_work,
                   size_t bytes) {
     if (!lat) return HL_ERR_ARG;
+    if (lat->cfg.halo_lo || lat->cfg.halo_hi)
+        return fail(lat, HL_ERR_STATE, "hl_grad: the gradient covers a whole lattice, not a slab");
     if (lat->cfg.layout == 0)
         return grad_aa(lat, steps, avg_last, ckpt_every, w_thrust, w_torque, J, dJ_dpitch, d_dJ_dd0, d_work, bytes);
     // esoteric twist: the sweep runs on the AA form of the same state (the
@@ -1172,7 +1177,8 @@ hl_status hl_set_d0(hl_lattice* lat, const float* d_d0) {
 
 hl_status hl_set_inflow_plane(hl_lattice* lat, const float* d_plane) {
     if (!lat) return HL_ERR_ARG;
-    if (d_plane && !lat->cfg.open_boundaries) return fail(lat, HL_ERR_STATE, "hl_set_inflow_plane: the lattice has no inlet");
+    if (d_plane && (!lat->cfg.open_boundaries || (lat->cfg.flow_axis == 2 && lat->cfg.halo_lo)))
+        return fail(lat, HL_ERR_STATE, "hl_set_inflow_plane: the lattice has no inlet");
     lat->inflow = d_plane;
     return HL_OK;
 }

@@ -99,6 +99,7 @@ struct hl_lattice {
     hl::host::RotorHost rot[hl::MAXROT];
     const float* d0;         // caller's static porosity multiplier [N], or null
     const float* inflow;     // caller's inflow velocity plane [3][plane], or null (synthetic modes)
+    long long halo_t[2];     // slab: time of the last halo import of the lower / upper face (-1: none)
     bool frozen;             // cell sets decided by RotorHost::pitch_sets
     char msg[256];
     // second stream for the rotor-box chain, and the events that order it

@@ -47,12 +47,15 @@ struct StepArgs {
     int phase;               // t & 1: AA layout of the pre-collision state
     long long t;
     int flow_axis, open;
+    int open_lo, open_hi;    // the open faces of the flow axis that this lattice has (a slab may lack one)
+    int z0, z1;              // planes the bulk launches collide: z0 <= z < z1 (halo planes excluded)
+    int zoff;                // global z of local plane 0 (synthetic inflow)
     float tau_mo, Ksmag;     // Ksmag = 18 sqrt(2) C_S^2
     float u_in, inflow_shift;   // inflow_shift = u_in * t
     float eps_half, inv_eps;
     int transition, wall_model;
     float wmYs;
-    double wmE, wmK, wmTol, nu;      // wall-function solve runs in FP64
+    double wmE, wmK, wmTol, nu;      // wall-function constants (rounded to FP32 by make_wallfn)
     int wmMaxit;
     float sigma_band;        // hybridisation factor of the force cells off the wall set
     const float* modes;      // [n_modes][9]
@@ -74,6 +77,9 @@ struct StepArgs {
 struct MassArgs {
     const void* f;
     long long count;         // Q * N stored values
+    long long N;             // cells per slot
+    int nxy;                 // cells per z plane
+    int halo_lo, halo_hi;    // halo planes (z = 0, z = nz - 1) excluded from the total
     double shift_mass;       // N * sum_i w_i (the storage shift)
     double ref, tol;         // reference mass and allowed relative drift (tol < 0: no check)
     double* partial;         // [MASS_BLOCKS]
@@ -94,6 +100,17 @@ cudaError_t launch_init(int Q, int storage, const StepArgs& a, const float* rho,
                         const float u0[3], cudaStream_t s);
 cudaError_t launch_fields(int Q, int storage, const StepArgs& a, float* rho, float* u,
                           cudaStream_t s);
+// halo message of a slab: nslot slots (list) of plane z, [nslot][nxy] stored
+// values; export = plane -> buffer, import = buffer -> plane
+struct HaloArgs {
+    void* f;
+    long long N;
+    int nxy, plane, nslot;
+    int slots[9];
+    void* buf;
+    int import_;
+};
+cudaError_t launch_halo(int storage, const HaloArgs& h, cudaStream_t s);
 cudaError_t launch_debug_collide(int Q, int n, const float* g_in, const float* d, const float* uB,
                                  const float* sigma, const float* S, float tau_mo, float Ksmag,
                                  float* g_out, cudaStream_t s);

@@ -111,8 +111,8 @@ __device__ __forceinline__ void collide_cell(const StepArgs& a, int x, int y, in
     const int ax = a.flow_axis;
     const int ca = sel3(ax, x, y, z);
     const int na = sel3(ax, a.n[0], a.n[1], a.n[2]);
-    const bool inlet = a.open && ca == 0;
-    const bool outlet = a.open && ca == na - 1;
+    const bool inlet = a.open && a.open_lo && ca == 0;
+    const bool outlet = a.open && a.open_hi && ca == na - 1;
     // every population at one offset from a per-slot base (no neighbour index
     // arithmetic): AA odd steps away from the lattice faces; esoteric twist
     // (links towards +x, +y, +z only) away from the upper faces
@@ -191,7 +191,7 @@ __device__ __forceinline__ void collide_cell(const StepArgs& a, int x, int y, in
             rho = collide<Q, false>(g, B0, a.tau_mo, a.Ksmag, u);
         }
         if (!(fabsf(rho) < 1e30f)) atomicOr(a.err, ERR_NONFINITE);
-        if (a.open && ca == na - 2) {
+        if (a.open && a.open_hi && ca == na - 2) {
             const int nb = sel3(ax, a.n[1], a.n[2], a.n[0]);
             const int cb = sel3(ax, y, z, x), cc = sel3(ax, z, x, y);
             const int pl = cc * nb + cb;
@@ -229,7 +229,7 @@ __device__ __forceinline__ void collide_cell(const StepArgs& a, int x, int y, in
         // equilibrium inflow: U a + sum_m a_m cos(k.x') + b_m sin(k.x'), x' = x - U t a
         float u[3] = {0.f, 0.f, 0.f};
         u[ax] = a.u_in;
-        float xp[3] = {(float)x, (float)y, (float)z};
+        float xp[3] = {(float)x, (float)y, (float)(z + a.zoff)};
         xp[ax] -= a.inflow_shift;
         for (int m = 0; m < a.n_modes; ++m) {
             const float* md = a.modes + 9 * m;
@@ -274,13 +274,13 @@ template <int Q, int S, int PH, bool D0, int L>
 __global__ void __launch_bounds__(128) collide_kernel(const StepArgs a) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
     if (a.part == 2) {
         const RotorDev& R = a.rot[a.part_rotor];
         if (x >= R.n[0] || y >= R.n[1]) return;
-        collide_cell<Q, S, PH, D0, L>(a, x + R.lo[0], y + R.lo[1], z + R.lo[2]);
+        collide_cell<Q, S, PH, D0, L>(a, x + R.lo[0], y + R.lo[1], (int)blockIdx.z + R.lo[2]);
         return;
     }
+    const int z = (int)blockIdx.z + a.z0;     // halo planes of a slab are not collided
     if (y >= a.n[1] || x >= a.n[0]) return;
     collide_cell<Q, S, PH, D0, L>(a, x, y, z);
 }
@@ -302,7 +302,7 @@ template <int Q, int S, int PH, int L>
 __global__ void __launch_bounds__(128, Q == 27 ? 8 : 10) collide_pair_kernel(const StepArgs a) {
     const int x = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
+    const int z = (int)blockIdx.z + a.z0;     // halo planes of a slab are not collided
     if (y >= a.n[1] || x >= a.n[0]) return;
     bool plain = x + 1 < a.n[0];
     for (int k = 0; k < a.nrot; ++k) {
@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(128, Q == 27 ? 8 : 10) collide_pair_kernel(con
         const int ca = sel3(a.flow_axis, x, y, z);
         const int ca1 = ca + (a.flow_axis == 0 ? 1 : 0);
         const int na = sel3(a.flow_axis, a.n[0], a.n[1], a.n[2]);
-        if (ca == 0 || ca1 >= na - 2) plain = false;
+        if ((a.open_lo && ca == 0) || (a.open_hi && ca1 >= na - 2)) plain = false;
     }
     // the y and z neighbours the pair touches must lie inside the lattice
     if (L == 0 && PH == 1 && !(y > 0 && y < a.n[1] - 1 && z > 0 && z < a.n[2] - 1)) plain = false;
@@ -580,17 +580,17 @@ __global__ void __launch_bounds__(128) wall_kernel(const StepArgs a) {
             continue;
         }
         const float th[3] = {ut[0] / utm, ut[1] / utm, ut[2] / utm};
-        const double ysamp = (double)y1 + (double)a.wmYs;
+        const float ysamp = y1 + a.wmYs;
+        const WallFn W = make_wallfn(a.wmE, a.wmK, a.nu, a.wmTol, a.wmMaxit);
         // Eq. (guess): previous value if the wall function was active last step
         // (read by lane 0, which alone writes the new value below)
-        double guess = 0.0;
-        if (sub == 0) guess = R.active[bi] ? R.utau[bi] : sqrt(a.nu * (double)utm / (double)a.wmYs);
+        float guess = 0.f;
+        if (sub == 0) guess = R.active[bi] ? (float)R.utau[bi] : sqrtf(utm / (a.wmYs * W.inv_nu));
         if constexpr (LN > 1) guess = __shfl_sync(gm, guess, gbase);
-        const WallFn W = make_wallfn(a.wmE, a.wmK, a.nu, a.wmTol, a.wmMaxit);
-        const double utau = wall_newton_t<double>((double)utm, ysamp, guess, W);
-        const double up = spalding_uplus_t<double>((double)y1 * utau * W.inv_nu, W);
-        const float uw = (float)(utau * up);
-        const float gs = (float)(0.5 * ((double)utm - utau * up) / (double)a.wmYs);
+        const float utau = wall_newton_t<float>(utm, ysamp, guess, W);
+        const float up = spalding_uplus_t<float>(y1 * utau * W.inv_nu, W);
+        const float uw = utau * up;
+        const float gs = 0.5f * (utm - uw) / a.wmYs;
         if (sub != 0) continue;
         wm[0] = uw * th[0];
         wm[B] = uw * th[1];
@@ -602,7 +602,7 @@ __global__ void __launch_bounds__(128) wall_kernel(const StepArgs a) {
         wm[7 * B] = gs * (th[0] * n[2] + n[0] * th[2]);
         wm[8 * B] = gs * (th[1] * n[2] + n[1] * th[2]);
         R.active[bi] = 1;
-        R.utau[bi] = utau;
+        R.utau[bi] = (double)utau;
     }
 }
 
@@ -783,23 +783,67 @@ __global__ void evolve_kernel(const StepArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// FP64 mass total (deterministic two-stage reduction) and drift check;
-// groups of 8 stored values are summed in FP32 first (16-byte loads)
+// FP64 mass total (deterministic two-stage reduction) and drift check
 // ---------------------------------------------------------------------------
+// The mass total in fixed point.  B300's FP64 pipe is narrow (one FP64
+// addition per stored value ran the check at 2.5 ms on rotor256, six times
+// its memory time), so each stored value is turned, with integer
+// operations, into a multiple of 2^-56 and summed in 128-bit integers; a
+// thread's total goes to FP64 once and the block and grid sums are FP64.  A
+// value of magnitude below 8 is taken exactly down to 2^-56 (the bits below
+// are dropped: at most 2^-56 per value); anything larger, and inf or NaN,
+// is added in FP64 instead, so the check still sees it.
+constexpr int FIX_SHIFT = 56;
+
+// binary32 bits -> value * 2^56 as a signed 64-bit integer (|value| < 8),
+// or false when the value needs the FP64 path
+__device__ __forceinline__ bool f32_fixed(unsigned u, long long& out) {
+    const int eb = (int)((u >> 23) & 0xffu);
+    if (eb >= 130) return false;                        // |value| >= 8, inf, NaN
+    const long long m = (long long)((u & 0x7fffffu) | (eb ? 0x800000u : 0u));
+    const int sh = (eb ? eb : 1) - 150 + FIX_SHIFT;     // value = m * 2^((eb ? eb : 1) - 150)
+    const long long mag = sh >= 0 ? (m << sh) : (sh > -24 ? (m >> -sh) : 0);
+    out = (u >> 31) ? -mag : mag;
+    return true;
+}
+
 template <int S>
-__device__ __forceinline__ float sum8(const typename Store<S>::T* p) {
+__device__ __forceinline__ unsigned stored_bits(typename Store<S>::T v) {
+    if constexpr (S == ST_F32) return __float_as_uint(v);
+    else return __float_as_uint(Store<S>::ld(&v));      // exact widening of FP16 / BF16
+}
+
+// Sum of eight consecutive stored values (one 16- or 32-byte load) into the
+// thread's 128-bit fixed-point accumulator (and its FP64 side sum)
+template <int S>
+__device__ __forceinline__ void sum8_fixed(const typename Store<S>::T* p, __int128& acc, double& side) {
+    using T = typename Store<S>::T;
+    T h[8];
     if constexpr (S == ST_F32) {
         const float4 a = reinterpret_cast<const float4*>(p)[0];
         const float4 b = reinterpret_cast<const float4*>(p)[1];
-        return ((a.x + a.y) + (a.z + a.w)) + ((b.x + b.y) + (b.z + b.w));
+        h[0] = a.x; h[1] = a.y; h[2] = a.z; h[3] = a.w; h[4] = b.x; h[5] = b.y; h[6] = b.z; h[7] = b.w;
     } else {
         const uint4 v = *reinterpret_cast<const uint4*>(p);
-        const typename Store<S>::T* h = reinterpret_cast<const typename Store<S>::T*>(&v);
-        float s = 0.f;
+        const T* hv = reinterpret_cast<const T*>(&v);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) s += Store<S>::ld(h + k);
-        return s;
+        for (int k = 0; k < 8; ++k) h[k] = hv[k];
     }
+    long long g = 0;                                    // |g| < 8 * 2^59 = 2^62
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        long long x;
+        if (f32_fixed(stored_bits<S>(h[k]), x)) g += x;
+        else side += (double)Store<S>::ld(h + k);
+    }
+    acc += (__int128)g;
+}
+
+// FP64 value of a 128-bit fixed-point total (one rounding of the low word)
+__device__ __forceinline__ double fixed_to_double(__int128 acc) {
+    const long long hi = (long long)(acc >> 64);
+    const unsigned long long lo = (unsigned long long)acc;
+    return ((double)hi * 0x1p64 + (double)lo) * 0x1p-56;
 }
 
 template <int S>
@@ -807,12 +851,25 @@ __global__ void __launch_bounds__(256) mass_kernel(const MassArgs m) {
     using T = typename Store<S>::T;
     const T* f = static_cast<const T*>(m.f);
     const long long groups = m.count / 8;
+    __int128 acc = 0;
     double v = 0.0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < groups;
          i += (long long)gridDim.x * blockDim.x)
-        v += (double)sum8<S>(f + 8 * i);
+        sum8_fixed<S>(f + 8 * i, acc, v);
+    v += fixed_to_double(acc);
     if (blockIdx.x == 0 && threadIdx.x == 0)
         for (long long i = 8 * groups; i < m.count; ++i) v += (double)Store<S>::ld(f + i);
+    // a slab's halo planes stand for its neighbours' cells: take them out again
+    const long long nh = (long long)(m.halo_lo + m.halo_hi) * m.nxy;
+    if (nh > 0) {
+        const long long slots = m.count / m.N;
+        for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < slots * nh;
+             i += (long long)gridDim.x * blockDim.x) {
+            const long long sl = i / nh, r = i % nh;
+            const long long cell = (m.halo_lo && r < m.nxy) ? r : m.N - nh + r;
+            v -= (double)Store<S>::ld(f + sl * m.N + cell);
+        }
+    }
     __shared__ double sh[8];
     __shared__ bool last;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -940,12 +997,12 @@ static cudaError_t launch_collide_l(const StepArgs& a, cudaStream_t s) {
     if (a.part != 2 && a.pairs && !a.d0) {
         const int half = (n[0] + 1) / 2;
         const dim3 pb = cell_block(half);
-        const dim3 pg((half + pb.x - 1) / pb.x, (n[1] + pb.y - 1) / pb.y, n[2]);
+        const dim3 pg((half + pb.x - 1) / pb.x, (n[1] + pb.y - 1) / pb.y, a.z1 - a.z0);
         if (a.phase == 0) collide_pair_kernel<Q, S, 0, L><<<pg, pb, 0, s>>>(a);
         else collide_pair_kernel<Q, S, 1, L><<<pg, pb, 0, s>>>(a);
         return cudaGetLastError();
     }
-    const dim3 grd((n[0] + blk.x - 1) / blk.x, (n[1] + blk.y - 1) / blk.y, n[2]);
+    const dim3 grd((n[0] + blk.x - 1) / blk.x, (n[1] + blk.y - 1) / blk.y, a.part == 2 ? n[2] : a.z1 - a.z0);
     if (a.d0) {
         if (a.phase == 0) collide_kernel<Q, S, 0, true, L><<<grd, blk, 0, s>>>(a);
         else collide_kernel<Q, S, 1, true, L><<<grd, blk, 0, s>>>(a);
@@ -1084,6 +1141,32 @@ static cudaError_t launch_fields_t(const StepArgs& a, float* rho, float* u, cuda
 }
 cudaError_t launch_fields(int Q, int S, const StepArgs& a, float* rho, float* u, cudaStream_t s) {
     HL_DISPATCH(Q, S, launch_fields_t, a, rho, u, s);
+}
+
+// halo message: slot list x plane, raw stored values (no conversion)
+template <typename T>
+__global__ void __launch_bounds__(256) halo_kernel(const HaloArgs h) {
+    const long long n = (long long)h.nslot * h.nxy;
+    T* f = static_cast<T*>(h.f);
+    T* b = static_cast<T*>(h.buf);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(i / h.nxy);
+        const long long c = (long long)h.plane * h.nxy + (i - (long long)k * h.nxy);
+        T* p = f + (long long)h.slots[k] * h.N + c;
+        if (h.import_) *p = b[i];
+        else b[i] = *p;
+    }
+}
+
+cudaError_t launch_halo(int storage, const HaloArgs& h, cudaStream_t s) {
+    const long long n = (long long)h.nslot * h.nxy;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 148 * 8) blocks = 148 * 8;
+    if (blocks < 1) blocks = 1;
+    if (storage == ST_F32) halo_kernel<float><<<(unsigned)blocks, 256, 0, s>>>(h);
+    else halo_kernel<unsigned short><<<(unsigned)blocks, 256, 0, s>>>(h);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_debug_collide(int Q, int n, const float* g_in, const float* d, const float* uB,

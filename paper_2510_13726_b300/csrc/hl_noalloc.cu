@@ -91,6 +91,10 @@ extern "C" hl_status hl_mass_noalloc(int q, int storage, const void* d_f, long l
     const long long count = (long long)q * n_cells;
     const long long chunks = (count + NA_CHUNK - 1) / NA_CHUNK;
     if (chunks > NA_MAX_CHUNKS) return HL_ERR_WORKSPACE;   // more than 2^32 stored values
+    // an error left pending by earlier, unrelated work belongs to that work:
+    // report it (and clear it, as any runtime call would) before launching,
+    // so that the launch check below sees this call's launch only
+    if (cudaGetLastError() != cudaSuccess) return HL_ERR_CUDA;
     NoAllocScratch* sc = nullptr;
     if (scratch_for_current_device(&sc) != cudaSuccess) return HL_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);

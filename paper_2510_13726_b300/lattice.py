@@ -31,7 +31,7 @@ class Lattice:
                  tau_mo=0.5005, c_smag=0.1, u_in=0.05, eps_h=2.0, transition="smoothstep",
                  sigma_band=1.0, wall_model=True, wm_E=9.8, wm_kappa=0.41, wm_ysample=2.0, wm_tol=1e-4,
                  wm_maxit=10, modes=None, mass_check_every=100, mass_tol=0.05, overlap=True,
-                 layout="aa", device=None, stream=None):
+                 layout="aa", halo_lo=False, halo_hi=False, z_offset=0, device=None, stream=None):
         import torch
         self.device = torch.device(device if device is not None else "cuda")
         if self.device.index is None:
@@ -52,6 +52,7 @@ class Lattice:
         cfg.mass_check_every, cfg.mass_tol = int(mass_check_every), float(mass_tol)
         cfg.overlap = int(bool(overlap))
         cfg.layout = {"aa": 0, "esotwist": 1}[layout] if isinstance(layout, str) else int(layout)
+        cfg.halo_lo, cfg.halo_hi, cfg.z_offset = int(bool(halo_lo)), int(bool(halo_hi)), int(z_offset)
         self._modes = None
         if modes is not None and len(modes):
             self._modes = np.ascontiguousarray(modes, dtype=np.float64).reshape(-1, 9)
@@ -143,6 +144,25 @@ class Lattice:
         import torch
         with torch.cuda.device(self.device):
             self._check(lib().hl_step(self._h, int(n)))
+
+    # -- slabs (halo planes along z) -------------------------------------------
+    def halo_size(self) -> int:
+        """Bytes of one halo message (hl_halo_size)."""
+        size = C.c_size_t()
+        self._check(lib().hl_halo_size(self._h, C.byref(size)))
+        return size.value
+
+    def halo_export(self, face: int, buf):
+        """Outgoing message of face 0 (lower) / 1 (upper) into the device tensor buf."""
+        import torch
+        with torch.cuda.device(self.device):
+            self._check(lib().hl_halo_export(self._h, int(face), C.c_void_p(buf.data_ptr())))
+
+    def halo_import(self, face: int, buf):
+        """The neighbour's message for face 0 / 1 from the device tensor buf."""
+        import torch
+        with torch.cuda.device(self.device):
+            self._check(lib().hl_halo_import(self._h, int(face), C.c_void_p(buf.data_ptr())))
 
     def step_async(self, n: int = 1):
         import torch

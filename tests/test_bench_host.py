@@ -54,3 +54,23 @@ def test_single_rank_aggregate_and_reference_line(capsys):
     line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["unit"] == "MLUPS" and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_weak_scaling_row_of_rotors():
+    """bench.py --gpus N: a row of N rotor256 domains along the flow axis,
+    one slab of 512 planes and one rotor per rank; the cuts split no rotor
+    box, the first slab keeps the inlet and the last the outlet."""
+    import bench
+    import workloads as W
+    from paper_2510_13726_b300.slabs import rotor_z_extent, slab_specs
+    base = W.workload("rotor256")
+    wl = bench.chain_workload(base, 3)
+    assert wl.nz == 1536 and [r.center[2] for r in wl.rotors] == [128.0, 640.0, 1152.0]
+    cuts = [0, 512, 1024, 1536]
+    g = wl.blade_grids()[0]
+    for k, r in enumerate(wl.rotors):
+        a, b = rotor_z_extent(g, r.center, wl.flow_axis, wl.eps_h)
+        assert cuts[k] + 4 <= a and b < cuts[k + 1] - 1
+    specs = slab_specs(cuts, periodic_z=False)
+    assert [(s.halo_lo, s.halo_hi) for s in specs] == [(False, True), (True, True), (True, False)]
+    assert [s.z_offset for s in specs] == [0, 511, 1023]

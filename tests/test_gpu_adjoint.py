@@ -266,10 +266,23 @@ def test_wall_sample_outside_box_is_reported(P):
 
 def test_gradient_study_128x128x256_against_finite_differences(P):
     """The gradient study (128x128x256 D3Q19, R = 32, wall model on): mean
-    thrust over the last 1000 of 4000 steps, checkpoint every 100 steps.
-    dJ/dpitch against a central difference of the CUDA forward (h = 1e-4
-    rad, cell sets frozen); dJ/dd0 at 32 random cells within 2R of the rotor
-    centre against central differences (h_d = 1e-3)."""
+    thrust over the last 1000 of 4000 steps, checkpoint every 100 steps,
+    against central differences of the CUDA forward (cell sets frozen; J is
+    the FP64 running mean of the per-step FP64 force sums).
+
+    Step sizes from an h-sweep of this workload: the pitch difference falls
+    onto the adjoint as h shrinks (relative gap 1.1e-2 at h = 1e-3, 2.0e-3 at
+    1e-4, 2.6e-4 at 3e-5, 3.6e-5 at 1e-5: the trilinear blade grid's kinks
+    make J only piecewise smooth in the pitch), so h = 1e-5 is the converged
+    difference, held to 1e-3.  A single cell's d0 moves J by ~1e-4 per unit,
+    so its difference carries the forward's rounding noise: the median error
+    over the 32 cells follows n/h + c h^2 (n ~ 6e-6, c ~ 7; 6.1e-3 at h =
+    0.03, 1.4e-3 at 0.01, 2.7e-3 at 0.003, 5.7e-3 at 0.001).  The test takes
+    the Richardson extrapolation (4 D(h/2) - D(h)) / 3 from h = 0.02 and 0.01,
+    which removes the h^2 term, and measures the noise itself as the spread
+    of two nearby differences, D(0.01) and D(0.0105), whose truncation is the
+    same to 1e-4: the median relative error must be within 1e-3 or within
+    twice the median noise level, whichever is larger."""
     import torch
     wl = W.workload("rotor128_adj")
     T, navg, K = 4000, 1000, 100
@@ -293,9 +306,10 @@ def test_gradient_study_128x128x256_against_finite_differences(P):
         return Fa[0, wl.flow_axis]
 
     assert abs(Jrun() - J) <= 1e-12 * abs(J)
-    fd = (Jrun(1e-4) - Jrun(-1e-4)) / 2e-4
-    print(f"dJ/dpitch adjoint {gp[0]:.6f} FD {fd:.6f}")
-    assert abs(gp[0] - fd) <= 2e-2 * abs(fd)
+    fd = {h: (Jrun(h) - Jrun(-h)) / (2 * h) for h in (3e-5, 1e-5)}
+    print("dJ/dpitch adjoint %.7f; central differences %s" % (gp[0], {h: round(v, 7) for h, v in fd.items()}))
+    assert abs(gp[0] - fd[1e-5]) <= 1e-3 * abs(fd[1e-5])
+    assert abs(gp[0] - fd[1e-5]) <= abs(gp[0] - fd[3e-5]) + 1e-4 * abs(fd[1e-5])   # converging onto it
     rng = np.random.default_rng(11)
     c, R = wl.rotors[0].center, wl.rotors[0].radius
     cells = []
@@ -304,22 +318,30 @@ def test_gradient_study_128x128x256_against_finite_differences(P):
         if np.linalg.norm(off) <= 2 * R:
             x, y, z = (int(round(c[k] + off[k])) for k in range(3))
             cells.append((z, y, x))
-    adj, fds = [], []
-    for cell in cells:
+
+    def D(cell, h):
         e = np.ones((wl.nz, wl.ny, wl.nx), np.float32)
-        e[cell] = 1.001
+        e[cell] = 1.0 + h
         Jp = Jrun(d0=e)
-        e[cell] = 0.999
-        Jm = Jrun(d0=e)
+        e[cell] = 1.0 - h
+        return (Jp - Jrun(d0=e)) / (2 * h)
+
+    adj, rich, spread = [], [], []
+    for cell in cells:
+        d1, d2, d3 = D(cell, 0.02), D(cell, 0.01), D(cell, 0.0105)
         adj.append(float(gd[cell]))
-        fds.append((Jp - Jm) / 2e-3)
-    adj, fds = np.array(adj), np.array(fds)
-    scale = np.abs(fds).max()
-    rel = np.abs(adj - fds) / np.maximum(np.abs(fds), 0.05 * scale)
-    print("dJ/dd0 relative error: median %.3g, 90th percentile %.3g, max %.3g" %
-          (np.median(rel), np.percentile(rel, 90), rel.max()))
-    assert np.median(rel) <= 0.02
-    assert np.percentile(rel, 90) <= 0.1
+        rich.append((4 * d2 - d1) / 3)
+        spread.append(abs(d2 - d3))
+    adj, rich, spread = np.array(adj), np.array(rich), np.array(spread)
+    scale = np.abs(rich).max()
+    den = np.maximum(np.abs(rich), 0.05 * scale)
+    rel = np.abs(adj - rich) / den
+    noise = spread / den
+    print("dJ/dd0 (Richardson h = 0.02/0.01) relative error: median %.3g, 90th percentile %.3g, max %.3g; "
+          "noise (|D(0.01) - D(0.0105)|) median %.3g" % (np.median(rel), np.percentile(rel, 90), rel.max(),
+                                                         np.median(noise)))
+    assert np.median(rel) <= max(1e-3, 2 * np.median(noise))
+    assert np.percentile(rel, 90) <= max(1e-2, 4 * np.percentile(noise, 90))
 
 
 def test_gradient_with_held_caller_inflow_plane(P):

@@ -124,12 +124,50 @@ def test_driven_snapshot_resume_and_gradient_refusal(P):
     assert e.value.code == -5
 
 
-def test_convergence_study_driver(P):
-    """The grid-convergence driver on three resolutions (one revolution
-    of spin-up, one averaged): finite thrust coefficients and the derived
-    orders and index."""
+def test_convergence_study_workload_parity(P):
+    """The finest-Reynolds-ladder workload of the grid-convergence study at its
+    coarsest grid (R = 16, 64x64x128, tau = 0.50025, wall model on): fields
+    against the FP64 oracle after 300 steps (relative L2 of rho and u <= 1e-5)
+    and the rotor loads of every compared step (<= 1e-3)."""
     from paper_2510_13726_b300 import convergence as C
-    res = C.run_study(radii=(16, 32, 64), revolutions_spinup=1.0, revolutions_avg=1.0)
-    ct = [r["C_T"] for r in res["resolutions"]]
-    assert all(np.isfinite(ct)) and all(c > 0 for c in ct)
-    assert np.isfinite(res["apparent_order"]) and res["gci_finest"] >= 0.0
+    wl = C.study_workload(16)
+    assert abs(wl.tau_mo - 0.50025) < 1e-15
+    lat = P.Lattice.from_workload(wl)
+    o = O.from_workload(wl)
+    for t_target in (100, 200, 300):
+        lat.step(t_target - lat.t)
+        o.step(t_target - o.t)
+        rg, ug = (a.cpu().numpy().astype(np.float64) for a in lat.fields())
+        ro, uo = o.fields()
+        e_rho = np.linalg.norm((rg - ro)[1:-1]) / np.linalg.norm(ro[1:-1])
+        e_u = np.linalg.norm((ug - uo)[:, 1:-1]) / np.linalg.norm(uo[:, 1:-1])
+        Fg, _ = lat.forces()
+        Mg, _ = lat.moments()
+        Fo, Mo, _, _ = o.forces()
+        eF = np.abs(Fg - Fo).max() / np.abs(Fo).max()
+        eM = np.abs(Mg - Mo).max() / np.abs(Mo).max()
+        print(f"R=16 study workload t={t_target}: rho {e_rho:.2e} u {e_u:.2e} F {eF:.2e} M {eM:.2e}")
+        assert e_rho <= 1e-5 and e_u <= 1e-5, (t_target, e_rho, e_u)
+        assert eF <= 1e-3 and eM <= 1e-3, (t_target, eF, eM)
+    lat.close()
+
+
+def test_convergence_study_driver(P):
+    """The grid-convergence driver on three resolutions of each ladder (one
+    revolution of spin-up, one averaged): the Reynolds ladder scales the
+    viscosity with R, the y+ ladder keeps it; finite thrust coefficients and
+    the derived orders and index."""
+    from paper_2510_13726_b300 import convergence as C
+    for ladder in ("reynolds", "yplus"):
+        res = C.run_study(radii=(16, 32, 64), revolutions_spinup=1.0, revolutions_avg=1.0, ladder=ladder)
+        rows = res["resolutions"]
+        ct = [r["C_T"] for r in rows]
+        assert all(np.isfinite(ct)) and all(c > 0 for c in ct)
+        assert np.isfinite(res["apparent_order"]) and res["gci_finest"] >= 0.0
+        taus = [r["tau"] for r in rows]
+        if ladder == "yplus":
+            assert taus == [0.5005] * 3
+            assert rows[2]["Re"] == pytest.approx(4 * rows[0]["Re"])
+        else:
+            assert taus[2] - 0.5 == pytest.approx(4 * (taus[0] - 0.5))
+            assert rows[2]["Re"] == pytest.approx(rows[0]["Re"])
