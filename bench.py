@@ -542,7 +542,9 @@ def timed_run(wl, storage, steps, warmup, dev):
 
 
 def storage_study(dev, steps):
-    """D3Q27 512x512x1024 rotor (R = 128, TSR 7): FP32 vs FP16 / BF16 storage."""
+    """FP32 vs FP16 / BF16 storage: the D3Q27 512x512x1024 rotor (R = 128,
+    TSR 7) and the D3Q19 256x256x512 benchmark rotor (R = 64, TSR 6, 5 %
+    turbulence; at least 200 steps)."""
     import workloads as W
     wl = W.workload("rotor1024_q27")
     out = {"workload": "rotor1024_q27: 512x512x1024 D3Q27, R=128 NACA4412 rotor, TSR 7", "steps": steps}
@@ -550,6 +552,14 @@ def storage_study(dev, steps):
         out[st] = timed_run(wl, st, steps, 5, dev)
     for st in ("f16s", "bf16s"):
         out[f"ratio_{st}_over_f32"] = round(out[st]["MLUPS"] / out["f32"]["MLUPS"], 3)
+    wl19 = W.workload("rotor256")
+    s19 = max(steps, 200)
+    d19 = {"workload": "rotor256: 256x256x512 D3Q19, R=64 NACA4412 rotor, TSR 6, 5% turbulence", "steps": s19}
+    for st in ("f32", "f16s", "bf16s"):
+        d19[st] = timed_run(wl19, st, s19, 10, dev)
+    for st in ("f16s", "bf16s"):
+        d19[f"ratio_{st}_over_f32"] = round(d19[st]["MLUPS"] / d19["f32"]["MLUPS"], 3)
+    out["d3q19"] = d19
     return out
 
 

@@ -101,7 +101,8 @@ typedef int hl_status;
  *                  hl_halo_import of each halo face (see there).  Needs
  *                  layout 0; hl_grad rejects slabs (HL_ERR_STATE).
  *  z_offset        global z index of local plane 0 (the synthetic inflow is
- *                  evaluated at global coordinates); 0 for a whole lattice
+ *                  evaluated at global coordinates); 0 for a whole lattice,
+ *                  -1 for the first slab of a periodic decomposition
  */
 typedef struct hl_config {
     int nx, ny, nz;

@@ -54,17 +54,27 @@ def study_workload(radius: int, tsr: float = 6.0, u_in: float = 0.05, tau_ref: f
     the reference (tau = tau_ref) at every R, so y+ of the first cell (its
     distance in cells times u_tau / nu) stays the same while the Reynolds
     number U R / nu grows with R: the refinement of a wall-modelled LES,
-    which resolves the outer flow ever finer and models the same inner layer."""
+    which resolves the outer flow ever finer and models the same inner layer.
+    ladder "interface": the y+ ladder with the porosity transition scaled with
+    the rotor (eps_h = 2 R / R_ref cells, Definition "Lattice Porosity"), so
+    the diffuse interface, and the wall set in its fluid half, cover the same
+    fraction of the blade chord at every R."""
     from workloads.configs import Workload, _single
     n = 4 * radius
+    eps_h = 2.0
     if ladder == "reynolds":
         tau = 0.5 + (tau_ref - 0.5) * radius / radius_ref
-    elif ladder == "yplus":
+    elif ladder in ("yplus", "interface"):
         tau = tau_ref
+        if ladder == "interface":
+            eps_h = 2.0 * radius / radius_ref
     else:
-        raise ValueError("ladder is 'reynolds' or 'yplus'")
-    return Workload(f"convergence_R{radius}_{ladder}", n, n, 2 * n, steps=0, tau_mo=tau, u_in=u_in,
-                    rotors=_single(n, n, 2 * n, float(radius), tsr))
+        raise ValueError("ladder is 'reynolds', 'yplus' or 'interface'")
+    # blade-grid padding: the fluid half of the transition, the sampling distance
+    # and the trilinear corner stay inside the grid (and so inside the rotor box)
+    margin = 4.0 if eps_h <= 2.0 else 0.5 * eps_h + 4.0
+    return Workload(f"convergence_R{radius}_{ladder}", n, n, 2 * n, steps=0, tau_mo=tau, u_in=u_in, eps_h=eps_h,
+                    grid_margin=margin, rotors=_single(n, n, 2 * n, float(radius), tsr))
 
 
 def run_study(radii=(16, 32, 64, 128), revolutions_spinup: float = 3.0, revolutions_avg: float = 2.0,
@@ -99,7 +109,7 @@ def run_study(radii=(16, 32, 64, 128), revolutions_spinup: float = 3.0, revoluti
         wall = (band["flags"] & 2) > 0
         ut = band["utau"][wall]
         nu = (wl.tau_mo - 0.5) / 3.0
-        rows.append({"R": R, "cells": wl.cells, "tau": wl.tau_mo, "Re": wl.u_in * R / nu,
+        rows.append({"R": R, "cells": wl.cells, "tau": wl.tau_mo, "eps_h": wl.eps_h, "Re": wl.u_in * R / nu,
                      "steps": n_spin + n_avg, "thrust": T, "C_T": thrust_coefficient(T, R, wl.u_in),
                      # wall units per lattice spacing, u_tau / nu, of the last step: median over the wall
                      # cells (a wall cell sits 0.5 to 1 spacing from the wall)
@@ -133,8 +143,9 @@ if __name__ == "__main__":
     ap.add_argument("--spinup", type=float, default=3.0, help="revolutions before averaging")
     ap.add_argument("--average", type=float, default=2.0, help="revolutions averaged")
     ap.add_argument("--no-wall-model", action="store_true", help="porous blades without the wall function")
-    ap.add_argument("--ladder", default="reynolds", choices=["reynolds", "yplus"],
-                    help="hold the Reynolds number (reynolds) or the first cell's y+ (yplus) across R")
+    ap.add_argument("--ladder", default="reynolds", choices=["reynolds", "yplus", "interface"],
+                    help="hold the Reynolds number (reynolds), the first cell's y+ (yplus), or y+ and the "
+                         "porosity transition relative to the rotor (interface) across R")
     args = ap.parse_args()
     radii = tuple(int(v) for v in args.radii.split(","))
     res = run_study(radii, args.spinup, args.average, wall_model=not args.no_wall_model, ladder=args.ladder,

@@ -43,7 +43,8 @@ bool valid_config(const hl_config* c) {
     if (c->wm_maxit < 0 || c->wm_maxit > 1000 || !(c->wm_ysample > 0.0)) return false;
     if (c->mass_check_every < 0) return false;
     if (c->layout < 0 || c->layout > 1) return false;
-    if (c->halo_lo < 0 || c->halo_lo > 1 || c->halo_hi < 0 || c->halo_hi > 1 || c->z_offset < 0) return false;
+    // z_offset may be -1: the first slab of a periodic z decomposition starts with the last slab's plane
+    if (c->halo_lo < 0 || c->halo_lo > 1 || c->halo_hi < 0 || c->halo_hi > 1) return false;
     if ((c->halo_lo || c->halo_hi) && c->layout != 0) return false;   // slabs use the AA pattern
     if (c->nz - c->halo_lo - c->halo_hi < 1) return false;
     return true;

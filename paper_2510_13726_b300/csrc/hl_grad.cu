@@ -433,15 +433,17 @@ __global__ void __launch_bounds__(128) adj_wall_kernel(const StepArgs a, const A
         const bool far = phi > 0.5f;
         const float y1 = far ? phi : 0.5f;
         const float ys = a.wmYs;
-        const float xs[3] = {x + ys * n[0], y + ys * n[1], z + ys * n[2]};
+        // the forward wall model's corner and weights (from the offset y_s n)
+        const float dv[3] = {ys * n[0], ys * n[1], ys * n[2]};
+        const int xc[3] = {x, y, z};
         int i0[3];
         float t[3];
         bool clamped[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const float fl = floorf(xs[k]);
-            i0[k] = (int)fl;
-            t[k] = xs[k] - fl;
+            const float fl = floorf(dv[k]);
+            i0[k] = xc[k] + (int)fl;
+            t[k] = dv[k] - fl;
             clamped[k] = false;
             if (a.open && k == a.flow_axis) {
                 if (i0[k] < 0) { i0[k] = 0; t[k] = 0.f; clamped[k] = true; }

@@ -26,7 +26,7 @@ constexpr long long WALL_SMALL_BOX = 1LL << 20;
 __device__ __forceinline__ int list_first(void) { return blockIdx.x * blockDim.x + threadIdx.x; }
 __device__ __forceinline__ int list_stride(void) { return gridDim.x * blockDim.x; }
 constexpr int MASS_BLOCKS = 592;     // 4 x 148 SMs
-constexpr int BAND_THREADS = 256;
+constexpr int BAND_THREADS = 128;
 
 // device error word; ERR_GEOMETRY: a wall cell's velocity sample reached
 // outside its rotor box (the blade grid needs more padding around the blade)

@@ -503,15 +503,18 @@ __global__ void __launch_bounds__(128) wall_kernel(const StepArgs a) {
         float n[3];
         rotor_normal(R, which, x, y, z, n);
         const float y1 = phi > 0.5f ? phi : 0.5f;
-        // sampling point x_s = x + y_s n and trilinear fluid velocity there
-        const float xs[3] = {x + a.wmYs * n[0], y + a.wmYs * n[1], z + a.wmYs * n[2]};
+        // sampling point x_s = x + y_s n and trilinear fluid velocity there; the
+        // corner and the weights come from the offset y_s n alone (x is an
+        // integer), so they do not depend on where the lattice's origin lies
+        const float dv[3] = {a.wmYs * n[0], a.wmYs * n[1], a.wmYs * n[2]};
+        const int xc[3] = {x, y, z};
         int i0[3];
         float t[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const float fl = floorf(xs[k]);
-            i0[k] = (int)fl;
-            t[k] = xs[k] - fl;
+            const float fl = floorf(dv[k]);
+            i0[k] = xc[k] + (int)fl;
+            t[k] = dv[k] - fl;
             if (a.open && k == a.flow_axis) {
                 if (i0[k] < 0) { i0[k] = 0; t[k] = 0.f; }
                 if (i0[k] > a.n[k] - 2) { i0[k] = a.n[k] - 2; t[k] = 1.f; }
@@ -1028,9 +1031,11 @@ static cudaError_t launch_band_t(const StepArgs& a, cudaStream_t s) {
     }
     constexpr int WPB = BAND_THREADS / 32;
     long long blocks = (maxrows + WPB - 1) / WPB;
-    // at most two blocks per SM: the embedding runs beside the bulk launch, and
-    // fewer blocks leave it more of the GPU (rotor256 step 0.797 -> 0.790 ms)
-    if (blocks > 148 * 2) blocks = 148 * 2;
+    // at most four 128-thread blocks per SM: the embedding runs beside the
+    // bulk launch, and fewer blocks leave it more of the GPU (rotor256 step
+    // 0.797 -> 0.790 ms with two 256-thread blocks); a 128-thread block of 48
+    // registers fits what one retiring bulk block frees (rotor128 40 -> 33 us)
+    if (blocks > 148 * 4) blocks = 148 * 4;
     if (blocks < 1) blocks = 1;
     band_kernel<<<dim3((unsigned)blocks, a.nrot), BAND_THREADS, 0, s>>>(a);
     return cudaGetLastError();

@@ -272,9 +272,12 @@ def test_gradient_study_128x128x256_against_finite_differences(P):
 
     Step sizes from an h-sweep of this workload: the pitch difference falls
     onto the adjoint as h shrinks (relative gap 1.1e-2 at h = 1e-3, 2.0e-3 at
-    1e-4, 2.6e-4 at 3e-5, 3.6e-5 at 1e-5: the trilinear blade grid's kinks
-    make J only piecewise smooth in the pitch), so h = 1e-5 is the converged
-    difference, held to 1e-3.  A single cell's d0 moves J by ~1e-4 per unit,
+    1e-4, 2.6e-4 at 3e-5: the trilinear blade grid's kinks make J only
+    piecewise smooth in the pitch) until the forward's rounding noise, which
+    grows like 1/h, takes over (at h = 1e-5 one run gave 3.6e-5, another
+    9.7e-4 on rounding-level changes of the collision).  The test holds the
+    adjoint to D(3e-5) within 1e-3, or within twice the noise measured as
+    |D(3e-5) - D(3.3e-5)| if that is larger.  A single cell's d0 moves J by ~1e-4 per unit,
     so its difference carries the forward's rounding noise: the median error
     over the 32 cells follows n/h + c h^2 (n ~ 6e-6, c ~ 7; 6.1e-3 at h =
     0.03, 1.4e-3 at 0.01, 2.7e-3 at 0.003, 5.7e-3 at 0.001).  The test takes
@@ -306,10 +309,10 @@ def test_gradient_study_128x128x256_against_finite_differences(P):
         return Fa[0, wl.flow_axis]
 
     assert abs(Jrun() - J) <= 1e-12 * abs(J)
-    fd = {h: (Jrun(h) - Jrun(-h)) / (2 * h) for h in (3e-5, 1e-5)}
+    fd = {h: (Jrun(h) - Jrun(-h)) / (2 * h) for h in (1e-4, 3.3e-5, 3e-5, 1e-5)}
     print("dJ/dpitch adjoint %.7f; central differences %s" % (gp[0], {h: round(v, 7) for h, v in fd.items()}))
-    assert abs(gp[0] - fd[1e-5]) <= 1e-3 * abs(fd[1e-5])
-    assert abs(gp[0] - fd[1e-5]) <= abs(gp[0] - fd[3e-5]) + 1e-4 * abs(fd[1e-5])   # converging onto it
+    noise_p = abs(fd[3e-5] - fd[3.3e-5]) / abs(fd[3e-5])
+    assert abs(gp[0] - fd[3e-5]) <= max(1e-3, 2 * noise_p) * abs(fd[3e-5])
     rng = np.random.default_rng(11)
     c, R = wl.rotors[0].center, wl.rotors[0].radius
     cells = []

@@ -155,19 +155,21 @@ def test_convergence_study_workload_parity(P):
 def test_convergence_study_driver(P):
     """The grid-convergence driver on three resolutions of each ladder (one
     revolution of spin-up, one averaged): the Reynolds ladder scales the
-    viscosity with R, the y+ ladder keeps it; finite thrust coefficients and
+    viscosity with R, the y+ ladder keeps it, the interface ladder keeps it
+    and scales the porosity transition with R; finite thrust coefficients and
     the derived orders and index."""
     from paper_2510_13726_b300 import convergence as C
-    for ladder in ("reynolds", "yplus"):
+    for ladder in ("reynolds", "yplus", "interface"):
         res = C.run_study(radii=(16, 32, 64), revolutions_spinup=1.0, revolutions_avg=1.0, ladder=ladder)
         rows = res["resolutions"]
         ct = [r["C_T"] for r in rows]
         assert all(np.isfinite(ct)) and all(c > 0 for c in ct)
         assert np.isfinite(res["apparent_order"]) and res["gci_finest"] >= 0.0
         taus = [r["tau"] for r in rows]
-        if ladder == "yplus":
+        if ladder in ("yplus", "interface"):
             assert taus == [0.5005] * 3
             assert rows[2]["Re"] == pytest.approx(4 * rows[0]["Re"])
+            assert [r["eps_h"] for r in rows] == ([1.0, 2.0, 4.0] if ladder == "interface" else [2.0] * 3)
         else:
             assert taus[2] - 0.5 == pytest.approx(4 * (taus[0] - 0.5))
             assert rows[2]["Re"] == pytest.approx(rows[0]["Re"])

@@ -51,6 +51,7 @@ class Workload:
     n_modes: int = 64
     rotors: list = dataclasses.field(default_factory=list)
     note: str = ""
+    grid_margin: float = 4.0         # blade-grid padding around the blade (cells)
 
     @property
     def cells(self) -> int:
@@ -66,7 +67,7 @@ class Workload:
         out = []
         for r in self.rotors:
             if r.radius not in cache:
-                cache[r.radius] = make_blade_grid(radius=r.radius)
+                cache[r.radius] = make_blade_grid(radius=r.radius, margin=self.grid_margin)
             out.append(cache[r.radius])
         return out
 
