@@ -189,7 +189,7 @@ def run_reference(args):
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one bulk collide
 # launch of the rotor256 step from one ncu capture; reported only while the
 # kernel sources hash to the value they had at the capture (else null)
-NCU_TRAFFIC = {"source_sha": "ea52b1fd83838e70", "bytes_per_launch": 4872314368}
+NCU_TRAFFIC = {"source_sha": "2049e52963182aa7", "bytes_per_launch": 4871713280}
 
 
 def inflow_planes_pinned(wl, t0, n, dev):

@@ -157,6 +157,13 @@ StepArgs make_args(const hl_lattice* lat) {
         a.rot[k].cpD = (float)std::cos(ps);
         a.rot[k].spD = (float)std::sin(ps);
         a.rot[k].frozen = lat->frozen ? 1 : 0;
+        // the cell lists and counters of this step's parity
+        const int p = (int)(lat->t & 1);
+        a.rot[k].list = reinterpret_cast<int*>(R.ws + R.L.list[p]);
+        a.rot[k].wlist = reinterpret_cast<int*>(R.ws + R.L.wlist[p]);
+        a.rot[k].wphi = reinterpret_cast<float*>(R.ws + R.L.wphi[p]);
+        a.rot[k].wwhich = reinterpret_cast<signed char*>(R.ws + R.L.wwhich[p]);
+        a.rot[k].count = R.dev.count + 2 * p;
     }
     set_shifted_bases(&a, c.q, store_bytes(c.storage));   // needs n and nxy
     return a;
@@ -308,6 +315,10 @@ hl_status hl_lattice_init(hl_lattice** out, const hl_config* cfg, void* d_worksp
                  cudaEventCreateWithFlags(&lat->ev_box[k], cudaEventDisableTiming) == cudaSuccess;
         ok = ok && cudaEventCreateWithFlags(&lat->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
              cudaEventCreateWithFlags(&lat->ev_join, cudaEventDisableTiming) == cudaSuccess;
+        ok = ok && cudaStreamCreateWithPriority(&lat->fst, cudaStreamNonBlocking, hi) == cudaSuccess;
+        for (int k = 0; ok && k < 2; ++k)
+            ok = cudaEventCreateWithFlags(&lat->ev_force[k], cudaEventDisableTiming) == cudaSuccess;
+        ok = ok && cudaEventCreateWithFlags(&lat->ev_join_f, cudaEventDisableTiming) == cudaSuccess;
         if (!ok) { hl_destroy(lat); return HL_ERR_CUDA; }
         lat->have_aux = true;
     }
@@ -431,10 +442,11 @@ hl_status hl_set_rotor(hl_lattice* lat, int* rotor_id, const hl_rotor_geometry* 
     D.wm = reinterpret_cast<float*>(R.ws + L.wm);
     D.utau = reinterpret_cast<double*>(R.ws + L.utau);
     D.active = reinterpret_cast<uint8_t*>(R.ws + L.active);
-    D.list = reinterpret_cast<int*>(R.ws + L.list);
-    D.wlist = reinterpret_cast<int*>(R.ws + L.wlist);
-    D.wphi = reinterpret_cast<float*>(R.ws + L.wphi);
-    D.wwhich = reinterpret_cast<signed char*>(R.ws + L.wwhich);
+    // set 0 of the cell lists; make_args selects the set of the step's parity
+    D.list = reinterpret_cast<int*>(R.ws + L.list[0]);
+    D.wlist = reinterpret_cast<int*>(R.ws + L.wlist[0]);
+    D.wphi = reinterpret_cast<float*>(R.ws + L.wphi[0]);
+    D.wwhich = reinterpret_cast<signed char*>(R.ws + L.wwhich[0]);
     D.count = reinterpret_cast<int*>(R.ws + L.count);
     D.done = reinterpret_cast<unsigned*>(R.ws + L.done);
     D.partial = reinterpret_cast<double*>(R.ws + L.partial);
@@ -492,7 +504,7 @@ static hl_status step_serial(hl_lattice* lat, const StepArgs& a0, bool with_forc
             HL_CUDA(lat, launch_evolve(a, st));
         } else {
             for (int k = 0; k < lat->nrot; ++k)
-                HL_CUDA(lat, cudaMemsetAsync(lat->rot[k].dev.count, 0, 2 * sizeof(int), st));
+                HL_CUDA(lat, cudaMemsetAsync(lat->rot[k].dev.count, 0, COUNT_BYTES, st));
         }
     }
     return HL_OK;
@@ -516,7 +528,12 @@ static hl_status step_overlap(hl_lattice* lat, const StepArgs& a0, bool with_for
     HL_CUDA(lat, launch_collide(Q, S, a, us));
     HL_CUDA(lat, prof_mark(lat, 1, us));
     HL_CUDA(lat, cudaEventRecord(lat->ev_bulk[p], us));
-    // aux stream: embedding, wall model, box collision, force
+    // aux stream: embedding, wall model, box collision; the force reduction
+    // and the driven-rotor update follow on the third stream.  A driven
+    // rotor's frames come from the previous step's update.
+    bool driven = false;
+    for (int k = 0; k < lat->nrot; ++k) driven = driven || lat->rot[k].driven;
+    if (driven) HL_CUDA(lat, cudaStreamWaitEvent(ax, lat->ev_force[q], 0));
     HL_CUDA(lat, prof_mark(lat, 0, ax));
     HL_CUDA(lat, launch_band(Q, S, a, ax));
     HL_CUDA(lat, launch_band_strain(Q, S, a, ax));
@@ -526,7 +543,10 @@ static hl_status step_overlap(hl_lattice* lat, const StepArgs& a0, bool with_for
         HL_CUDA(lat, launch_wall(Q, S, a, ax));
         HL_CUDA(lat, prof_mark(lat, 4, ax));
     }
+    // the box collision overwrites the populations the previous step's force
+    // reduction reads (and the bulk launch's boundary slots)
     HL_CUDA(lat, cudaStreamWaitEvent(ax, lat->ev_bulk[q], 0));
+    HL_CUDA(lat, cudaStreamWaitEvent(ax, lat->ev_force[q], 0));
     a.part = 2;
     for (int k = 0; k < lat->nrot; ++k) {
         a.part_rotor = k;
@@ -537,13 +557,16 @@ static hl_status step_overlap(hl_lattice* lat, const StepArgs& a0, bool with_for
     HL_CUDA(lat, cudaEventRecord(lat->ev_box[p], ax));
     a.part = 0;
     if (with_force) {
-        HL_CUDA(lat, prof_mark(lat, 2, ax));
-        HL_CUDA(lat, launch_force(Q, S, a, ax));
-        HL_CUDA(lat, prof_mark(lat, 2, ax));
-        HL_CUDA(lat, launch_evolve(a, ax));
+        cudaStream_t fs = lat->fst;
+        HL_CUDA(lat, cudaStreamWaitEvent(fs, lat->ev_box[p], 0));
+        HL_CUDA(lat, prof_mark(lat, 2, fs));
+        HL_CUDA(lat, launch_force(Q, S, a, fs));
+        HL_CUDA(lat, prof_mark(lat, 2, fs));
+        HL_CUDA(lat, launch_evolve(a, fs));
+        HL_CUDA(lat, cudaEventRecord(lat->ev_force[p], fs));
     } else {
         for (int k = 0; k < lat->nrot; ++k)
-            HL_CUDA(lat, cudaMemsetAsync(lat->rot[k].dev.count, 0, 2 * sizeof(int), ax));
+            HL_CUDA(lat, cudaMemsetAsync(lat->rot[k].dev.count, 0, COUNT_BYTES, ax));
     }
     return HL_OK;
 }
@@ -595,9 +618,11 @@ hl_status hl_step_async(hl_lattice* lat, int n) {
         }
     }
     if (two && n > 0) {
-        // the lattice stream sees the completed aux work
+        // the lattice stream sees the completed aux and force-stream work
         HL_CUDA(lat, cudaEventRecord(lat->ev_join, lat->aux));
         HL_CUDA(lat, cudaStreamWaitEvent(lat->stream, lat->ev_join, 0));
+        HL_CUDA(lat, cudaEventRecord(lat->ev_join_f, lat->fst));
+        HL_CUDA(lat, cudaStreamWaitEvent(lat->stream, lat->ev_join_f, 0));
     }
     return HL_OK;
 }
@@ -999,13 +1024,17 @@ void hl_destroy(hl_lattice* lat) {
     for (auto& v : lat->prof_ev)
         for (cudaEvent_t e : v) cudaEventDestroy(e);
     if (lat->aux) cudaStreamSynchronize(lat->aux);
+    if (lat->fst) cudaStreamSynchronize(lat->fst);
     for (int k = 0; k < 2; ++k) {
         if (lat->ev_bulk[k]) cudaEventDestroy(lat->ev_bulk[k]);
         if (lat->ev_box[k]) cudaEventDestroy(lat->ev_box[k]);
+        if (lat->ev_force[k]) cudaEventDestroy(lat->ev_force[k]);
     }
     if (lat->ev_fork) cudaEventDestroy(lat->ev_fork);
     if (lat->ev_join) cudaEventDestroy(lat->ev_join);
+    if (lat->ev_join_f) cudaEventDestroy(lat->ev_join_f);
     if (lat->aux) cudaStreamDestroy(lat->aux);
+    if (lat->fst) cudaStreamDestroy(lat->fst);
     delete lat;
 }
 

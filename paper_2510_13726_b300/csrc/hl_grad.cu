@@ -900,6 +900,8 @@ hl_status join_aux(hl_lattice* lat) {
     if (!(lat->have_aux && lat->nrot > 0)) return HL_OK;
     HL_CUDA(lat, cudaEventRecord(lat->ev_join, lat->aux));
     HL_CUDA(lat, cudaStreamWaitEvent(lat->stream, lat->ev_join, 0));
+    HL_CUDA(lat, cudaEventRecord(lat->ev_join_f, lat->fst));
+    HL_CUDA(lat, cudaStreamWaitEvent(lat->stream, lat->ev_join_f, 0));
     return HL_OK;
 }
 
@@ -1043,7 +1045,7 @@ static hl_status grad_aa(hl_lattice* lat, int steps, int avg_last, int ckpt_ever
         // recompute the segment out of place, recording each step's small state;
         // the cell lists start empty (the last reverse step left them filled)
         if ((rc = ckpt_copy(lat, ck, false, false)) != HL_OK) return rc;
-        for (int k = 0; k < lat->nrot; ++k) HL_CUDA(lat, cudaMemsetAsync(lat->rot[k].dev.count, 0, 2 * sizeof(int), st));
+        for (int k = 0; k < lat->nrot; ++k) HL_CUDA(lat, cudaMemsetAsync(lat->rot[k].dev.count, 0, COUNT_BYTES, st));
         if ((rc = fork_aux(lat)) != HL_OK) return rc;
         for (int jj = 0; jj < L; ++jj) {
             const long long t = ts + jj;
@@ -1063,7 +1065,7 @@ static hl_status grad_aa(hl_lattice* lat, int steps, int avg_last, int ckpt_ever
                 HL_CUDA(lat, launch_band_strain(Q, S, a, bs));
                 if (lat->cfg.wall_model) HL_CUDA(lat, launch_wall(Q, S, a, bs));
                 for (int k = 0; k < lat->nrot; ++k)
-                    HL_CUDA(lat, cudaMemsetAsync(lat->rot[k].dev.count, 0, 2 * sizeof(int), bs));
+                    HL_CUDA(lat, cudaMemsetAsync(lat->rot[k].dev.count, 0, COUNT_BYTES, bs));
             }
         }
         // both halves of the reverse step read states written by both halves
@@ -1113,7 +1115,7 @@ static hl_status grad_aa(hl_lattice* lat, int steps, int avg_last, int ckpt_ever
                     D.pacc = ra[k].pacc;
                     D.wT = force_on ? (float)(w_thrust[k] / na) : 0.0f;
                     D.wQ = force_on ? (float)(w_torque[k] / na) : 0.0f;
-                    HL_CUDA(lat, cudaMemsetAsync(lat->rot[k].dev.count, 0, 2 * sizeof(int), bs));
+                    HL_CUDA(lat, cudaMemsetAsync(lat->rot[k].dev.count, 0, COUNT_BYTES, bs));
                     // only this step's wall cells hand an adjoint to the previous step's u_tau
                     HL_CUDA(lat, cudaMemsetAsync(ra[k].gut[uc ^ 1], 0, sizeof(double) * D.box_cells, bs));
                 }
@@ -1131,7 +1133,7 @@ static hl_status grad_aa(hl_lattice* lat, int steps, int avg_last, int ckpt_ever
     }
     // the lattice ends where the forward pass ended
     if ((rc = ckpt_copy(lat, ws + G.ck + (size_t)G.n_ck * ckb, false, true)) != HL_OK) return rc;
-    for (int k = 0; k < lat->nrot; ++k) HL_CUDA(lat, cudaMemsetAsync(lat->rot[k].dev.count, 0, 2 * sizeof(int), st));
+    for (int k = 0; k < lat->nrot; ++k) HL_CUDA(lat, cudaMemsetAsync(lat->rot[k].dev.count, 0, COUNT_BYTES, st));
     for (int k = 0; k < lat->nrot; ++k) {
         double pacc[PACC_SLOTS];
         HL_CUDA(lat, cudaMemcpyAsync(pacc, ra[k].pacc, sizeof pacc, cudaMemcpyDeviceToHost, st));

@@ -44,8 +44,15 @@ inline Layout lattice_layout(const hl_config& c) {
 }
 
 struct RotorLayout {
-    size_t sdf, d, flags, wm, utau, active, list, wlist, wphi, wwhich, count, done, partial, acc, drive, total;
+    size_t sdf, d, flags, wm, utau, active, list[2], wlist[2], wphi[2], wwhich[2], count, done, partial, acc, drive,
+        total;
 };
+
+// The cell lists of the embedding (force cells, wall cells and their data)
+// are kept twice, by step parity, so that the next step's embedding can run
+// while this step's force reduction still reads its lists; the counters of
+// both sets are four ints from `count` (set p at count + 2 p).
+constexpr size_t COUNT_BYTES = 4 * sizeof(int);
 
 inline RotorLayout rotor_layout(long long ngrid, long long box) {
     RotorLayout L{};
@@ -56,11 +63,13 @@ inline RotorLayout rotor_layout(long long ngrid, long long box) {
     L.wm = o; o = align_up(o + sizeof(float) * 9 * box);
     L.utau = o; o = align_up(o + sizeof(double) * box);
     L.active = o; o = align_up(o + box);
-    L.list = o; o = align_up(o + sizeof(int) * box);
-    L.wlist = o; o = align_up(o + sizeof(int) * box);
-    L.wphi = o; o = align_up(o + sizeof(float) * box);
-    L.wwhich = o; o = align_up(o + box);
-    L.count = o; o = align_up(o + 2 * sizeof(int));
+    for (int p = 0; p < 2; ++p) {
+        L.list[p] = o; o = align_up(o + sizeof(int) * box);
+        L.wlist[p] = o; o = align_up(o + sizeof(int) * box);
+        L.wphi[p] = o; o = align_up(o + sizeof(float) * box);
+        L.wwhich[p] = o; o = align_up(o + box);
+    }
+    L.count = o; o = align_up(o + COUNT_BYTES);
     L.done = o; o = align_up(o + sizeof(unsigned));
     L.partial = o; o = align_up(o + sizeof(double) * 6 * FORCE_BLOCKS);
     L.acc = o; o = align_up(o + sizeof(double) * 12);
@@ -106,6 +115,10 @@ struct hl_lattice {
     cudaStream_t aux;
     cudaEvent_t ev_bulk[2], ev_box[2], ev_fork, ev_join;
     bool have_aux;
+    // third stream: the force reduction (and the driven-rotor update) of a
+    // step, beside the next step's embedding and wall model
+    cudaStream_t fst;
+    cudaEvent_t ev_force[2], ev_join_f;
     // per-kernel event timing (hl_profile_begin / hl_profile_end)
     bool prof_on;
     int prof_cap;

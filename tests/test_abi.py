@@ -97,3 +97,23 @@ def test_null_and_invalid_handles_are_rejected(L):
     assert L.hl_forces(None, None, None, 0) == -1
     assert L.hl_last_error(None) == b"null handle"
     assert L.hl_debug_collide(20, 1, None, None, None, None, None, 0.6, 0.1, None, None) == -1
+
+
+def test_slab_configuration_rules(L):
+    """Halo planes need the AA layout and at least one owned plane; a
+    periodic slab may start at z_offset -1 (host-side validation only)."""
+    cfg = _lib.HlConfig()
+    L.hl_config_defaults(C.byref(cfg))
+    cfg.nx, cfg.ny, cfg.nz = 8, 8, 6
+    size = C.c_size_t()
+    assert L.hl_workspace_size(C.byref(cfg), C.byref(size)) == 0
+    plain = size.value
+    cfg.halo_lo, cfg.halo_hi, cfg.z_offset = 1, 1, -1
+    assert L.hl_workspace_size(C.byref(cfg), C.byref(size)) == 0 and size.value == plain
+    cfg.layout = 1
+    assert L.hl_workspace_size(C.byref(cfg), C.byref(size)) == -1      # slabs use the AA pattern
+    cfg.layout = 0
+    cfg.halo_lo = 2
+    assert L.hl_workspace_size(C.byref(cfg), C.byref(size)) == -1
+    cfg.halo_lo, cfg.nz = 1, 2
+    assert L.hl_workspace_size(C.byref(cfg), C.byref(size)) == -1      # nz < 3

@@ -79,6 +79,14 @@ def test_slabs_with_turbulent_inflow_and_16bit_storage(P):
     _compare(P, wl, [0, 20 if 20 <= a else a, b + 1, 96], 60, storage="bf16s")
 
 
+def test_slabs_d3q27(P):
+    """D3Q27 (nine populations cross each face): three slabs, rotor box next
+    to a cut, FP16 storage."""
+    wl = dataclasses.replace(W.workload("rotor48"), q=27)
+    a, b = _box_z(wl)
+    _compare(P, wl, [0, b + 1, 70, 96], 60, storage="f16s")
+
+
 def test_periodic_slabs_flow_along_x(P):
     """Flow along x with z periodic (two rotors side by side across z, as the
     wind farm's columns): two slabs, each wrapping onto the other.  nx is odd,
