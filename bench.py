@@ -222,10 +222,13 @@ def inflow_planes_pinned(wl, t0, n, dev):
     return out
 
 
-def bulk_kernel_name(wl) -> str:
-    """The kernel of the bulk collide-and-stream launch: x-adjacent cell pairs
-    in packed FP32x2 arithmetic when nx is even, one cell per thread otherwise."""
-    return "collide_pair_kernel" if wl.nx % 2 == 0 else "collide_kernel"
+def bulk_kernel_name(wl, layout="aa") -> str:
+    """The kernel of the bulk collide-and-stream launch: cell pairs in packed
+    FP32x2 arithmetic when nx is even (x-adjacent pairs; (x, x + nx/2) in the
+    AA layout with x halves), one cell per thread otherwise."""
+    if wl.nx % 2:
+        return "collide_kernel"
+    return "collide_halves_kernel" if layout == "aa_halves" else "collide_pair_kernel"
 
 
 def kernel_source_sha():
@@ -467,7 +470,7 @@ def run_cuda(args):
                        "rotors": len(wl.rotors), "parallelism": "single GPU",
                        "l2": "no flush: the populations (%.2f GB) exceed the 126 MB L2" %
                              (wl.cells * wl.q * (4 if args.storage == "f32" else 2) / 1e9)},
-            "roofline": {"bound": "hbm", "kernel": bulk_kernel_name(wl), "achieved": round(achieved, 1),
+            "roofline": {"bound": "hbm", "kernel": bulk_kernel_name(wl, args.layout), "achieved": round(achieved, 1),
                          "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                          "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
                          else "fallback", "traffic": traffic,
@@ -507,13 +510,13 @@ def run_cuda(args):
     return 0
 
 
-def timed_run(wl, storage, steps, warmup, dev):
+def timed_run(wl, storage, steps, warmup, dev, layout="aa"):
     """MLUPS of `steps` steps of a workload (CUDA events on the lattice stream)
     and the per-launch roofline of its collide-and-stream launch."""
     import torch
     from paper_2510_13726_b300 import Lattice
     from paper_2510_13726_b300.perf import collide_bytes
-    lat = Lattice.from_workload(wl, storage=storage, device=dev)
+    lat = Lattice.from_workload(wl, storage=storage, layout=layout, device=dev)
     lat.step(warmup)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -535,7 +538,7 @@ def timed_run(wl, storage, steps, warmup, dev):
     lat.close()
     del lat
     torch.cuda.empty_cache()
-    return {"MLUPS": round(wl.cells / ms / 1e3, 1), "ms_per_step": round(ms, 4),
+    return {"layout": layout, "MLUPS": round(wl.cells / ms / 1e3, 1), "ms_per_step": round(ms, 4),
             "collide_gbs": round(gbs, 1), "collide_frac": round(gbs / peak, 4),
             "thrust_last": [round(float(f[wl.flow_axis]), 6) for f in F],
             "torque_last": [round(float(m[wl.flow_axis]), 6) for m in M]}
@@ -544,22 +547,25 @@ def timed_run(wl, storage, steps, warmup, dev):
 def storage_study(dev, steps):
     """FP32 vs FP16 / BF16 storage: the D3Q27 512x512x1024 rotor (R = 128,
     TSR 7) and the D3Q19 256x256x512 benchmark rotor (R = 64, TSR 6, 5 %
-    turbulence; at least 200 steps)."""
+    turbulence; at least 200 steps).  Each storage form in its faster
+    layout: FP32 in the AA layout, 16-bit storage in the AA layout with x
+    halves (every bulk access aligned; the plain AA layout is reported
+    beside it)."""
     import workloads as W
-    wl = W.workload("rotor1024_q27")
-    out = {"workload": "rotor1024_q27: 512x512x1024 D3Q27, R=128 NACA4412 rotor, TSR 7", "steps": steps}
-    for st in ("f32", "f16s", "bf16s"):
-        out[st] = timed_run(wl, st, steps, 5, dev)
-    for st in ("f16s", "bf16s"):
-        out[f"ratio_{st}_over_f32"] = round(out[st]["MLUPS"] / out["f32"]["MLUPS"], 3)
-    wl19 = W.workload("rotor256")
-    s19 = max(steps, 200)
-    d19 = {"workload": "rotor256: 256x256x512 D3Q19, R=64 NACA4412 rotor, TSR 6, 5% turbulence", "steps": s19}
-    for st in ("f32", "f16s", "bf16s"):
-        d19[st] = timed_run(wl19, st, s19, 10, dev)
-    for st in ("f16s", "bf16s"):
-        d19[f"ratio_{st}_over_f32"] = round(d19[st]["MLUPS"] / d19["f32"]["MLUPS"], 3)
-    out["d3q19"] = d19
+
+    def study(wl, desc, n, warm):
+        out = {"workload": desc, "steps": n, "f32": timed_run(wl, "f32", n, warm, dev)}
+        for st in ("f16s", "bf16s"):
+            out[st] = timed_run(wl, st, n, warm, dev, layout="aa_halves")
+            out[f"ratio_{st}_over_f32"] = round(out[st]["MLUPS"] / out["f32"]["MLUPS"], 3)
+        out["aa_layout"] = {st: timed_run(wl, st, n, warm, dev) for st in ("f16s", "bf16s")}
+        return out
+
+    out = study(W.workload("rotor1024_q27"), "rotor1024_q27: 512x512x1024 D3Q27, R=128 NACA4412 rotor, TSR 7",
+                steps, 5)
+    out["d3q19"] = study(W.workload("rotor256"),
+                         "rotor256: 256x256x512 D3Q19, R=64 NACA4412 rotor, TSR 6, 5% turbulence",
+                         max(steps, 200), 10)
     return out
 
 
@@ -710,8 +716,8 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
     ap.add_argument("--workload", default="rotor256")
     ap.add_argument("--storage", default="f32", choices=["f32", "f16s", "bf16s"])
-    ap.add_argument("--layout", default="aa", choices=["aa", "esotwist"],
-                    help="population layout: AA pattern or esoteric twist")
+    ap.add_argument("--layout", default="aa", choices=["aa", "esotwist", "aa_halves"],
+                    help="population layout: AA pattern, esoteric twist, or AA pattern with x halves")
     ap.add_argument("--cpu-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the 16-bit storage study, the farm run and the gradient run")

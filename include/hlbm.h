@@ -88,7 +88,12 @@ typedef int hl_status;
  *                  steps its neighbours'), 1 the esoteric twist (every step
  *                  a cell reads and writes the links to its +x/+y/+z
  *                  neighbours, the slot of each link alternating with the
- *                  step parity); same results, hl_grad needs 0
+ *                  step parity), 2 the AA pattern with each x row of a slot
+ *                  stored as its two halves interleaved (cell x < nx/2 at
+ *                  position 2x, cell x >= nx/2 at 2(x - nx/2) + 1; nx even):
+ *                  the bulk launch then moves the cell pair (x, x + nx/2)
+ *                  with one aligned access per slot at both step parities.
+ *                  Same cell model; hl_grad takes 0 and 1 (HL_ERR_STATE for 2)
  *  halo_lo, halo_hi  slab of a lattice decomposed along z (the domain
  *                  decomposition of the paper's multi-GPU runs, Sec. 5): 1
  *                  makes the plane z = 0 (halo_lo) or z = nz - 1 (halo_hi) a
@@ -99,7 +104,7 @@ typedef int hl_status;
  *                  inlet belongs to the first slab, the outlet to the last).
  *                  Every odd step is bracketed by hl_halo_export /
  *                  hl_halo_import of each halo face (see there).  Needs
- *                  layout 0; hl_grad rejects slabs (HL_ERR_STATE).
+ *                  layout 0 or 2; hl_grad rejects slabs (HL_ERR_STATE).
  *  z_offset        global z index of local plane 0 (the synthetic inflow is
  *                  evaluated at global coordinates); 0 for a whole lattice,
  *                  -1 for the first slab of a periodic decomposition

@@ -14,6 +14,8 @@ HL_OK = 0
 STATUS = {0: "HL_OK", -1: "HL_ERR_ARG", -2: "HL_ERR_CUDA", -3: "HL_ERR_NONFINITE",
           -4: "HL_ERR_WORKSPACE", -5: "HL_ERR_STATE", -8: "HL_ERR_MASS", -9: "HL_ERR_GEOMETRY"}
 STORAGE = {"f32": 0, "f16s": 1, "bf16s": 2}
+# population layouts: AA pattern, esoteric twist, AA pattern with each x row stored as interleaved halves
+LAYOUTS = {"aa": 0, "esotwist": 1, "aa_halves": 2}
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int)

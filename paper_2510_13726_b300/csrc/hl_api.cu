@@ -42,10 +42,11 @@ bool valid_config(const hl_config* c) {
     if (c->n_modes < 0 || (c->n_modes > 0 && !c->modes)) return false;
     if (c->wm_maxit < 0 || c->wm_maxit > 1000 || !(c->wm_ysample > 0.0)) return false;
     if (c->mass_check_every < 0) return false;
-    if (c->layout < 0 || c->layout > 1) return false;
+    if (c->layout < 0 || c->layout > 2) return false;
+    if (c->layout == 2 && c->nx % 2) return false;                      // x halves need nx even
     // z_offset may be -1: the first slab of a periodic z decomposition starts with the last slab's plane
     if (c->halo_lo < 0 || c->halo_lo > 1 || c->halo_hi < 0 || c->halo_hi > 1) return false;
-    if ((c->halo_lo || c->halo_hi) && c->layout != 0) return false;   // slabs use the AA pattern
+    if ((c->halo_lo || c->halo_hi) && c->layout == 1) return false;   // slabs use the AA pattern
     if (c->nz - c->halo_lo - c->halo_hi < 1) return false;
     return true;
 }
@@ -61,7 +62,6 @@ void set_shifted_bases(StepArgs* a, int q, int esize) {
     hl_velocity_set(q, c.data(), w.data());
     const int P = (q - 1) / 2;
     for (int s = 0; s < q; ++s) {
-        const long long D = c[3 * s] + (long long)c[3 * s + 1] * a->n[0] + (long long)c[3 * s + 2] * a->nxy;
         const int sbar = s == 0 ? 0 : (s <= P ? s + P : s - P);
         // integer arithmetic on the addresses: the shifted bases may lie
         // outside the buffer, every address formed from them lies inside
@@ -80,6 +80,10 @@ void set_shifted_bases(StepArgs* a, int q, int esize) {
             a->rshift[s] = reinterpret_cast<const void*>(reinterpret_cast<uintptr_t>(a->slot[rs]) + Dn * esize);
             a->wshift[s] = reinterpret_cast<void*>(reinterpret_cast<uintptr_t>(a->wslot[ws]) + Dp * esize);
         } else {
+            // with x halves a cell's x neighbours sit two positions away
+            // (away from the wrap and the seam between the halves)
+            const long long D = (a->xpair ? 2 : 1) * (long long)c[3 * s] + (long long)c[3 * s + 1] * a->n[0] +
+                                (long long)c[3 * s + 2] * a->nxy;
             a->rshift[s] = reinterpret_cast<const void*>(reinterpret_cast<uintptr_t>(a->slot[sbar]) - D * esize);
             a->wshift[s] = reinterpret_cast<void*>(reinterpret_cast<uintptr_t>(a->wslot[s]) + D * esize);
         }
@@ -109,7 +113,9 @@ StepArgs make_args(const hl_lattice* lat) {
     a.nxy = c.nx * c.ny;
     a.nplane = (int)plane_cells(c);
     a.phase = (int)(lat->t & 1);
-    a.layout = c.layout;
+    a.layout = c.layout == 1 ? 1 : 0;
+    a.xpair = c.layout == 2 ? 1 : 0;
+    a.hx = c.nx / 2;
     a.t = lat->t;
     a.flow_axis = c.flow_axis;
     a.open = c.open_boundaries;

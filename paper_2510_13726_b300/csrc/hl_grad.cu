@@ -1153,6 +1153,8 @@ hl_status hl_grad(hl_lattice* lat, int steps, int avg_last, int ckpt_every, cons
     if (!lat) return HL_ERR_ARG;
     if (lat->cfg.halo_lo || lat->cfg.halo_hi)
         return fail(lat, HL_ERR_STATE, "hl_grad: the gradient covers a whole lattice, not a slab");
+    if (lat->cfg.layout == 2)
+        return fail(lat, HL_ERR_STATE, "hl_grad: the AA layout with x halves is not supported (use layout 0)");
     if (lat->cfg.layout == 0)
         return grad_aa(lat, steps, avg_last, ckpt_every, w_thrust, w_torque, J, dJ_dpitch, d_dJ_dd0, d_work, bytes);
     // esoteric twist: the sweep runs on the AA form of the same state (the

@@ -69,7 +69,9 @@ struct StepArgs {
     const float* inflow_plane;  // [3][plane] caller's inflow velocity, null = the synthetic modes
     int tangent;             // band kernel also writes d(porosity)/d(pitch) (reverse sweep)
     int pairs;               // bulk launches take x-adjacent cell pairs (nx even, slot bases 2-element aligned)
-    int layout;              // 0 AA pattern, 1 esoteric twist
+    int layout;              // 0 AA pattern, 1 esoteric twist (an AA lattice with x halves has 0 here)
+    int xpair;               // AA with x halves: cell x of a row stored at 2x (x < hx), 2(x - hx) + 1 (x >= hx)
+    int hx;                  // nx / 2
     int nrot;
     RotorDev rot[MAXROT];
 };

@@ -38,11 +38,19 @@ struct Offs {
     int x[3], y[3], z[3];
 };
 
+// Position of cell x within its row of a population slot.  The AA layout
+// with x halves stores cells x and x + nx/2 side by side (x < nx/2 at 2x,
+// x >= nx/2 at 2(x - nx/2) + 1), so that a shift by one cell along x moves a
+// whole pair of stored values (see collide_halves_kernel).
+__device__ __forceinline__ int xmap(const StepArgs& a, int x) {
+    return a.xpair ? (x < a.hx ? 2 * x : 2 * (x - a.hx) + 1) : x;
+}
+
 __device__ __forceinline__ void make_offs(const StepArgs& a, int x, int y, int z, Offs& o) {
     const int nx = a.n[0], ny = a.n[1], nz = a.n[2], nxy = a.nxy;
-    o.x[0] = x == 0 ? nx - 1 : x - 1;
-    o.x[1] = x;
-    o.x[2] = x == nx - 1 ? 0 : x + 1;
+    o.x[0] = xmap(a, x == 0 ? nx - 1 : x - 1);
+    o.x[1] = xmap(a, x);
+    o.x[2] = xmap(a, x == nx - 1 ? 0 : x + 1);
     o.y[0] = (y == 0 ? ny - 1 : y - 1) * nx;
     o.y[1] = y * nx;
     o.y[2] = (y == ny - 1 ? 0 : y + 1) * nx;
@@ -74,14 +82,14 @@ __device__ __forceinline__ int eso_write_node(const Offs& o, int cx, int cy, int
 // neighbour across an open face wraps: that value is undefined by the scheme
 // and only read for cells on an open boundary plane)
 template <int Q, int S, int PH, int L>
-__device__ __forceinline__ void load_pre(const StepArgs& a, int cell, const Offs& o, float (&g)[Q]) {
+__device__ __forceinline__ void load_pre(const StepArgs& a, const Offs& o, float (&g)[Q]) {
 #pragma unroll
     for (int s = 0; s < Q; ++s) {
         if (L == 1) {
             const int cx = cslot(Q, s, 0), cy = cslot(Q, s, 1), cz = cslot(Q, s, 2);
             g[s] = Store<S>::ld(slot_ptr<Q, S>(a, PH == 0 ? s : oslot(Q, s)) + eso_read_node(o, cx, cy, cz));
         } else if (PH == 0) {
-            g[s] = Store<S>::ld(slot_ptr<Q, S>(a, s) + cell);
+            g[s] = Store<S>::ld(slot_ptr<Q, S>(a, s) + (o.x[1] + o.y[1] + o.z[1]));
         } else {
             const int cx = cslot(Q, s, 0), cy = cslot(Q, s, 1), cz = cslot(Q, s, 2);
             const int src = o.x[1 - cx] + o.y[1 - cy] + o.z[1 - cz];
@@ -117,11 +125,14 @@ __device__ __forceinline__ void collide_cell(const StepArgs& a, int x, int y, in
     // arithmetic): AA odd steps away from the lattice faces; esoteric twist
     // (links towards +x, +y, +z only) away from the upper faces
     constexpr bool eso = L == 1;
+    // (with x halves a shift along x also crosses between the halves at
+    // x = nx/2 - 1 and nx/2)
     const bool shifted = eso ? (x < a.n[0] - 1 && y < a.n[1] - 1 && z < a.n[2] - 1)
                              : (PH == 1 && x > 0 && x < a.n[0] - 1 && y > 0 && y < a.n[1] - 1 && z > 0 &&
-                                z < a.n[2] - 1);
+                                z < a.n[2] - 1 && !(a.xpair && (x == a.hx - 1 || x == a.hx)));
     Offs o;
     make_offs(a, x, y, z, o);
+    const int pc = o.x[1] + o.y[1] + o.z[1];   // the cell's position in a population slot
     float g[Q];
     if (!inlet && !outlet) {
         int rk = -1, bi = 0;
@@ -138,9 +149,9 @@ __device__ __forceinline__ void collide_cell(const StepArgs& a, int x, int y, in
         if (shifted) {
             using T = typename Store<S>::T;
 #pragma unroll
-            for (int s = 0; s < Q; ++s) g[s] = Store<S>::ld(static_cast<const T*>(a.rshift[s]) + cell);
+            for (int s = 0; s < Q; ++s) g[s] = Store<S>::ld(static_cast<const T*>(a.rshift[s]) + pc);
         } else {
-            load_pre<Q, S, PH, L>(a, cell, o, g);
+            load_pre<Q, S, PH, L>(a, o, g);
         }
         float u[3];
         float rho;
@@ -202,7 +213,7 @@ __device__ __forceinline__ void collide_cell(const StepArgs& a, int x, int y, in
         if (shifted) {
             using T = typename Store<S>::T;
 #pragma unroll
-            for (int s = 0; s < Q; ++s) Store<S>::st(static_cast<T*>(a.wshift[s]) + cell, g[s]);
+            for (int s = 0; s < Q; ++s) Store<S>::st(static_cast<T*>(a.wshift[s]) + pc, g[s]);
             return;
         }
 #pragma unroll
@@ -211,7 +222,7 @@ __device__ __forceinline__ void collide_cell(const StepArgs& a, int x, int y, in
             if (eso) {
                 Store<S>::st(wslot_ptr<Q, S>(a, PH == 0 ? oslot(Q, s) : s) + eso_write_node(o, cx, cy, cz), g[s]);
             } else if (PH == 0) {
-                Store<S>::st(wslot_ptr<Q, S>(a, oslot(Q, s)) + cell, g[s]);
+                Store<S>::st(wslot_ptr<Q, S>(a, oslot(Q, s)) + pc, g[s]);
             } else {
                 Store<S>::st(wslot_ptr<Q, S>(a, s) + (o.x[1 + cx] + o.y[1 + cy] + o.z[1 + cz]), g[s]);
             }
@@ -258,7 +269,7 @@ __device__ __forceinline__ void collide_cell(const StepArgs& a, int x, int y, in
             if ((inlet && cas < 0) || (outlet && cas > 0)) continue;
             Store<S>::st(wslot_ptr<Q, S>(a, PH == 0 ? oslot(Q, s) : s) + eso_write_node(o, cx, cy, cz), g[s]);
         } else if (PH == 0) {
-            Store<S>::st(wslot_ptr<Q, S>(a, oslot(Q, s)) + cell, g[s]);
+            Store<S>::st(wslot_ptr<Q, S>(a, oslot(Q, s)) + pc, g[s]);
         } else {
             const int cx = cslot(Q, s, 0), cy = cslot(Q, s, 1), cz = cslot(Q, s, 2);
             const int cas = sel3(ax, cx, cy, cz);
@@ -298,12 +309,9 @@ __global__ void __launch_bounds__(128) collide_kernel(const StepArgs a) {
 // spill), 2-3 % faster for 16-bit storage than the unbounded 72 (56, 9 blocks,
 // spills 60-100 bytes and is slower on every storage); D3Q19 at most 48 (10
 // blocks), 3 % faster for 16-bit storage than the unbounded 56, FP32 unchanged.
+// Does the pair (x, x + 1) of row (y, z) take the packed path?
 template <int Q, int S, int PH, int L>
-__global__ void __launch_bounds__(128, Q == 27 ? 8 : 10) collide_pair_kernel(const StepArgs a) {
-    const int x = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = (int)blockIdx.z + a.z0;     // halo planes of a slab are not collided
-    if (y >= a.n[1] || x >= a.n[0]) return;
+__device__ __forceinline__ bool pair_plain(const StepArgs& a, int x, int y, int z) {
     bool plain = x + 1 < a.n[0];
     for (int k = 0; k < a.nrot; ++k) {
         const RotorDev& R = a.rot[k];
@@ -320,34 +328,15 @@ __global__ void __launch_bounds__(128, Q == 27 ? 8 : 10) collide_pair_kernel(con
     // the y and z neighbours the pair touches must lie inside the lattice
     if (L == 0 && PH == 1 && !(y > 0 && y < a.n[1] - 1 && z > 0 && z < a.n[2] - 1)) plain = false;
     if (L == 1 && !(y < a.n[1] - 1 && z < a.n[2] - 1)) plain = false;
-    if (!plain) {
-        collide_cell<Q, S, PH, false, L>(a, x, y, z);
-        if (x + 1 < a.n[0]) collide_cell<Q, S, PH, false, L>(a, x + 1, y, z);
-        return;
-    }
+    return plain;
+}
+
+// packed collision of a plain pair and its stores (x even, cell = index of x)
+template <int Q, int S, int PH, int L>
+__device__ __forceinline__ void pair_collide_store(const StepArgs& a, int x, int cell, F2 (&g)[Q]) {
     using T = typename Store<S>::T;
-    const int cell = (z * a.n[1] + y) * a.n[0] + x;
-    // periodic x: the first cell's neighbour at x - 1 (AA odd steps) and the
-    // last cell's neighbour at x + 2 (AA odd steps, esoteric twist) lie one
-    // row length away
     const int lo_wrap = (L == 0 && PH == 1 && x == 0) ? a.n[0] : 0;
     const int hi_wrap = ((L == 1 || PH == 1) && x + 2 == a.n[0]) ? -a.n[0] : 0;
-    F2 g[Q];
-#pragma unroll
-    for (int s = 0; s < Q; ++s) {
-        const int cx = cslot(Q, s, 0);
-        if (L == 1) {
-            // f_s over the link at x + max(-c_s, 0): one element off for c_x < 0
-            const T* src = static_cast<const T*>(a.rshift[s]) + cell;
-            if (cx >= 0) g[s] = Store2<S>::ld(src);
-            else g[s] = {make_float2(Store<S>::ld(src), Store<S>::ld(src + 1 + hi_wrap))};
-            continue;
-        }
-        const T* src = PH == 0 ? slot_ptr<Q, S>(a, s) + cell : static_cast<const T*>(a.rshift[s]) + cell;
-        if (PH == 0 || cx == 0) g[s] = Store2<S>::ld(src);
-        else if (cx > 0) g[s] = {make_float2(Store<S>::ld(src + lo_wrap), Store<S>::ld(src + 1))};
-        else g[s] = {make_float2(Store<S>::ld(src), Store<S>::ld(src + 1 + hi_wrap))};
-    }
     F2 u[3];
     const F2 rho = collide_pair<Q>(g, a.tau_mo, a.Ksmag, u);
     if (!(fabsf(rho.v.x) < 1e30f) || !(fabsf(rho.v.y) < 1e30f)) atomicOr(a.err, ERR_NONFINITE);
@@ -376,6 +365,153 @@ __global__ void __launch_bounds__(128, Q == 27 ? 8 : 10) collide_pair_kernel(con
             Store<S>::st(dst + 1, g[s].v.y);
         }
     }
+}
+
+template <int Q, int S, int PH, int L>
+__global__ void __launch_bounds__(128, Q == 27 ? 8 : 10) collide_pair_kernel(const StepArgs a) {
+    const int x = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = (int)blockIdx.z + a.z0;     // halo planes of a slab are not collided
+    if (y >= a.n[1] || x >= a.n[0]) return;
+    if (!pair_plain<Q, S, PH, L>(a, x, y, z)) {
+        collide_cell<Q, S, PH, false, L>(a, x, y, z);
+        if (x + 1 < a.n[0]) collide_cell<Q, S, PH, false, L>(a, x + 1, y, z);
+        return;
+    }
+    using T = typename Store<S>::T;
+    const int cell = (z * a.n[1] + y) * a.n[0] + x;
+    // periodic x: the first cell's neighbour at x - 1 (AA odd steps) and the
+    // last cell's neighbour at x + 2 (AA odd steps, esoteric twist) lie one
+    // row length away
+    const int lo_wrap = (L == 0 && PH == 1 && x == 0) ? a.n[0] : 0;
+    const int hi_wrap = ((L == 1 || PH == 1) && x + 2 == a.n[0]) ? -a.n[0] : 0;
+    F2 g[Q];
+#pragma unroll
+    for (int s = 0; s < Q; ++s) {
+        const int cx = cslot(Q, s, 0);
+        if (L == 1) {
+            // f_s over the link at x + max(-c_s, 0): one element off for c_x < 0
+            const T* src = static_cast<const T*>(a.rshift[s]) + cell;
+            if (cx >= 0) g[s] = Store2<S>::ld(src);
+            else g[s] = {make_float2(Store<S>::ld(src), Store<S>::ld(src + 1 + hi_wrap))};
+            continue;
+        }
+        const T* src = PH == 0 ? slot_ptr<Q, S>(a, s) + cell : static_cast<const T*>(a.rshift[s]) + cell;
+        if (PH == 0 || cx == 0) g[s] = Store2<S>::ld(src);
+        else if (cx > 0) g[s] = {make_float2(Store<S>::ld(src + lo_wrap), Store<S>::ld(src + 1))};
+        else g[s] = {make_float2(Store<S>::ld(src), Store<S>::ld(src + 1 + hi_wrap))};
+    }
+    pair_collide_store<Q, S, PH, L>(a, x, cell, g);
+}
+
+// AA layout with x halves: a thread takes cells t and t + nx/2 of a row,
+// stored side by side (one 8-byte FP32 or 4-byte 16-bit access).  A shift by
+// c_x = +-1 moves both cells to the neighbouring pair position, so every slot
+// is one aligned access at both step parities; only at the periodic wrap
+// (t = 0 reading / writing across x = 0, t = nx/2 - 1 across x = nx - 1)
+// the pair lies at the other end of the row with its two cells exchanged.
+// Rows on a periodic y or z face take the packed path too, with the wrapped
+// row offsets added per slot (a branch uniform over the row's warps).
+// Same cell model as collide_pair_kernel (packed FP32x2 per lane).
+template <int Q, int S, int PH>
+__device__ __forceinline__ bool halves_plain(const StepArgs& a, int t, int y, int z) {
+    const int xs[2] = {t, t + a.hx};
+    bool plain = true;
+    for (int k = 0; k < a.nrot; ++k) {
+        const RotorDev& R = a.rot[k];
+        if ((unsigned)(y - R.lo[1]) < (unsigned)R.n[1] && (unsigned)(z - R.lo[2]) < (unsigned)R.n[2] &&
+            ((unsigned)(xs[0] - R.lo[0]) < (unsigned)R.n[0] || (unsigned)(xs[1] - R.lo[0]) < (unsigned)R.n[0]))
+            plain = false;
+    }
+    if (a.open) {
+        const int na = sel3(a.flow_axis, a.n[0], a.n[1], a.n[2]);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int ca = sel3(a.flow_axis, xs[c], y, z);
+            if ((a.open_lo && ca == 0) || (a.open_hi && ca >= na - 2)) plain = false;
+        }
+    }
+    return plain;
+}
+
+// Periodic offsets of one axis at odd steps: a read with c = +1 (from the
+// plane below) or a write with c = -1 (onto it) crosses the lower face from
+// plane 0 (lo = +n planes), a read with c = -1 or a write with c = +1 the upper
+// face from plane n - 1 (hi = -n planes).
+struct WrapOff {
+    int lo, hi;
+};
+__device__ __forceinline__ int wrap_read(const WrapOff& o, int c) { return c > 0 ? o.lo : (c < 0 ? o.hi : 0); }
+__device__ __forceinline__ int wrap_write(const WrapOff& o, int c) { return c > 0 ? o.hi : (c < 0 ? o.lo : 0); }
+
+template <int Q, int S, int PH, bool YZ>
+__device__ __forceinline__ void halves_packed(const StepArgs& a, int t, int y, int z) {
+    using T = typename Store<S>::T;
+    const int w = (z * a.n[1] + y) * a.n[0] + 2 * t;   // the pair's position in a slot
+    // x: the first pair reads (c_x = +1) and writes (c_x = -1) across x = 0,
+    // the last pair reads (c_x = -1) and writes (c_x = +1) across x = nx - 1,
+    // each at the row's other end with its cells exchanged
+    const WrapOff ox = {t == 0 ? a.n[0] : 0, t == a.hx - 1 ? -a.n[0] : 0};
+    const unsigned sel_lo = t == 0 ? SWAP2 : KEEP2, sel_hi = t == a.hx - 1 ? SWAP2 : KEEP2;
+    WrapOff oy = {0, 0}, oz = {0, 0};
+    if constexpr (YZ) {
+        oy = {y == 0 ? a.nxy : 0, y == a.n[1] - 1 ? -a.nxy : 0};
+        const int nzxy = a.n[2] * a.nxy;
+        oz = {z == 0 ? nzxy : 0, z == a.n[2] - 1 ? -nzxy : 0};
+    }
+    F2 g[Q];
+#pragma unroll
+    for (int s = 0; s < Q; ++s) {
+        const int cx = cslot(Q, s, 0), cy = cslot(Q, s, 1), cz = cslot(Q, s, 2);
+        if (PH == 0) {
+            g[s] = Store2<S>::ld(slot_ptr<Q, S>(a, s) + w);
+            continue;
+        }
+        int off = w + wrap_read(ox, cx);
+        if constexpr (YZ) off += wrap_read(oy, cy) + wrap_read(oz, cz);
+        const T* src = static_cast<const T*>(a.rshift[s]) + off;
+        if (cx == 0) g[s] = Store2<S>::ld(src);
+        else g[s] = Store2x<S>::ld(src, cx > 0 ? sel_lo : sel_hi);
+    }
+    F2 u[3];
+    const F2 rho = collide_pair<Q>(g, a.tau_mo, a.Ksmag, u);
+    if (!(fabsf(rho.v.x) < 1e30f) || !(fabsf(rho.v.y) < 1e30f)) atomicOr(a.err, ERR_NONFINITE);
+#pragma unroll
+    for (int s = 0; s < Q; ++s) {
+        const int cx = cslot(Q, s, 0), cy = cslot(Q, s, 1), cz = cslot(Q, s, 2);
+        if (PH == 0) {
+            Store2<S>::st(wslot_ptr<Q, S>(a, oslot(Q, s)) + w, g[s]);
+            continue;
+        }
+        int off = w + wrap_write(ox, cx);
+        if constexpr (YZ) off += wrap_write(oy, cy) + wrap_write(oz, cz);
+        T* dst = static_cast<T*>(a.wshift[s]) + off;
+        if (cx == 0) Store2<S>::st(dst, g[s]);
+        else Store2x<S>::st(dst, g[s], cx > 0 ? sel_hi : sel_lo);
+    }
+}
+
+// the face rows out of line: their extra offsets keep their registers to themselves
+template <int Q, int S>
+__device__ __noinline__ void halves_packed_faces(const StepArgs& a, int t, int y, int z) {
+    halves_packed<Q, S, 1, true>(a, t, y, z);
+}
+
+// Register caps: D3Q19 FP16 at 56 (9 blocks of 128 per SM), 2 % faster than
+// 48; BF16 (cheaper conversions) and FP32 at 48 (10 blocks); D3Q27 at 64.
+template <int Q, int S, int PH>
+__global__ void __launch_bounds__(128, Q == 27 ? 8 : (S == ST_F16S ? 9 : 10)) collide_halves_kernel(const __grid_constant__ StepArgs a) {
+    const int t = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = (int)blockIdx.z + a.z0;     // halo planes of a slab are not collided
+    if (y >= a.n[1] || t >= a.hx) return;
+    if (!halves_plain<Q, S, PH>(a, t, y, z)) {
+        collide_cell<Q, S, PH, false, 0>(a, t, y, z);
+        collide_cell<Q, S, PH, false, 0>(a, t + a.hx, y, z);
+        return;
+    }
+    if (PH == 1 && (y == 0 || y == a.n[1] - 1 || z == 0 || z == a.n[2] - 1)) halves_packed_faces<Q, S>(a, t, y, z);
+    else halves_packed<Q, S, PH, false>(a, t, y, z);
 }
 
 // ---------------------------------------------------------------------------
@@ -467,10 +603,9 @@ template <int Q, int S, int PH>
 __device__ void cell_velocity(const StepArgs& a, int x, int y, int z, float u[3]) {
     Offs o;
     make_offs(a, x, y, z, o);
-    const int cell = (z * a.n[1] + y) * a.n[0] + x;
     float g[Q];
-    if (a.layout == 1) load_pre<Q, S, PH, 1>(a, cell, o, g);
-    else load_pre<Q, S, PH, 0>(a, cell, o, g);
+    if (a.layout == 1) load_pre<Q, S, PH, 1>(a, o, g);
+    else load_pre<Q, S, PH, 0>(a, o, g);
     float drho, j[3];
     moments01<Q>(g, drho, j);
     const float inv = 1.0f / (1.0f + drho);
@@ -679,9 +814,9 @@ __global__ void __launch_bounds__(256) force_kernel(const StepArgs a) {
         const int by = (int)(r2 % R.n[1]);
         const int bz = (int)(r2 / R.n[1]);
         const int x = R.lo[0] + bx, y = R.lo[1] + by, z = R.lo[2] + bz;
-        const int cell = (z * a.n[1] + y) * a.n[0] + x;
         Offs o;
         make_offs(a, x, y, z, o);
+        const int cell = o.x[1] + o.y[1] + o.z[1];   // position in a population slot
         float us[3];
         solid_velocity(R, x, y, z, us);
         // per-cell link sum in FP32 on the shifted populations (the rest-weight
@@ -816,22 +951,26 @@ __device__ __forceinline__ unsigned stored_bits(typename Store<S>::T v) {
     else return __float_as_uint(Store<S>::ld(&v));      // exact widening of FP16 / BF16
 }
 
-// Sum of eight consecutive stored values (one 16- or 32-byte load) into the
-// thread's 128-bit fixed-point accumulator (and its FP64 side sum)
+// Eight consecutive stored values (one 16-byte load for 16-bit storage, two
+// for FP32), loaded ahead of their summation
 template <int S>
-__device__ __forceinline__ void sum8_fixed(const typename Store<S>::T* p, __int128& acc, double& side) {
-    using T = typename Store<S>::T;
-    T h[8];
-    if constexpr (S == ST_F32) {
-        const float4 a = reinterpret_cast<const float4*>(p)[0];
-        const float4 b = reinterpret_cast<const float4*>(p)[1];
-        h[0] = a.x; h[1] = a.y; h[2] = a.z; h[3] = a.w; h[4] = b.x; h[5] = b.y; h[6] = b.z; h[7] = b.w;
-    } else {
-        const uint4 v = *reinterpret_cast<const uint4*>(p);
-        const T* hv = reinterpret_cast<const T*>(&v);
+struct Group8 {
+    uint4 w[S == ST_F32 ? 2 : 1];
+};
+template <int S>
+__device__ __forceinline__ Group8<S> load8(const typename Store<S>::T* p) {
+    Group8<S> g;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) h[k] = hv[k];
-    }
+    for (int k = 0; k < (S == ST_F32 ? 2 : 1); ++k) g.w[k] = reinterpret_cast<const uint4*>(p)[k];
+    return g;
+}
+
+// Sum of eight consecutive stored values into the thread's 128-bit
+// fixed-point accumulator (and its FP64 side sum)
+template <int S>
+__device__ __forceinline__ void sum8_fixed(const Group8<S>& grp, __int128& acc, double& side) {
+    using T = typename Store<S>::T;
+    const T* h = reinterpret_cast<const T*>(grp.w);
     long long g = 0;                                    // |g| < 8 * 2^59 = 2^62
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
@@ -850,15 +989,24 @@ __device__ __forceinline__ double fixed_to_double(__int128 acc) {
 }
 
 template <int S>
-__global__ void __launch_bounds__(256) mass_kernel(const MassArgs m) {
+__global__ void __launch_bounds__(256, MASS_BLOCKS / 148) mass_kernel(const MassArgs m) {
     using T = typename Store<S>::T;
     const T* f = static_cast<const T*>(m.f);
     const long long groups = m.count / 8;
     __int128 acc = 0;
     double v = 0.0;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < groups;
-         i += (long long)gridDim.x * blockDim.x)
-        sum8_fixed<S>(f + 8 * i, acc, v);
+    // four groups in flight per thread: one 16-byte load each left the
+    // kernel short of requests in flight (0.47 of HBM for FP32 storage)
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + 3 * stride < groups; i += 4 * stride) {
+        Group8<S> g4[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) g4[k] = load8<S>(f + 8 * (i + k * stride));
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sum8_fixed<S>(g4[k], acc, v);
+    }
+    for (; i < groups; i += stride) sum8_fixed<S>(load8<S>(f + 8 * i), acc, v);
     v += fixed_to_double(acc);
     if (blockIdx.x == 0 && threadIdx.x == 0)
         for (long long i = 8 * groups; i < m.count; ++i) v += (double)Store<S>::ld(f + i);
@@ -934,8 +1082,9 @@ __global__ void init_kernel(const StepArgs a, const float* rho, const float* u, 
                          g[s]);
         return;
     }
+    const int pc = (z * a.n[1] + y) * a.n[0] + xmap(a, x);
 #pragma unroll
-    for (int s = 0; s < Q; ++s) Store<S>::st(slot_ptr<Q, S>(a, s) + cell, g[s]);
+    for (int s = 0; s < Q; ++s) Store<S>::st(slot_ptr<Q, S>(a, s) + pc, g[s]);
 }
 
 template <int Q, int S, int PH>
@@ -948,8 +1097,8 @@ __global__ void fields_kernel(const StepArgs a, float* rho, float* u) {
     Offs o;
     make_offs(a, x, y, z, o);
     float g[Q];
-    if (a.layout == 1) load_pre<Q, S, PH, 1>(a, cell, o, g);
-    else load_pre<Q, S, PH, 0>(a, cell, o, g);
+    if (a.layout == 1) load_pre<Q, S, PH, 1>(a, o, g);
+    else load_pre<Q, S, PH, 0>(a, o, g);
     float drho, j[3];
     moments01<Q>(g, drho, j);
     const float r = 1.0f + drho;
@@ -1001,8 +1150,13 @@ static cudaError_t launch_collide_l(const StepArgs& a, cudaStream_t s) {
         const int half = (n[0] + 1) / 2;
         const dim3 pb = cell_block(half);
         const dim3 pg((half + pb.x - 1) / pb.x, (n[1] + pb.y - 1) / pb.y, a.z1 - a.z0);
-        if (a.phase == 0) collide_pair_kernel<Q, S, 0, L><<<pg, pb, 0, s>>>(a);
-        else collide_pair_kernel<Q, S, 1, L><<<pg, pb, 0, s>>>(a);
+        if (L == 0 && a.xpair) {
+            if (a.phase == 0) collide_halves_kernel<Q, S, 0><<<pg, pb, 0, s>>>(a);
+            else collide_halves_kernel<Q, S, 1><<<pg, pb, 0, s>>>(a);
+        } else {
+            if (a.phase == 0) collide_pair_kernel<Q, S, 0, L><<<pg, pb, 0, s>>>(a);
+            else collide_pair_kernel<Q, S, 1, L><<<pg, pb, 0, s>>>(a);
+        }
         return cudaGetLastError();
     }
     const dim3 grd((n[0] + blk.x - 1) / blk.x, (n[1] + blk.y - 1) / blk.y, a.part == 2 ? n[2] : a.z1 - a.z0);

@@ -55,6 +55,40 @@ struct Store2<ST_BF16S> {
     }
 };
 
+// The same with the two values exchanged where sel is SWAP2 (the pair at a
+// periodic x wrap of the AA layout with x halves); KEEP2 leaves them.  For
+// 16-bit storage one byte permutation of the stored word, for FP32 a select.
+constexpr unsigned KEEP2 = 0x3210u, SWAP2 = 0x1032u;
+template <int S>
+struct Store2x;
+template <>
+struct Store2x<ST_F32> {
+    static __device__ __forceinline__ F2 ld(const float* p, unsigned sel) {
+        const float2 v = *reinterpret_cast<const float2*>(p);
+        return {sel == SWAP2 ? make_float2(v.y, v.x) : v};
+    }
+    static __device__ __forceinline__ void st(float* p, F2 v, unsigned sel) {
+        *reinterpret_cast<float2*>(p) = sel == SWAP2 ? make_float2(v.v.y, v.v.x) : v.v;
+    }
+};
+template <int S>
+struct Store2x16 {
+    using T = typename Store<S>::T;
+    static __device__ __forceinline__ F2 ld(const T* p, unsigned sel) {
+        const unsigned w = __byte_perm(*reinterpret_cast<const unsigned*>(p), 0u, sel);
+        return Store2<S>::ld(reinterpret_cast<const T*>(&w));
+    }
+    static __device__ __forceinline__ void st(T* p, F2 v, unsigned sel) {
+        unsigned w;
+        Store2<S>::st(reinterpret_cast<T*>(&w), v);
+        *reinterpret_cast<unsigned*>(p) = __byte_perm(w, 0u, sel);
+    }
+};
+template <>
+struct Store2x<ST_F16S> : Store2x16<ST_F16S> {};
+template <>
+struct Store2x<ST_BF16S> : Store2x16<ST_BF16S> {};
+
 // Sum of integer multiples of packed values whose first term needs no
 // addition: inside the fully unrolled loops every coefficient is a constant
 // and `on` is known at each point, so the branches fold away.

@@ -12,7 +12,7 @@ import ctypes as C
 
 import numpy as np
 
-from ._lib import STORAGE, HlConfig, HlRotorGeometry, check, lib
+from ._lib import LAYOUTS, STORAGE, HlConfig, HlRotorGeometry, check, lib
 
 _ALIGN = 256
 
@@ -51,7 +51,7 @@ class Lattice:
         cfg.wm_tol, cfg.wm_maxit = float(wm_tol), int(wm_maxit)
         cfg.mass_check_every, cfg.mass_tol = int(mass_check_every), float(mass_tol)
         cfg.overlap = int(bool(overlap))
-        cfg.layout = {"aa": 0, "esotwist": 1}[layout] if isinstance(layout, str) else int(layout)
+        cfg.layout = LAYOUTS[layout] if isinstance(layout, str) else int(layout)
         cfg.halo_lo, cfg.halo_hi, cfg.z_offset = int(bool(halo_lo)), int(bool(halo_hi)), int(z_offset)
         self._modes = None
         if modes is not None and len(modes):

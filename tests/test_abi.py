@@ -60,13 +60,22 @@ def test_defaults_and_workspace_size(L):
     assert L.hl_workspace_size(C.byref(cfg), C.byref(s16)) == 0
     assert s16.value < size.value
     for bad in (dict(q=20), dict(storage=5), dict(flow_axis=3), dict(tau_mo=0.5), dict(nx=1),
-                dict(sigma_band=1.5), dict(sigma_band=-0.25), dict(mass_check_every=-1)):
+                dict(sigma_band=1.5), dict(sigma_band=-0.25), dict(mass_check_every=-1), dict(layout=3),
+                dict(layout=2, nx=47), dict(layout=1, halo_hi=1)):
         c2 = _lib.HlConfig()
         L.hl_config_defaults(C.byref(c2))
         c2.nx, c2.ny, c2.nz = 48, 48, 96
         for k, v in bad.items():
             setattr(c2, k, v)
         assert L.hl_workspace_size(C.byref(c2), C.byref(size)) == -1, bad
+    # the AA layout with x halves: nx even, slabs allowed
+    for good in (dict(layout=2), dict(layout=2, halo_lo=1, halo_hi=1)):
+        c2 = _lib.HlConfig()
+        L.hl_config_defaults(C.byref(c2))
+        c2.nx, c2.ny, c2.nz = 48, 48, 96
+        for k, v in good.items():
+            setattr(c2, k, v)
+        assert L.hl_workspace_size(C.byref(c2), C.byref(size)) == 0, good
 
 
 def test_bytes_per_cell_match_paper_table(golden):
