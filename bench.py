@@ -187,9 +187,12 @@ def run_reference(args):
 # CUDA arm
 # --------------------------------------------------------------------------
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one bulk collide
-# launch of the rotor256 step from one ncu capture; reported only while the
-# kernel sources hash to the value they had at the capture (else null)
-NCU_TRAFFIC = {"source_sha": "2049e52963182aa7", "bytes_per_launch": 4871713280}
+# launch of the rotor256 step from one ncu capture (the mean of an even- and
+# an odd-step launch where both were captured), per (storage, layout);
+# reported only while the kernel sources hash to the value they had at the
+# capture (else null)
+NCU_TRAFFIC = {"source_sha": "da7e05395d4b4b12",
+               "bytes_per_launch": {("f32", "aa"): 4871964928, ("f16s", "aa_halves"): 2484186752}}
 
 
 def inflow_planes_pinned(wl, t0, n, dev):
@@ -401,9 +404,8 @@ def run_cuda(args):
     achieved = alg_bytes / per_launch_s / 1e9
     peak, peak_src = measured_peaks()
     sha = kernel_source_sha()
-    traffic = (NCU_TRAFFIC["bytes_per_launch"]
-               if NCU_TRAFFIC["source_sha"] == sha and args.workload == "rotor256" and args.storage == "f32"
-               else None)
+    traffic = (NCU_TRAFFIC["bytes_per_launch"].get((args.storage, args.layout))
+               if NCU_TRAFFIC["source_sha"] == sha and args.workload == "rotor256" else None)
     total_kernel_ms = sum(v[0] for v in prof.values())
     kernels = {k: {"launches": n, "ms_per_launch": round(ms / n, 4) if n else None,
                    "share": round(ms / total_kernel_ms, 4) if total_kernel_ms else None}
