@@ -95,11 +95,16 @@ typedef int hl_status;
  *                  with one aligned access per slot at both step parities.
  *                  Same cell model; hl_grad takes 0 and 1 (HL_ERR_STATE for 2)
  *  halo_lo, halo_hi  slab of a lattice decomposed along z (the domain
- *                  decomposition of the paper's multi-GPU runs, Sec. 5): 1
- *                  makes the plane z = 0 (halo_lo) or z = nz - 1 (halo_hi) a
- *                  halo plane that stands for the neighbouring slab's
- *                  boundary plane.  Halo planes are never collided, take no
- *                  part in the mass total, and their fields are undefined;
+ *                  decomposition of the paper's multi-GPU runs, Sec. 5):
+ *                  D > 0 makes the planes z < D (halo_lo) or z >= nz - D
+ *                  (halo_hi) halo planes that stand for the neighbouring
+ *                  slab's planes next to the face (0 <= D <= 8; the owned
+ *                  planes number at least max(halo_lo, halo_hi)).  One plane
+ *                  carries the streaming across the face; a face that cuts a
+ *                  rotor's box needs at least ceil(wm_ysample) + 2 (the
+ *                  wall-model sample reaches through it).  Halo planes are
+ *                  never collided, take no part in the mass total, and their
+ *                  fields are undefined;
  *                  with flow_axis 2 the open face on that side is absent (the
  *                  inlet belongs to the first slab, the outlet to the last).
  *                  Every odd step is bracketed by hl_halo_export /
@@ -386,7 +391,20 @@ hl_status hl_profile_end(hl_lattice* lat, double* ms, long long* launches);
  * (storage type, hl_halo_size bytes); the caller carries it (a device copy
  * on one GPU, a send/receive between ranks).  hl_step on a slab advances one
  * step per call and returns HL_ERR_STATE if a halo face has not imported at
- * the current t (t > 0). */
+ * the current t (t > 0).
+ *
+ * A rotor's box may be cut by a halo face of enough planes (see halo_lo):
+ * each slab then embeds, models and collides the box cells in its own
+ * planes, and the wall-model samples of cells next to the face read the
+ * neighbour's planes in the deep halo.  After every step, once both one-plane
+ * messages of every face have been imported, each such face also moves its
+ * deep message (every slot of the D planes next to it) with
+ * hl_halo_deep_export / hl_halo_deep_import; before the first step too.  The
+ * force and torque of a cut rotor are this slab's share (sum them over the
+ * slabs); its force reduction of a step runs at the next hl_step_async or
+ * the next load query (hl_forces, hl_moments, hl_loads_async,
+ * hl_save_state), which must come after the deep exchange.  A cut rotor
+ * needs sigma_band = 1 (HL_ERR_ARG) and takes no hl_set_drive (HL_ERR_STATE). */
 
 /* Bytes of one halo message of this lattice (HL_ERR_ARG without halo planes). */
 hl_status hl_halo_size(const hl_lattice* lat, size_t* bytes);
@@ -401,6 +419,20 @@ hl_status hl_halo_export(hl_lattice* lat, int face, void* d_buf);
  * record that the face is up to date at the current t.  Asynchronous on the
  * lattice stream: the caller orders it after the neighbour's export. */
 hl_status hl_halo_import(hl_lattice* lat, int face, const void* d_buf);
+
+/* Bytes of the deep message of face `face`: every slot of its D halo planes,
+ * [q][D][nx * ny] stored values (HL_ERR_ARG if the face has no halo). */
+hl_status hl_halo_deep_size(const hl_lattice* lat, int face, size_t* bytes);
+
+/* Copy every slot of the slab's own D planes next to face `face` into d_buf
+ * (hl_halo_deep_size bytes, device).  Asynchronous on the lattice stream;
+ * call after the one-plane imports of the current t on both sides. */
+hl_status hl_halo_deep_export(hl_lattice* lat, int face, void* d_buf);
+
+/* Store the neighbour's deep message (its hl_halo_deep_export of the opposite
+ * face at the same t; both faces have the same D) into the D halo planes of
+ * face `face` and record the face as up to date at the current t. */
+hl_status hl_halo_deep_import(hl_lattice* lat, int face, const void* d_buf);
 
 /* Total mass of a population array, without allocating anything.
  * The paper has no counterpart: this is a service for callers that cannot

@@ -95,6 +95,9 @@ SIGNATURES = {
     "hl_halo_size": (C.c_int, [_vp, C.POINTER(C.c_size_t)]),
     "hl_halo_export": (C.c_int, [_vp, C.c_int, _vp]),
     "hl_halo_import": (C.c_int, [_vp, C.c_int, _vp]),
+    "hl_halo_deep_size": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_size_t)]),
+    "hl_halo_deep_export": (C.c_int, [_vp, C.c_int, _vp]),
+    "hl_halo_deep_import": (C.c_int, [_vp, C.c_int, _vp]),
     "hl_last_error": (C.c_char_p, [_vp]),
     "hl_destroy": (None, [_vp]),
 }

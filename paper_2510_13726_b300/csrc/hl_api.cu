@@ -45,9 +45,11 @@ bool valid_config(const hl_config* c) {
     if (c->layout < 0 || c->layout > 2) return false;
     if (c->layout == 2 && c->nx % 2) return false;                      // x halves need nx even
     // z_offset may be -1: the first slab of a periodic z decomposition starts with the last slab's plane
-    if (c->halo_lo < 0 || c->halo_lo > 1 || c->halo_hi < 0 || c->halo_hi > 1) return false;
+    if (c->halo_lo < 0 || c->halo_lo > HALO_MAX || c->halo_hi < 0 || c->halo_hi > HALO_MAX) return false;
     if ((c->halo_lo || c->halo_hi) && c->layout == 1) return false;   // slabs use the AA pattern
-    if (c->nz - c->halo_lo - c->halo_hi < 1) return false;
+    // the owned planes fill a neighbour's deep halo
+    const int owned = c->nz - c->halo_lo - c->halo_hi;
+    if (owned < 1 || owned < c->halo_lo || owned < c->halo_hi) return false;
     return true;
 }
 
@@ -293,6 +295,7 @@ hl_status hl_lattice_init(hl_lattice** out, const hl_config* cfg, void* d_worksp
     lat->err = reinterpret_cast<unsigned*>(lat->ws + L.err);
     std::snprintf(lat->msg, sizeof lat->msg, "no error");
     lat->halo_t[0] = lat->halo_t[1] = -1;
+    lat->deep_t[0] = lat->deep_t[1] = -1;
     hl_status st;
     if (cfg->n_modes > 0) {
         std::vector<float> m(9 * cfg->n_modes);
@@ -349,24 +352,53 @@ static void rotor_reach(const hl_lattice* lat, const hl_rotor_geometry* g, doubl
     *reach_axial = std::fmax(g->n_blades > 0 ? w : 0.0, hubr);
 }
 
-static bool rotor_box(const hl_lattice* lat, const hl_rotor_geometry* g, int lo[3], int nn[3]) {
+// halo planes a face needs when it cuts a rotor box: the wall-model sample
+// (y_s along the normal, trilinear corners) and, at odd steps, the one more
+// plane its corner velocities are gathered from
+static int deep_halo_min(const hl_config& c) { return (int)std::ceil(c.wm_ysample) + 2; }
+
+// The rotor's box of cells.  A slab's box lies in its own planes; where it
+// reaches through a halo face of at least deep_halo_min planes it is cut
+// there (clip[f]) and the slab beyond takes the rest.  Returns an error text
+// or null.
+static const char* rotor_box(const hl_lattice* lat, const hl_rotor_geometry* g, int lo[3], int nn[3],
+                             bool clip[2]) {
     double rp, ra;
     rotor_reach(lat, g, &rp, &ra);
     const double reach_plane = rp + 2.0, reach_axial = ra + 2.0;
     const int dims[3] = {lat->cfg.nx, lat->cfg.ny, lat->cfg.nz};
+    const int halo[2] = {lat->cfg.halo_lo, lat->cfg.halo_hi};
+    clip[0] = clip[1] = false;
     for (int k = 0; k < 3; ++k) {
         const double r = (k == g->axis) ? reach_axial : reach_plane;
-        const int a = (int)std::floor(g->center[k] - r);
-        const int b = (int)std::ceil(g->center[k] + r);
+        int a = (int)std::floor(g->center[k] - r);
+        int b = (int)std::ceil(g->center[k] + r);
         const bool open = lat->cfg.open_boundaries && k == lat->cfg.flow_axis;
-        // 4 cells from an open face; a slab's box lies in its own planes
-        const int m_lo = (open && !(k == 2 && lat->cfg.halo_lo)) ? 4 : (k == 2 ? lat->cfg.halo_lo : 0);
-        const int m_hi = (open && !(k == 2 && lat->cfg.halo_hi)) ? 4 : (k == 2 ? lat->cfg.halo_hi : 0);
-        if (a < m_lo || b > dims[k] - 1 - m_hi) return false;
+        if (k == 2 && (halo[0] || halo[1])) {
+            // owned planes halo_lo .. nz - 1 - halo_hi; a face without halo is open or periodic
+            const int z0 = halo[0], z1 = dims[2] - 1 - halo[1];
+            for (int f = 0; f < 2; ++f) {
+                const bool beyond = f == 0 ? a < z0 : b > z1;
+                if (!beyond) continue;
+                if (!halo[f]) return "rotor box leaves the lattice or touches an open boundary";
+                if (halo[f] < deep_halo_min(lat->cfg))
+                    return "rotor box cut by a slab face with fewer halo planes than the wall-model sample needs";
+                clip[f] = true;
+                if (f == 0) a = z0;
+                else b = z1;
+            }
+            const bool open_lo = open && !halo[0], open_hi = open && !halo[1];
+            if ((open_lo && a < 4) || (open_hi && b > dims[2] - 5)) return "rotor box touches an open boundary";
+            if (a > b) return "rotor box outside the slab's planes";
+        } else {
+            // 4 cells from an open face
+            const int m = open ? 4 : 0;
+            if (a < m || b > dims[k] - 1 - m) return "rotor box leaves the lattice or touches an open boundary";
+        }
         lo[k] = a;
         nn[k] = b - a + 1;
     }
-    return true;
+    return nullptr;
 }
 
 static bool valid_geometry(const hl_rotor_geometry* g) {
@@ -381,7 +413,8 @@ static bool valid_geometry(const hl_rotor_geometry* g) {
 hl_status hl_rotor_workspace_size(const hl_lattice* lat, const hl_rotor_geometry* geom, size_t* bytes) {
     if (!lat || !valid_geometry(geom) || !bytes) return HL_ERR_ARG;
     int lo[3], nn[3];
-    if (!rotor_box(lat, geom, lo, nn)) return HL_ERR_ARG;
+    bool clip[2];
+    if (rotor_box(lat, geom, lo, nn, clip)) return HL_ERR_ARG;
     const long long box = (long long)nn[0] * nn[1] * nn[2];
     const long long ng = geom->n_blades > 0 ? (long long)geom->gx * geom->gy * geom->gz : 1;
     *bytes = rotor_layout(ng, box).total;
@@ -396,8 +429,12 @@ hl_status hl_set_rotor(hl_lattice* lat, int* rotor_id, const hl_rotor_geometry* 
     if (reinterpret_cast<size_t>(d_workspace) % ALIGN) return fail(lat, HL_ERR_ARG, "workspace not aligned");
     if (lat->nrot >= MAXROT) return fail(lat, HL_ERR_ARG, "too many rotors");
     int lo[3], nn[3];
-    if (!rotor_box(lat, geom, lo, nn))
-        return fail(lat, HL_ERR_ARG, "rotor box leaves the lattice or touches an open boundary");
+    bool clip[2];
+    if (const char* why = rotor_box(lat, geom, lo, nn, clip)) return fail(lat, HL_ERR_ARG, why);
+    // a cut box: its band cells read the neighbouring slab's state only through
+    // the wall-model sample and the force reduction (no finite-difference strain)
+    if ((clip[0] || clip[1]) && lat->cfg.sigma_band < 1.0)
+        return fail(lat, HL_ERR_ARG, "a rotor box cut by a slab face needs sigma_band = 1");
     for (int k = 0; k < lat->nrot; ++k) {
         const RotorDev& o = lat->rot[k].dev;
         bool overlap = true;
@@ -427,6 +464,13 @@ hl_status hl_set_rotor(hl_lattice* lat, int* rotor_id, const hl_rotor_geometry* 
         D.origin[k] = (float)geom->origin[k];
     }
     if (geom->n_blades == 0) D.g[0] = D.g[1] = D.g[2] = 2;
+    // wall-model samples stay in the box, or cross a cut face into the halo
+    // (one plane short of its end: odd steps gather a corner's populations
+    // from its neighbours)
+    R.clip[0] = clip[0];
+    R.clip[1] = clip[1];
+    D.zs_lo = clip[0] ? 1 : lo[2];
+    D.zs_hi = clip[1] ? lat->cfg.nz - 1 : lo[2] + nn[2];
     D.box_cells = box;
     D.omega = (float)omega;
     D.axis = geom->axis;
@@ -465,6 +509,8 @@ hl_status hl_set_rotor(hl_lattice* lat, int* rotor_id, const hl_rotor_geometry* 
     HL_CUDA(lat, cudaStreamSynchronize(lat->stream));
     if (rotor_id) *rotor_id = lat->nrot;
     lat->nrot += 1;
+    lat->clip_face[0] = lat->clip_face[0] || clip[0];
+    lat->clip_face[1] = lat->clip_face[1] || clip[1];
     return HL_OK;
 }
 
@@ -481,6 +527,23 @@ static cudaError_t prof_mark(hl_lattice* lat, int k, cudaStream_t st) {
 }
 
 }  // extern "C"
+
+// a rotor box cut by a halo face: the force reduction of a step waits for
+// the halo exchange that follows it
+static bool defers_force(const hl_lattice* lat) { return lat->clip_face[0] || lat->clip_face[1]; }
+
+// the deferred force reduction (and driven-rotor update) of the last step,
+// on the lattice stream
+static hl_status flush_force(hl_lattice* lat) {
+    if (!lat->force_pending) return HL_OK;
+    lat->force_pending = false;
+    const int Q = lat->cfg.q, S = lat->cfg.storage;
+    HL_CUDA(lat, prof_mark(lat, 2, lat->stream));
+    HL_CUDA(lat, launch_force(Q, S, lat->pending, lat->stream));
+    HL_CUDA(lat, prof_mark(lat, 2, lat->stream));
+    HL_CUDA(lat, launch_evolve(lat->pending, lat->stream));
+    return HL_OK;
+}
 
 // one step on a single stream
 static hl_status step_serial(hl_lattice* lat, const StepArgs& a0, bool with_force) {
@@ -503,12 +566,12 @@ static hl_status step_serial(hl_lattice* lat, const StepArgs& a0, bool with_forc
     HL_CUDA(lat, launch_collide(Q, S, a, st));
     HL_CUDA(lat, prof_mark(lat, 1, st));
     if (lat->nrot > 0) {
-        if (with_force) {
+        if (with_force && !defers_force(lat)) {
             HL_CUDA(lat, prof_mark(lat, 2, st));
             HL_CUDA(lat, launch_force(Q, S, a, st));
             HL_CUDA(lat, prof_mark(lat, 2, st));
             HL_CUDA(lat, launch_evolve(a, st));
-        } else {
+        } else if (!with_force) {
             for (int k = 0; k < lat->nrot; ++k)
                 HL_CUDA(lat, cudaMemsetAsync(lat->rot[k].dev.count, 0, COUNT_BYTES, st));
         }
@@ -562,7 +625,9 @@ static hl_status step_overlap(hl_lattice* lat, const StepArgs& a0, bool with_for
     }
     HL_CUDA(lat, cudaEventRecord(lat->ev_box[p], ax));
     a.part = 0;
-    if (with_force) {
+    if (with_force && defers_force(lat)) {
+        // taken after the halo exchange (flush_force)
+    } else if (with_force) {
         cudaStream_t fs = lat->fst;
         HL_CUDA(lat, cudaStreamWaitEvent(fs, lat->ev_box[p], 0));
         HL_CUDA(lat, prof_mark(lat, 2, fs));
@@ -595,9 +660,18 @@ hl_status hl_step_async(hl_lattice* lat, int n) {
     if (lat->cfg.halo_lo || lat->cfg.halo_hi) {
         // a slab steps once per call, after the halo exchange of its parity
         if (n > 1) return fail(lat, HL_ERR_ARG, "a slab (halo planes) advances one step per call");
-        for (int f = 0; f < 2 && n > 0; ++f)
+        for (int f = 0; f < 2 && n > 0; ++f) {
             if ((f == 0 ? lat->cfg.halo_lo : lat->cfg.halo_hi) && lat->t > 0 && lat->halo_t[f] != lat->t)
                 return fail(lat, HL_ERR_STATE, "halo face not imported at the current time step");
+            // a face that cuts a rotor box: its deep halo holds the neighbour's state
+            // of this step, also at t = 0 (the wall model samples through it)
+            if (lat->clip_face[f] && lat->deep_t[f] != lat->t)
+                return fail(lat, HL_ERR_STATE, "deep halo of a face that cuts a rotor box not imported at this step");
+        }
+        if (n > 0) {
+            hl_status fst_ = flush_force(lat);
+            if (fst_ != HL_OK) return fst_;
+        }
     }
     const bool two = lat->have_aux && lat->nrot > 0;
     if (two && n > 0) {
@@ -606,8 +680,14 @@ hl_status hl_step_async(hl_lattice* lat, int n) {
         HL_CUDA(lat, cudaStreamWaitEvent(lat->aux, lat->ev_fork, 0));
     }
     for (int s = 0; s < n; ++s) {
-        hl_status st = issue_step(lat, make_args(lat), true);
+        const StepArgs a = make_args(lat);
+        hl_status st = issue_step(lat, a, true);
         if (st != HL_OK) return st;
+        if (defers_force(lat) && lat->nrot > 0) {
+            lat->pending = a;
+            lat->pending.part = 0;
+            lat->force_pending = true;
+        }
         const long long t_done = lat->t;
         lat->t += 1;
         lat->n_avg += 1;
@@ -679,6 +759,7 @@ hl_status hl_step(hl_lattice* lat, int n) {
 }
 
 static hl_status read_acc(hl_lattice* lat, std::vector<double>& acc) {
+    if (hl_status st = flush_force(lat); st != HL_OK) return st;
     acc.assign(12 * (size_t)lat->nrot, 0.0);
     for (int k = 0; k < lat->nrot; ++k)
         HL_CUDA(lat, cudaMemcpyAsync(acc.data() + 12 * k, lat->rot[k].dev.acc, 12 * sizeof(double),
@@ -689,6 +770,7 @@ static hl_status read_acc(hl_lattice* lat, std::vector<double>& acc) {
 
 hl_status hl_loads_async(hl_lattice* lat, double* h_loads) {
     if (!lat || !h_loads) return HL_ERR_ARG;
+    if (hl_status st = flush_force(lat); st != HL_OK) return st;
     for (int k = 0; k < lat->nrot; ++k)
         HL_CUDA(lat, cudaMemcpyAsync(h_loads + 6 * k, lat->rot[k].dev.acc, 6 * sizeof(double),
                                      cudaMemcpyDeviceToHost, lat->stream));
@@ -755,11 +837,13 @@ hl_status hl_init_fields(hl_lattice* lat, const float* d_rho, const float* d_u) 
 
 // ---- slabs: halo exchange (AA pattern, decomposition along z) ----
 // The message of a face is one plane of the slots whose velocity crosses
-// that face, chosen by the step parity (see include/hlbm.h):
-//   export  face 0: t odd plane 1 (c_z = +1),      t even plane 0 (c_z = -1)
-//           face 1: t odd plane nz-2 (c_z = -1),   t even plane nz-1 (c_z = +1)
-//   import  face 0: t odd plane 0 (c_z = -1),      t even plane 1 (c_z = +1)
-//           face 1: t odd plane nz-1 (c_z = +1),   t even plane nz-2 (c_z = -1)
+// that face, chosen by the step parity (see include/hlbm.h); with D_lo /
+// D_hi halo planes the plane next to the lower face is D_lo - 1 and the
+// lower boundary plane D_lo (upper: nz - D_hi and nz - D_hi - 1):
+//   export  face 0: t odd boundary plane (c_z = +1),  t even halo plane (c_z = -1)
+//           face 1: t odd boundary plane (c_z = -1),  t even halo plane (c_z = +1)
+//   import  face 0: t odd halo plane (c_z = -1),      t even boundary plane (c_z = +1)
+//           face 1: t odd halo plane (c_z = +1),      t even boundary plane (c_z = -1)
 static int halo_slot_list(int q, int sign, int* out) {
     std::vector<int> c(3 * q);
     std::vector<double> w(q);
@@ -774,15 +858,18 @@ static hl_status halo_copy(hl_lattice* lat, int face, void* buf, bool import_) {
     if (!lat || face < 0 || face > 1 || !buf) return HL_ERR_ARG;
     if (!(face == 0 ? lat->cfg.halo_lo : lat->cfg.halo_hi))
         return fail(lat, HL_ERR_ARG, "hl_halo_export/import: the face is not a halo face");
+    // the halo plane next to the face and the slab's own boundary plane
     const int nz = lat->cfg.nz;
+    const int h_lo = lat->cfg.halo_lo - 1, b_lo = lat->cfg.halo_lo;
+    const int h_hi = nz - lat->cfg.halo_hi, b_hi = nz - lat->cfg.halo_hi - 1;
     const bool odd = (lat->t & 1) != 0;
     int plane, sign;
     if (!import_) {
-        if (face == 0) { plane = odd ? 1 : 0; sign = odd ? +1 : -1; }
-        else { plane = odd ? nz - 2 : nz - 1; sign = odd ? -1 : +1; }
+        if (face == 0) { plane = odd ? b_lo : h_lo; sign = odd ? +1 : -1; }
+        else { plane = odd ? b_hi : h_hi; sign = odd ? -1 : +1; }
     } else {
-        if (face == 0) { plane = odd ? 0 : 1; sign = odd ? -1 : +1; }
-        else { plane = odd ? nz - 1 : nz - 2; sign = odd ? +1 : -1; }
+        if (face == 0) { plane = odd ? h_lo : b_lo; sign = odd ? -1 : +1; }
+        else { plane = odd ? h_hi : b_hi; sign = odd ? +1 : -1; }
     }
     HaloArgs h;
     std::memset(&h, 0, sizeof h);
@@ -790,6 +877,7 @@ static hl_status halo_copy(hl_lattice* lat, int face, void* buf, bool import_) {
     h.N = lat->N;
     h.nxy = lat->cfg.nx * lat->cfg.ny;
     h.plane = plane;
+    h.nplanes = 1;
     h.nslot = halo_slot_list(lat->cfg.q, sign, h.slots);
     h.buf = buf;
     h.import_ = import_ ? 1 : 0;
@@ -809,6 +897,46 @@ hl_status hl_halo_export(hl_lattice* lat, int face, void* d_buf) { return halo_c
 
 hl_status hl_halo_import(hl_lattice* lat, int face, const void* d_buf) {
     return halo_copy(lat, face, const_cast<void*>(d_buf), true);
+}
+
+// Deep halo: every slot of the D planes next to a face.  Export: the slab's
+// own D planes next to the face; import: its D halo planes beyond it.  Runs
+// after the one-plane exchange of the same step, so the neighbour's planes
+// are complete.
+static hl_status deep_copy(hl_lattice* lat, int face, void* buf, bool import_) {
+    if (!lat || face < 0 || face > 1 || !buf) return HL_ERR_ARG;
+    const int D = face == 0 ? lat->cfg.halo_lo : lat->cfg.halo_hi;
+    if (D < 1) return fail(lat, HL_ERR_ARG, "hl_halo_deep_export/import: the face is not a halo face");
+    const int nz = lat->cfg.nz;
+    HaloArgs h;
+    std::memset(&h, 0, sizeof h);
+    h.f = lat->f;
+    h.N = lat->N;
+    h.nxy = lat->cfg.nx * lat->cfg.ny;
+    if (face == 0) h.plane = import_ ? 0 : D;
+    else h.plane = import_ ? nz - D : nz - 2 * D;
+    h.nplanes = D;
+    h.nslot = lat->cfg.q;
+    for (int s = 0; s < lat->cfg.q; ++s) h.slots[s] = s;
+    h.buf = buf;
+    h.import_ = import_ ? 1 : 0;
+    HL_CUDA(lat, launch_halo(lat->cfg.storage, h, lat->stream));
+    if (import_) lat->deep_t[face] = lat->t;
+    return HL_OK;
+}
+
+hl_status hl_halo_deep_size(const hl_lattice* lat, int face, size_t* bytes) {
+    if (!lat || !bytes || face < 0 || face > 1) return HL_ERR_ARG;
+    const int D = face == 0 ? lat->cfg.halo_lo : lat->cfg.halo_hi;
+    if (D < 1) return HL_ERR_ARG;
+    *bytes = (size_t)D * lat->cfg.q * lat->cfg.nx * lat->cfg.ny * store_bytes(lat->cfg.storage);
+    return HL_OK;
+}
+
+hl_status hl_halo_deep_export(hl_lattice* lat, int face, void* d_buf) { return deep_copy(lat, face, d_buf, false); }
+
+hl_status hl_halo_deep_import(hl_lattice* lat, int face, const void* d_buf) {
+    return deep_copy(lat, face, const_cast<void*>(d_buf), true);
 }
 
 hl_status hl_mass(hl_lattice* lat, double* mass) {
@@ -886,6 +1014,7 @@ static hl_status state_copy(hl_lattice* lat, char* buf, bool save) {
 hl_status hl_save_state(hl_lattice* lat, void* d_buf, size_t bytes) {
     if (!lat || !d_buf) return HL_ERR_ARG;
     if (bytes < state_bytes(lat)) return fail(lat, HL_ERR_WORKSPACE, "state buffer too small");
+    if (hl_status fs = flush_force(lat); fs != HL_OK) return fs;
     StateHeader h{STATE_MAGIC, lat->t, lat->n_avg, lat->N, lat->cfg.q, lat->cfg.storage, lat->nrot, 0,
                   lat->mass_ref};
     HL_CUDA(lat, cudaMemcpyAsync(d_buf, &h, sizeof h, cudaMemcpyHostToDevice, lat->stream));
@@ -908,6 +1037,8 @@ hl_status hl_load_state(hl_lattice* lat, const void* d_buf, size_t bytes) {
     lat->n_avg = h.n_avg;
     lat->mass_ref = h.mass_ref;
     lat->halo_t[0] = lat->halo_t[1] = -1;   // a slab exchanges again before its next step
+    lat->deep_t[0] = lat->deep_t[1] = -1;
+    lat->force_pending = false;             // the snapshot's loads are complete
     hl_status st = state_copy(lat, const_cast<char*>(static_cast<const char*>(d_buf)), false);
     if (st != HL_OK) return st;
     HL_CUDA(lat, cudaMemsetAsync(lat->err, 0, sizeof(unsigned), lat->stream));
@@ -920,6 +1051,8 @@ hl_status hl_set_drive(hl_lattice* lat, int rotor, double inertia, double k_gen,
     if (!(inertia > 0.0) || !std::isfinite(inertia) || !std::isfinite(k_gen) || !std::isfinite(q_gen0))
         return fail(lat, HL_ERR_ARG, "hl_set_drive: inertia must be positive and finite");
     RotorHost& R = lat->rot[rotor];
+    if (R.clip[0] || R.clip[1])
+        return fail(lat, HL_ERR_STATE, "hl_set_drive: the rotor's box is cut by a slab face (its torque is split)");
     DriveDev h;
     std::memset(&h, 0, sizeof h);
     double th, om;

@@ -266,6 +266,8 @@ struct DriveDev {
 
 struct RotorDev {
     int lo[3], n[3];            // box of lattice cells that may be touched
+    int zs_lo, zs_hi;           // planes a wall-model sample may read: the box's, or through a slab
+                                // face that cuts the box, the halo planes beyond it (zs_lo <= z < zs_hi)
     long long box_cells;
     float cf[3];                // centre (binary32)
     float omega;

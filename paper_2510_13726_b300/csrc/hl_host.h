@@ -83,6 +83,7 @@ struct RotorHost {
     double omega, pitch;
     double pitch_sets;       // pitch that decides the cell sets while they are frozen
     bool driven;             // torque-driven rotation (device state at dev.drive)
+    bool clip[2];            // the box is cut by the slab's lower / upper halo face
     RotorDev dev;
     char* ws;
     RotorLayout L;
@@ -109,6 +110,13 @@ struct hl_lattice {
     const float* d0;         // caller's static porosity multiplier [N], or null
     const float* inflow;     // caller's inflow velocity plane [3][plane], or null (synthetic modes)
     long long halo_t[2];     // slab: time of the last halo import of the lower / upper face (-1: none)
+    long long deep_t[2];     // slab: time of the last deep halo import of each face (-1: none)
+    bool clip_face[2];       // a rotor box is cut by the lower / upper halo face
+    // a rotor box cut by a halo face: the force reduction of a step reads the
+    // neighbouring slab's cells, so it runs after the halo exchange, at the
+    // start of the next step or before the next load query
+    bool force_pending;
+    hl::StepArgs pending;
     bool frozen;             // cell sets decided by RotorHost::pitch_sets
     char msg[256];
     // second stream for the rotor-box chain, and the events that order it

@@ -81,7 +81,7 @@ struct MassArgs {
     long long count;         // Q * N stored values
     long long N;             // cells per slot
     int nxy;                 // cells per z plane
-    int halo_lo, halo_hi;    // halo planes (z = 0, z = nz - 1) excluded from the total
+    int halo_lo, halo_hi;    // halo planes (z < halo_lo, z >= nz - halo_hi) excluded from the total
     double shift_mass;       // N * sum_i w_i (the storage shift)
     double ref, tol;         // reference mass and allowed relative drift (tol < 0: no check)
     double* partial;         // [MASS_BLOCKS]
@@ -102,16 +102,18 @@ cudaError_t launch_init(int Q, int storage, const StepArgs& a, const float* rho,
                         const float u0[3], cudaStream_t s);
 cudaError_t launch_fields(int Q, int storage, const StepArgs& a, float* rho, float* u,
                           cudaStream_t s);
-// halo message of a slab: nslot slots (list) of plane z, [nslot][nxy] stored
-// values; export = plane -> buffer, import = buffer -> plane
+// halo message of a slab: nslot slots (list) of nplanes consecutive planes,
+// [nslot][nplanes][nxy] stored values; export = planes -> buffer, import =
+// buffer -> planes
 struct HaloArgs {
     void* f;
     long long N;
-    int nxy, plane, nslot;
-    int slots[9];
-    void* buf;
+    int nxy, plane, nplanes, nslot;   // planes plane .. plane + nplanes - 1
+    int slots[27];
+    void* buf;                        // [nslot][nplanes][nxy]
     int import_;
 };
+constexpr int HALO_MAX = 8;           // halo planes per face at most
 cudaError_t launch_halo(int storage, const HaloArgs& h, cudaStream_t s);
 cudaError_t launch_debug_collide(int Q, int n, const float* g_in, const float* d, const float* uB,
                                  const float* sigma, const float* S, float tau_mo, float Ksmag,

@@ -657,9 +657,11 @@ __global__ void __launch_bounds__(128) wall_kernel(const StepArgs a) {
         }
         // the sample's corner cells must lie in the rotor box: the box chain
         // runs beside the bulk launch, which updates every cell outside it
-        bool inside = true;
+        // (along z, through a slab face that cuts the box, the neighbouring
+        // slab's planes in the deep halo, which only the halo exchange writes)
+        bool inside = i0[2] >= R.zs_lo && i0[2] + 1 < R.zs_hi;
 #pragma unroll
-        for (int k = 0; k < 3; ++k)
+        for (int k = 0; k < 2; ++k)
             inside = inside && i0[k] - R.lo[k] >= 0 && i0[k] + 1 - R.lo[k] < R.n[k];
         const long long B = R.box_cells;
         float* wm = R.wm + bi;
@@ -1017,7 +1019,7 @@ __global__ void __launch_bounds__(256, MASS_BLOCKS / 148) mass_kernel(const Mass
         for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < slots * nh;
              i += (long long)gridDim.x * blockDim.x) {
             const long long sl = i / nh, r = i % nh;
-            const long long cell = (m.halo_lo && r < m.nxy) ? r : m.N - nh + r;
+            const long long cell = r < (long long)m.halo_lo * m.nxy ? r : m.N - nh + r;
             v -= (double)Store<S>::ld(f + sl * m.N + cell);
         }
     }
@@ -1302,16 +1304,17 @@ cudaError_t launch_fields(int Q, int S, const StepArgs& a, float* rho, float* u,
     HL_DISPATCH(Q, S, launch_fields_t, a, rho, u, s);
 }
 
-// halo message: slot list x plane, raw stored values (no conversion)
+// halo message: slot list x consecutive planes, raw stored values (no conversion)
 template <typename T>
 __global__ void __launch_bounds__(256) halo_kernel(const HaloArgs h) {
-    const long long n = (long long)h.nslot * h.nxy;
+    const long long per_slot = (long long)h.nplanes * h.nxy;
+    const long long n = (long long)h.nslot * per_slot;
     T* f = static_cast<T*>(h.f);
     T* b = static_cast<T*>(h.buf);
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        const int k = (int)(i / h.nxy);
-        const long long c = (long long)h.plane * h.nxy + (i - (long long)k * h.nxy);
+        const int k = (int)(i / per_slot);
+        const long long c = (long long)h.plane * h.nxy + (i - (long long)k * per_slot);
         T* p = f + (long long)h.slots[k] * h.N + c;
         if (h.import_) *p = b[i];
         else b[i] = *p;
@@ -1319,7 +1322,7 @@ __global__ void __launch_bounds__(256) halo_kernel(const HaloArgs h) {
 }
 
 cudaError_t launch_halo(int storage, const HaloArgs& h, cudaStream_t s) {
-    const long long n = (long long)h.nslot * h.nxy;
+    const long long n = (long long)h.nslot * h.nplanes * h.nxy;
     long long blocks = (n + 255) / 256;
     if (blocks > 148 * 8) blocks = 148 * 8;
     if (blocks < 1) blocks = 1;

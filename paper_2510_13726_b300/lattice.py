@@ -52,7 +52,7 @@ class Lattice:
         cfg.mass_check_every, cfg.mass_tol = int(mass_check_every), float(mass_tol)
         cfg.overlap = int(bool(overlap))
         cfg.layout = LAYOUTS[layout] if isinstance(layout, str) else int(layout)
-        cfg.halo_lo, cfg.halo_hi, cfg.z_offset = int(bool(halo_lo)), int(bool(halo_hi)), int(z_offset)
+        cfg.halo_lo, cfg.halo_hi, cfg.z_offset = int(halo_lo), int(halo_hi), int(z_offset)
         self._modes = None
         if modes is not None and len(modes):
             self._modes = np.ascontiguousarray(modes, dtype=np.float64).reshape(-1, 9)
@@ -163,6 +163,24 @@ class Lattice:
         import torch
         with torch.cuda.device(self.device):
             self._check(lib().hl_halo_import(self._h, int(face), C.c_void_p(buf.data_ptr())))
+
+    def halo_deep_size(self, face: int) -> int:
+        """Bytes of the deep message of face 0 / 1 (hl_halo_deep_size)."""
+        size = C.c_size_t()
+        self._check(lib().hl_halo_deep_size(self._h, int(face), C.byref(size)))
+        return size.value
+
+    def halo_deep_export(self, face: int, buf):
+        """Every slot of the slab's planes next to face 0 / 1 into the device tensor buf."""
+        import torch
+        with torch.cuda.device(self.device):
+            self._check(lib().hl_halo_deep_export(self._h, int(face), C.c_void_p(buf.data_ptr())))
+
+    def halo_deep_import(self, face: int, buf):
+        """The neighbour's deep message for face 0 / 1 from the device tensor buf."""
+        import torch
+        with torch.cuda.device(self.device):
+            self._check(lib().hl_halo_deep_import(self._h, int(face), C.c_void_p(buf.data_ptr())))
 
     def step_async(self, n: int = 1):
         import torch

@@ -109,8 +109,10 @@ def test_null_and_invalid_handles_are_rejected(L):
 
 
 def test_slab_configuration_rules(L):
-    """Halo planes need the AA layout and at least one owned plane; a
-    periodic slab may start at z_offset -1 (host-side validation only)."""
+    """Halo planes (0 to 8 per face) need an AA layout and at least as many
+    owned planes as either face has halo planes (the deep message of a face
+    is the slab's own planes next to it); a periodic slab may start at
+    z_offset -1 (host-side validation only)."""
     cfg = _lib.HlConfig()
     L.hl_config_defaults(C.byref(cfg))
     cfg.nx, cfg.ny, cfg.nz = 8, 8, 6
@@ -121,8 +123,16 @@ def test_slab_configuration_rules(L):
     assert L.hl_workspace_size(C.byref(cfg), C.byref(size)) == 0 and size.value == plain
     cfg.layout = 1
     assert L.hl_workspace_size(C.byref(cfg), C.byref(size)) == -1      # slabs use the AA pattern
+    cfg.layout = 2
+    assert L.hl_workspace_size(C.byref(cfg), C.byref(size)) == 0       # the AA layout with x halves
     cfg.layout = 0
-    cfg.halo_lo = 2
+    cfg.halo_lo = 2                                                     # 2 + 1 halo planes, 3 owned
+    assert L.hl_workspace_size(C.byref(cfg), C.byref(size)) == 0
+    cfg.halo_lo = 4                                                     # 4 + 1 halo planes, 1 owned
     assert L.hl_workspace_size(C.byref(cfg), C.byref(size)) == -1
-    cfg.halo_lo, cfg.nz = 1, 2
+    cfg.nz, cfg.halo_lo, cfg.halo_hi = 20, 9, 1
+    assert L.hl_workspace_size(C.byref(cfg), C.byref(size)) == -1      # at most 8
+    cfg.halo_lo, cfg.halo_hi = -1, 1
+    assert L.hl_workspace_size(C.byref(cfg), C.byref(size)) == -1
+    cfg.halo_lo, cfg.halo_hi, cfg.nz = 1, 1, 2
     assert L.hl_workspace_size(C.byref(cfg), C.byref(size)) == -1      # nz < 3

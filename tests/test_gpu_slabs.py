@@ -2,8 +2,9 @@
 exchanging halo messages through hl_halo_export / hl_halo_import, equals the
 undecomposed lattice bit for bit (same kernels, same per-cell arithmetic,
 only the place where a population is stored differs), with the rotor box next
-to a cut; flow along z (inlet in the first slab, outlet in the last) and flow
-along x with z periodic (the last slab wraps onto the first).
+to a cut or cut by it (deep halos, hl_halo_deep_export / import); flow along
+z (inlet in the first slab, outlet in the last) and flow along x with z
+periodic (the last slab wraps onto the first).
 """
 
 import dataclasses
@@ -28,11 +29,11 @@ def P():
     return P
 
 
-def _compare(P, wl, cuts, steps, storage="f32"):
+def _compare(P, wl, cuts, steps, storage="f32", layout="aa"):
     import torch
     from paper_2510_13726_b300.slabs import SlabDomain
-    whole = P.Lattice.from_workload(wl, storage=storage)
-    dom = SlabDomain.from_workload(wl, cuts=cuts, storage=storage)
+    whole = P.Lattice.from_workload(wl, storage=storage, layout=layout)
+    dom = SlabDomain.from_workload(wl, cuts=cuts, storage=storage, layout=layout)
     # with the flow along z the inlet and outlet planes' fields are not defined
     # by the scheme (at odd steps they read across the open face, where a slab
     # and the whole lattice wrap to different planes): compare the others
@@ -70,6 +71,71 @@ def test_two_and_three_slabs_equal_the_lattice_flow_along_z(P):
     _compare(P, wl, [0, b + 1, 96], 200)
     _compare(P, wl, [0, b + 1, 64, 96], 200)
     _compare(P, wl, [0, a, b + 1, 96], 40)          # a slab that is exactly the rotor box
+
+
+def test_rotor_box_cut_by_slab_faces(P):
+    """rotor48 with the cuts inside the rotor box (planes 12..36): through the
+    rotor plane (24), two cuts 10 planes apart (20, 30), and a cut two planes
+    after the box's start (14).  Faces that cut the box keep 4 halo planes,
+    refilled with the neighbour's planes after every step; each slab embeds,
+    models and collides its part of the box, the wall-model samples of cells
+    next to the face read through it, and the rotor's loads are the sum of the
+    slabs' shares (FP64 sums in another order: 1e-12).  200 steps, bit for
+    bit on the fields."""
+    wl = W.workload("rotor48")
+    a, b = _box_z(wl)
+    assert (a, b) == (12, 36)
+    _compare(P, wl, [0, 24, 96], 200)
+    _compare(P, wl, [0, 20, 30, 96], 200)
+    _compare(P, wl, [0, 14, 96], 60)
+
+
+@pytest.mark.parametrize("storage,layout", [("bf16s", "aa"), ("f16s", "aa_halves")])
+def test_rotor_box_cut_16bit(P, storage, layout):
+    """The cut rotor box with 16-bit storage, in the AA layout and with x halves."""
+    _compare(P, W.workload("rotor48"), [0, 22, 96], 60, storage=storage, layout=layout)
+
+
+def test_cut_rotor_box_rules(P):
+    """A face that cuts a rotor box needs the deep halo (4 planes with y_s =
+    2), sigma_band = 1, no torque drive, and the deep import of every step
+    (also before the first); its force reduction runs after the exchange."""
+    wl = W.workload("rotor48")
+    g = wl.blade_grids()[0]
+    rot = wl.rotors[0]
+    c = (rot.center[0], rot.center[1], rot.center[2])
+
+    def slab(hi, **kw):
+        L = P.Lattice(wl.nx, wl.ny, 24 + hi, halo_hi=hi, **kw)
+        return L
+
+    L = slab(1)
+    with pytest.raises(P.HlError) as e:
+        L.add_rotor(g, center=c, omega=rot.omega(wl.u_in))     # box 12..36 leaves through a 1-plane face
+    assert e.value.code == -1
+    L.close()
+    L = slab(4, sigma_band=0.5)
+    with pytest.raises(P.HlError) as e:
+        L.add_rotor(g, center=c, omega=rot.omega(wl.u_in))
+    assert e.value.code == -1
+    L.close()
+    L = slab(4)
+    L.add_rotor(g, center=c, omega=rot.omega(wl.u_in))
+    lo, n = L.rotor_box(0)
+    assert lo[2] == 12 and lo[2] + n[2] == 24                 # cut at the slab's last owned plane
+    with pytest.raises(P.HlError) as e:
+        L.set_drive(0, 1e6)
+    assert e.value.code == -5
+    with pytest.raises(P.HlError) as e:
+        L.step(1)                                             # no deep import yet, even at t = 0
+    assert e.value.code == -5
+    import torch
+    buf = torch.empty(L.halo_deep_size(1), dtype=torch.uint8, device=L.device)
+    assert L.halo_deep_size(1) == 4 * 19 * wl.nx * wl.ny * 4
+    L.halo_deep_export(1, buf)
+    L.halo_deep_import(1, buf)
+    L.step(1)
+    L.close()
 
 
 def test_slabs_with_turbulent_inflow_and_16bit_storage(P):

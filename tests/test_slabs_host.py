@@ -18,7 +18,7 @@ import numpy as np
 import pytest
 import torch
 
-from paper_2510_13726_b300.slabs import SlabDomain, partition, slab_specs
+from paper_2510_13726_b300.slabs import SlabDomain, cuts_in_boxes, deep_halo, partition, slab_specs
 
 C19 = np.array([c for c in itertools.product((-1, 0, 1), repeat=3) if sum(abs(v) for v in c) <= 2])
 OPP = np.array([int(np.nonzero((C19 == -c).all(1))[0][0]) for c in C19])
@@ -38,9 +38,9 @@ class AAEngine:
     """AA-pattern lattice (x, y periodic; z periodic unless it has halo
     planes, which are never updated)."""
 
-    def __init__(self, g, halo_lo=False, halo_hi=False):
+    def __init__(self, g, halo_lo=0, halo_hi=0):
         self.g = g.copy()                      # (q, nz, ny, nx): slot s of every cell
-        self.halo_lo, self.halo_hi = halo_lo, halo_hi
+        self.halo_lo, self.halo_hi = int(halo_lo), int(halo_hi)
         self.t = 0
         self.device = "cpu"
 
@@ -78,12 +78,37 @@ class AAEngine:
     def check(self):
         pass
 
-    # halo protocol of include/hlbm.h
+    # halo protocol of include/hlbm.h: the halo plane next to each face and
+    # the slab's boundary plane (D halo planes on a face)
     def _plane_sign(self, face, import_):
         nz, odd = self.g.shape[1], self.t % 2 == 1
+        h_lo, b_lo = self.halo_lo - 1, self.halo_lo
+        h_hi, b_hi = nz - self.halo_hi, nz - self.halo_hi - 1
         if not import_:
-            return (1, +1) if face == 0 and odd else (0, -1) if face == 0 else (nz - 2, -1) if odd else (nz - 1, +1)
-        return (0, -1) if face == 0 and odd else (1, +1) if face == 0 else (nz - 1, +1) if odd else (nz - 2, -1)
+            if face == 0:
+                return (b_lo, +1) if odd else (h_lo, -1)
+            return (b_hi, -1) if odd else (h_hi, +1)
+        if face == 0:
+            return (h_lo, -1) if odd else (b_lo, +1)
+        return (h_hi, +1) if odd else (b_hi, -1)
+
+    def _deep_planes(self, face, import_):
+        nz = self.g.shape[1]
+        D = self.halo_lo if face == 0 else self.halo_hi
+        if face == 0:
+            return slice(0, D) if import_ else slice(D, 2 * D)
+        return slice(nz - D, nz) if import_ else slice(nz - 2 * D, nz - D)
+
+    def halo_deep_size(self, face):
+        D = self.halo_lo if face == 0 else self.halo_hi
+        return 19 * D * self.g.shape[2] * self.g.shape[3] * 8
+
+    def halo_deep_export(self, face, buf):
+        buf.numpy().view(np.float64)[:] = self.g[:, self._deep_planes(face, False)].ravel()
+
+    def halo_deep_import(self, face, buf):
+        sl = self._deep_planes(face, True)
+        self.g[:, sl] = buf.numpy().view(np.float64).reshape(self.g[:, sl].shape)
 
     def halo_size(self):
         return 5 * self.g.shape[2] * self.g.shape[3] * 8
@@ -154,15 +179,26 @@ def test_partition_avoids_rotor_boxes():
 
 def test_slab_specs_topology():
     s = slab_specs([0, 10, 30, 40], periodic_z=False)
-    assert [(x.halo_lo, x.halo_hi) for x in s] == [(False, True), (True, True), (True, False)]
+    assert [(x.halo_lo, x.halo_hi) for x in s] == [(0, 1), (1, 1), (1, 0)]
     assert [x.nz_local for x in s] == [11, 22, 11] and [x.z_offset for x in s] == [0, 9, 29]
     s = slab_specs([0, 10, 40], periodic_z=True)
-    assert [(x.halo_lo, x.halo_hi) for x in s] == [(True, True), (True, True)]
-    assert slab_specs([0, 40], periodic_z=True)[0].halo_lo is False
+    assert [(x.halo_lo, x.halo_hi) for x in s] == [(1, 1), (1, 1)]
+    assert slab_specs([0, 40], periodic_z=True)[0].halo_lo == 0
+    # a cut inside a rotor box gets deep halo planes on both sides
+    assert cuts_in_boxes([0, 30, 60, 96], [(20, 40)], 96, False) == {1}
+    assert cuts_in_boxes([0, 30, 60, 96], [(30, 40)], 96, False) == set()     # cut at the box's first plane
+    assert cuts_in_boxes([0, 48, 96], [(-5, 10)], 96, True) == {0}            # across the periodic face
+    s = slab_specs([0, 30, 60, 96], periodic_z=False, deep={1}, depth=4)
+    assert [(x.halo_lo, x.halo_hi) for x in s] == [(0, 4), (4, 1), (1, 0)]
+    assert [x.nz_local for x in s] == [34, 35, 37] and [x.z_offset for x in s] == [0, 26, 59]
+    s = slab_specs([0, 30, 60], periodic_z=True, deep={0}, depth=3)
+    assert [(x.halo_lo, x.halo_hi) for x in s] == [(3, 1), (1, 3)]
+    assert partition(96, 2, [(40, 55)], split_boxes=True) == [0, 48, 96]
+    assert deep_halo(2.0) == 4 and deep_halo(2.5) == 5
 
 
-def _slab_engines(g0, cuts, held):
-    specs = slab_specs(cuts, periodic_z=True)
+def _slab_engines(g0, cuts, held, deep=(), depth=1):
+    specs = slab_specs(cuts, periodic_z=True, deep=deep, depth=depth)
     nz = g0.shape[1]
     eng = {}
     for k in held:
@@ -172,9 +208,9 @@ def _slab_engines(g0, cuts, held):
     return specs, eng
 
 
-def _run_slabs(cuts, held, steps, rank_of=None, group=None, shape=(12, 5, 4)):
+def _run_slabs(cuts, held, steps, rank_of=None, group=None, shape=(12, 5, 4), deep=(), depth=1):
     g0 = _initial(shape)
-    specs, eng = _slab_engines(g0, cuts, held)
+    specs, eng = _slab_engines(g0, cuts, held, deep, depth)
     dom = SlabDomain(specs, eng, rank_of=rank_of, group=group, rotor_slab=[(k, 0) for k in range(len(specs))])
     dom.step(steps)
     return dom, specs
@@ -194,20 +230,60 @@ def test_local_slabs_equal_the_whole_lattice(cuts):
     assert abs(dom.mass() - whole.g.sum()) < 1e-12 * whole.g.sum()
 
 
+@pytest.mark.parametrize("cuts,deep,depth", [([0, 6, 12], {1}, 3), ([0, 5, 12], {0, 1}, 4),
+                                              ([0, 4, 8, 12], {2}, 2)])
+def test_deep_halos_carry_the_neighbours_state(cuts, deep, depth):
+    """Faces that cut a rotor box keep D halo planes, refilled after every
+    step (after the one-plane exchange) with every slot of the neighbour's
+    D planes next to the face, and before the first step.  Between steps:
+    the owned planes equal the undecomposed lattice, the deep halo planes
+    hold exactly the lattice's planes there (every slot), and the
+    pre-collision populations of the halo cells (every plane but the one
+    farthest from the face, whose odd-step populations sit one plane
+    further) equal the lattice's, at both parities: what the wall-model
+    sample and the force reduction read through the face."""
+    shape = (12, 5, 4)
+    nz = shape[0]
+    g0 = _initial(shape)
+    whole = AAEngine(g0)
+    specs, eng = _slab_engines(g0, cuts, range(len(cuts) - 1), deep, depth)
+    dom = SlabDomain(specs, eng)
+    for t in range(1, 9):
+        dom.step(1)
+        whole.step_async(1)
+        nat_w = _natural(whole.g, whole.t)
+        for sp in specs:
+            e = dom.engines[sp.k]
+            a = sp.halo_lo
+            assert np.array_equal(e.g[:, a:a + sp.z_hi - sp.z_lo], whole.g[:, sp.z_lo:sp.z_hi]), (t, sp)
+            nat_s = _natural(e.g, e.t)
+            for f, D in ((0, sp.halo_lo), (1, sp.halo_hi)):
+                if D < 2:
+                    continue
+                loc = range(0, D) if f == 0 else range(e.g.shape[1] - D, e.g.shape[1])
+                for zl in loc:
+                    zg = (zl + sp.z_offset) % nz
+                    assert np.array_equal(e.g[:, zl], whole.g[:, zg]), (t, sp, f, zl)
+                    farthest = zl == (0 if f == 0 else e.g.shape[1] - 1)
+                    if not farthest:
+                        assert np.array_equal(nat_s[:, zl], nat_w[:, zg]), (t, sp, f, zl)
+
+
 def _free_port():
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))
         return s.getsockname()[1]
 
 
-def _rank_main(rank, world, port, cuts, held_of, steps, out_dir):
+def _rank_main(rank, world, port, cuts, held_of, steps, out_dir, deep=(), depth=1):
     import torch.distributed as dist
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
         rank_of = [r for k in range(len(cuts) - 1) for r in range(world) if k in held_of[r]]
-        dom, specs = _run_slabs(cuts, held_of[rank], steps, rank_of=rank_of, group=dist.group.WORLD)
+        dom, specs = _run_slabs(cuts, held_of[rank], steps, rank_of=rank_of, group=dist.group.WORLD,
+                                deep=deep, depth=depth)
         F, Fa, M, Ma = dom.loads()
         res = {"mass": dom.mass(), "F": F, "M": M}
         for k in dom.held:
@@ -217,25 +293,34 @@ def _rank_main(rank, world, port, cuts, held_of, steps, out_dir):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("cuts,held_of", [([0, 6, 12], [[0], [1]]),
-                                          ([0, 3, 7, 12], [[0, 1], [2]])])
-def test_slabs_over_two_gloo_ranks(tmp_path, cuts, held_of):
+@pytest.mark.parametrize("cuts,held_of,deep,depth", [([0, 6, 12], [[0], [1]], (), 1),
+                                                     ([0, 3, 7, 12], [[0, 1], [2]], (), 1),
+                                                     ([0, 6, 12], [[0], [1]], {0, 1}, 3),
+                                                     ([0, 4, 8, 12], [[0, 2], [1]], {1}, 2)])
+def test_slabs_over_two_gloo_ranks(tmp_path, cuts, held_of, deep, depth):
     """Slabs split over two processes (gloo): messages between ranks through
-    torch.distributed point-to-point, between slabs of one rank by copies.
-    Every slab equals the undecomposed lattice bit for bit; the mass and the
-    per-rotor loads (one 'rotor' per slab here) are reduced over the ranks."""
+    torch.distributed point-to-point, between slabs of one rank by copies;
+    faces that cut a rotor box also move their deep messages (tagged apart
+    from the one-plane ones).  Every slab equals the undecomposed lattice bit
+    for bit, deep halos included; the mass and the per-rotor loads (one
+    'rotor' per slab here) are reduced over the ranks."""
     import torch.multiprocessing as mp
     steps = 9
-    mp.spawn(_rank_main, args=(2, _free_port(), cuts, held_of, steps, str(tmp_path)), nprocs=2, join=True)
+    mp.spawn(_rank_main, args=(2, _free_port(), cuts, held_of, steps, str(tmp_path), deep, depth), nprocs=2,
+             join=True)
     whole = AAEngine(_initial((12, 5, 4)))
     whole.step_async(steps)
-    specs = slab_specs(cuts, periodic_z=True)
+    specs = slab_specs(cuts, periodic_z=True, deep=deep, depth=depth)
     got = [dict(np.load(tmp_path / f"rank{r}.npz")) for r in range(2)]
     for r in range(2):
         for k in held_of[r]:
             s = specs[k]
             a = int(s.halo_lo)
             assert np.array_equal(got[r][f"g{k}"][:, a:a + s.z_hi - s.z_lo], whole.g[:, s.z_lo:s.z_hi])
+            # deep halo planes hold the neighbours' planes
+            for zl in list(range(s.halo_lo if s.halo_lo > 1 else 0)) + \
+                    list(range(s.nz_local - (s.halo_hi if s.halo_hi > 1 else 0), s.nz_local)):
+                assert np.array_equal(got[r][f"g{k}"][:, zl], whole.g[:, (zl + s.z_offset) % 12])
         assert abs(got[r]["mass"] - whole.g.sum()) < 1e-12 * whole.g.sum()
     assert np.array_equal(got[0]["F"], got[1]["F"]) and np.array_equal(got[0]["M"], got[1]["M"])
     assert got[0]["F"].shape == (len(specs), 3) and np.all(got[0]["F"][:, 1] == steps)
