@@ -404,7 +404,7 @@ hl_status hl_profile_end(hl_lattice* lat, double* ms, long long* launches);
  * slabs); its force reduction of a step runs at the next hl_step_async or
  * the next load query (hl_forces, hl_moments, hl_loads_async,
  * hl_save_state), which must come after the deep exchange.  A cut rotor
- * needs sigma_band = 1 (HL_ERR_ARG) and takes no hl_set_drive (HL_ERR_STATE). */
+ * takes no hl_set_drive (HL_ERR_STATE: its torque is split over the slabs). */
 
 /* Bytes of one halo message of this lattice (HL_ERR_ARG without halo planes). */
 hl_status hl_halo_size(const hl_lattice* lat, size_t* bytes);

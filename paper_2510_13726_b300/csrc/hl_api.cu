@@ -431,10 +431,6 @@ hl_status hl_set_rotor(hl_lattice* lat, int* rotor_id, const hl_rotor_geometry* 
     int lo[3], nn[3];
     bool clip[2];
     if (const char* why = rotor_box(lat, geom, lo, nn, clip)) return fail(lat, HL_ERR_ARG, why);
-    // a cut box: its band cells read the neighbouring slab's state only through
-    // the wall-model sample and the force reduction (no finite-difference strain)
-    if ((clip[0] || clip[1]) && lat->cfg.sigma_band < 1.0)
-        return fail(lat, HL_ERR_ARG, "a rotor box cut by a slab face needs sigma_band = 1");
     for (int k = 0; k < lat->nrot; ++k) {
         const RotorDev& o = lat->rot[k].dev;
         bool overlap = true;

@@ -767,9 +767,11 @@ __global__ void __launch_bounds__(128) band_strain_kernel(const StepArgs a) {
         const int by = (int)(r2 % R.n[1]);
         const int bz = (int)(r2 / R.n[1]);
         float* wm = R.wm + bi;
-        // the stencil must lie in the rotor box: the bulk launch updates every
-        // cell outside it at the same time
-        if (bx < 1 || by < 1 || bz < 1 || bx > R.n[0] - 2 || by > R.n[1] - 2 || bz > R.n[2] - 2) {
+        // the stencil must lie in the rotor box (the bulk launch updates every
+        // cell outside it at the same time), or along z through a slab face
+        // that cuts the box in the deep halo, which only the exchange writes
+        const int zc = R.lo[2] + bz;
+        if (bx < 1 || by < 1 || bx > R.n[0] - 2 || by > R.n[1] - 2 || zc - 1 < R.zs_lo || zc + 1 >= R.zs_hi) {
             atomicOr(a.err, ERR_GEOMETRY);
 #pragma unroll
             for (int k = 3; k < 9; ++k) wm[k * B] = 0.f;
