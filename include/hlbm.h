@@ -93,7 +93,8 @@ typedef int hl_status;
  *                  position 2x, cell x >= nx/2 at 2(x - nx/2) + 1; nx even):
  *                  the bulk launch then moves the cell pair (x, x + nx/2)
  *                  with one aligned access per slot at both step parities.
- *                  Same cell model; hl_grad takes 0 and 1 (HL_ERR_STATE for 2)
+ *                  Same cell model; hl_grad permutes layouts 1 and 2 into
+ *                  the AA layout of the same step for its sweep and back
  *  halo_lo, halo_hi  slab of a lattice decomposed along z (the domain
  *                  decomposition of the paper's multi-GPU runs, Sec. 5):
  *                  D > 0 makes the planes z < D (halo_lo) or z >= nz - D

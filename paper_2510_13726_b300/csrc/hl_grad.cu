@@ -106,6 +106,28 @@ __global__ void __launch_bounds__(128) relayout_kernel(const StepArgs a, const v
     }
 }
 
+// AA layout with x halves <-> AA layout: every stored value moves along its
+// x row, cell x's place 2x (x < nx/2) or 2(x - nx/2) + 1 <-> x (raw storage
+// words, either step parity)
+template <int S>
+__global__ void __launch_bounds__(128) xhalves_kernel(const StepArgs a, int q, const void* src, void* dst,
+                                                      int to_halves) {
+    using T = typename Store<S>::T;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
+    if (x >= a.n[0]) return;
+    const int hx = a.n[0] / 2;
+    const long long row = ((long long)z * a.n[1] + y) * a.n[0];
+    const long long xh = row + (x < hx ? 2 * x : 2 * (x - hx) + 1), xa = row + x;
+    const T* in = static_cast<const T*>(src);
+    T* out = static_cast<T*>(dst);
+    for (int s = 0; s < q; ++s) {
+        const long long b = (long long)s * a.N;
+        if (to_halves) out[b + xh] = in[b + xa];
+        else out[b + xa] = in[b + xh];
+    }
+}
+
 // lam*_s(x) = lam_{t+1, s}(x + c_s); the adjoint is zero on the open planes,
 // so the periodic index of a neighbour across an open face reads a zero
 template <int Q>
@@ -719,6 +741,14 @@ cudaError_t launch_relayout(int Q, int S, const StepArgs& a, const void* src, vo
     HL_ADJ_DISPATCH(Q, S, launch_relayout_t, a, src, dst, to_eso, s);
 }
 
+cudaError_t launch_xhalves(int Q, int S, const StepArgs& a, const void* src, void* dst, bool to_halves,
+                           cudaStream_t st) {
+    const dim3 grd((a.n[0] + 127) / 128, a.n[1], a.n[2]);
+    if (S == ST_F32) xhalves_kernel<ST_F32><<<grd, 128, 0, st>>>(a, Q, src, dst, to_halves ? 1 : 0);
+    else xhalves_kernel<ST_F16S><<<grd, 128, 0, st>>>(a, Q, src, dst, to_halves ? 1 : 0);   // 16-bit words
+    return cudaGetLastError();
+}
+
 // unit check of the packed bulk collision: cells 2k and 2k+1 of [n][q] in one thread
 template <int Q>
 __global__ void debug_collide_pair_kernel(int n, const float* gin, float tau_mo, float Ksmag, float* gout) {
@@ -909,7 +939,12 @@ hl_status join_aux(hl_lattice* lat) {
 // current step, through a scratch buffer of the gradient workspace
 hl_status relayout_state(hl_lattice* lat, void* scratch, bool to_eso) {
     const StepArgs a = make_args(lat);
-    HL_CUDA(lat, launch_relayout(lat->cfg.q, lat->cfg.storage, a, lat->f, scratch, to_eso, lat->stream));
+    if (lat->cfg.layout == 2) {
+        // the AA layout with x halves <-> the AA layout
+        HL_CUDA(lat, launch_xhalves(lat->cfg.q, lat->cfg.storage, a, lat->f, scratch, to_eso, lat->stream));
+    } else {
+        HL_CUDA(lat, launch_relayout(lat->cfg.q, lat->cfg.storage, a, lat->f, scratch, to_eso, lat->stream));
+    }
     HL_CUDA(lat, cudaMemcpyAsync(lat->f, scratch, (size_t)pop_bytes(lat), cudaMemcpyDeviceToDevice, lat->stream));
     return HL_OK;
 }
@@ -1153,20 +1188,21 @@ hl_status hl_grad(hl_lattice* lat, int steps, int avg_last, int ckpt_every, cons
     if (!lat) return HL_ERR_ARG;
     if (lat->cfg.halo_lo || lat->cfg.halo_hi)
         return fail(lat, HL_ERR_STATE, "hl_grad: the gradient covers a whole lattice, not a slab");
-    if (lat->cfg.layout == 2)
-        return fail(lat, HL_ERR_STATE, "hl_grad: the AA layout with x halves is not supported (use layout 0)");
     if (lat->cfg.layout == 0)
         return grad_aa(lat, steps, avg_last, ckpt_every, w_thrust, w_torque, J, dJ_dpitch, d_dJ_dd0, d_work, bytes);
-    // esoteric twist: the sweep runs on the AA form of the same state (the
-    // two layouts give the same trajectory); the adjoint arrays of the
-    // workspace, not yet or no longer in use, hold the permuted copy
+    // esoteric twist and the AA layout with x halves: the sweep runs on the
+    // AA form of the same state (the esoteric twist gives the same
+    // trajectory; with x halves the forward steps of the sweep take the AA
+    // layout's cell pairs); the adjoint arrays of the workspace, not yet or
+    // no longer in use, hold the permuted copy
     hl_status rc = grad_check(lat, steps, avg_last, ckpt_every, w_thrust, w_torque, d_work, bytes);
     if (rc != HL_OK) return rc;
     void* scratch = static_cast<char*>(d_work) + grad_layout(lat, steps, ckpt_every).lam;
     if ((rc = relayout_state(lat, scratch, false)) != HL_OK) return rc;
+    const int layout = lat->cfg.layout;
     lat->cfg.layout = 0;
     rc = grad_aa(lat, steps, avg_last, ckpt_every, w_thrust, w_torque, J, dJ_dpitch, d_dJ_dd0, d_work, bytes);
-    lat->cfg.layout = 1;
+    lat->cfg.layout = layout;
     // back at the step the lattice ended on, also after a failed sweep
     const hl_status rb = relayout_state(lat, scratch, true);
     if (rc != HL_OK) return rc;

@@ -6,7 +6,7 @@ path differs between the layouts (the x-halves launch also packs the rows on
 periodic y and z faces at odd steps), so the two agree to the rounding of
 the two paths.  The parity of this layout with the FP64 oracle is in
 test_gpu_rotor128.py; slabs in this layout equal the whole lattice bit for
-bit.
+bit; the gradient sweep runs on the AA form of the state.
 """
 
 import numpy as np
@@ -134,12 +134,28 @@ def test_slabs_with_x_halves_equal_the_lattice(P):
     dom.close()
 
 
-def test_gradient_refuses_x_halves(P):
-    """The discrete adjoint sweeps the AA layout (and the esoteric twist through
-    a permuted copy); a lattice with x halves gets HL_ERR_STATE."""
-    wl = Workload("halves_grad", 48, 48, 96, rotors=_single(48, 48, 96, 12.0, 6.0))
-    lat = P.Lattice.from_workload(wl, layout="aa_halves")
-    with pytest.raises(P.HlError) as e:
-        lat.grad(8, 4, [1.0], [0.0], ckpt_every=4)
-    assert e.value.code == -5
-    lat.close()
+@pytest.mark.parametrize("storage,q", [("f32", 19), ("bf16s", 19), ("f32", 27)])
+def test_gradient_in_x_halves_equals_aa(P, storage, q):
+    """hl_grad on a lattice with x halves permutes the state into the AA
+    layout of the same step for the sweep and back: from the same initial
+    state the objective equals the AA lattice's to 1e-12, the gradients to the
+    rounding of the reverse pass's atomic sums (1e-6), the fields after the
+    sweep bit for bit, and after three more steps in each layout to 1e-6."""
+    import torch
+    wl = Workload("halves_grad", 48, 48, 96, q=q, turbulence=0.05, rotors=_single(48, 48, 96, 12.0, 6.0))
+    out = []
+    for layout in ("aa", "aa_halves"):
+        lat = P.Lattice.from_workload(wl, layout=layout, storage=storage)
+        J, gp, gd = lat.grad(11, 5, [1.0], [0.3], ckpt_every=4)
+        u_after = lat.fields()[1][:, 1:-1].clone()
+        lat.step(3)
+        u_more = lat.fields()[1][:, 1:-1].clone()
+        out.append((J, float(gp[0]), gd.double().cpu().numpy(), u_after, u_more, lat.t))
+        lat.close()
+    (Ja, ga, da, ua, va, ta), (Jh, gh, dh, uh, vh, th) = out
+    assert th == ta == 14
+    assert abs(Jh - Ja) <= 1e-12 * abs(Ja)
+    assert abs(gh - ga) <= 1e-6 * abs(ga)
+    assert float(np.linalg.norm(dh - da) / np.linalg.norm(da)) <= 1e-6
+    assert torch.equal(uh, ua)
+    assert _rel(vh, va) <= (1e-6 if storage == "f32" else 2e-3)
