@@ -410,8 +410,8 @@ __global__ void __launch_bounds__(128, Q == 27 ? 8 : 10) collide_pair_kernel(con
 // is one aligned access at both step parities; only at the periodic wrap
 // (t = 0 reading / writing across x = 0, t = nx/2 - 1 across x = nx - 1)
 // the pair lies at the other end of the row with its two cells exchanged.
-// Rows on a periodic y or z face take the packed path too, with the wrapped
-// row offsets added per slot (a branch uniform over the row's warps).
+// Rows on a periodic y or z face take the packed path too (D3Q19), with the
+// wrapped row offsets added per slot (a branch uniform over the row's warps).
 // Same cell model as collide_pair_kernel (packed FP32x2 per lane).
 template <int Q, int S, int PH>
 __device__ __forceinline__ bool halves_plain(const StepArgs& a, int t, int y, int z) {
@@ -510,8 +510,18 @@ __global__ void __launch_bounds__(128, Q == 27 ? 8 : (S == ST_F16S ? 9 : 10)) co
         collide_cell<Q, S, PH, false, 0>(a, t + a.hx, y, z);
         return;
     }
-    if (PH == 1 && (y == 0 || y == a.n[1] - 1 || z == 0 || z == a.n[2] - 1)) halves_packed_faces<Q, S>(a, t, y, z);
-    else halves_packed<Q, S, PH, false>(a, t, y, z);
+    if (PH == 1 && (y == 0 || y == a.n[1] - 1 || z == 0 || z == a.n[2] - 1)) {
+        // D3Q27: the out-of-line call costs the packed path registers (spills at
+        // the 64-register cap), so its face rows take the per-cell path
+        if constexpr (Q == 19) {
+            halves_packed_faces<Q, S>(a, t, y, z);
+        } else {
+            collide_cell<Q, S, PH, false, 0>(a, t, y, z);
+            collide_cell<Q, S, PH, false, 0>(a, t + a.hx, y, z);
+        }
+        return;
+    }
+    halves_packed<Q, S, PH, false>(a, t, y, z);
 }
 
 // ---------------------------------------------------------------------------
