@@ -444,15 +444,17 @@ struct WrapOff {
 __device__ __forceinline__ int wrap_read(const WrapOff& o, int c) { return c > 0 ? o.lo : (c < 0 ? o.hi : 0); }
 __device__ __forceinline__ int wrap_write(const WrapOff& o, int c) { return c > 0 ? o.hi : (c < 0 ? o.lo : 0); }
 
-template <int Q, int S, int PH, bool YZ>
+// XW: the warp holds the first or the last pair of its row (the others need
+// neither the wrap offsets nor the byte permutations)
+template <int Q, int S, int PH, bool YZ, bool XW>
 __device__ __forceinline__ void halves_packed(const StepArgs& a, int t, int y, int z) {
     using T = typename Store<S>::T;
     const int w = (z * a.n[1] + y) * a.n[0] + 2 * t;   // the pair's position in a slot
     // x: the first pair reads (c_x = +1) and writes (c_x = -1) across x = 0,
     // the last pair reads (c_x = -1) and writes (c_x = +1) across x = nx - 1,
     // each at the row's other end with its cells exchanged
-    const WrapOff ox = {t == 0 ? a.n[0] : 0, t == a.hx - 1 ? -a.n[0] : 0};
-    const unsigned sel_lo = t == 0 ? SWAP2 : KEEP2, sel_hi = t == a.hx - 1 ? SWAP2 : KEEP2;
+    const WrapOff ox = {XW && t == 0 ? a.n[0] : 0, XW && t == a.hx - 1 ? -a.n[0] : 0};
+    const unsigned sel_lo = XW && t == 0 ? SWAP2 : KEEP2, sel_hi = XW && t == a.hx - 1 ? SWAP2 : KEEP2;
     WrapOff oy = {0, 0}, oz = {0, 0};
     if constexpr (YZ) {
         oy = {y == 0 ? a.nxy : 0, y == a.n[1] - 1 ? -a.nxy : 0};
@@ -467,10 +469,11 @@ __device__ __forceinline__ void halves_packed(const StepArgs& a, int t, int y, i
             g[s] = Store2<S>::ld(slot_ptr<Q, S>(a, s) + w);
             continue;
         }
-        int off = w + wrap_read(ox, cx);
+        int off = w;
+        if constexpr (XW) off += wrap_read(ox, cx);
         if constexpr (YZ) off += wrap_read(oy, cy) + wrap_read(oz, cz);
         const T* src = static_cast<const T*>(a.rshift[s]) + off;
-        if (cx == 0) g[s] = Store2<S>::ld(src);
+        if (cx == 0 || !XW) g[s] = Store2<S>::ld(src);
         else g[s] = Store2x<S>::ld(src, cx > 0 ? sel_lo : sel_hi);
     }
     F2 u[3];
@@ -483,10 +486,11 @@ __device__ __forceinline__ void halves_packed(const StepArgs& a, int t, int y, i
             Store2<S>::st(wslot_ptr<Q, S>(a, oslot(Q, s)) + w, g[s]);
             continue;
         }
-        int off = w + wrap_write(ox, cx);
+        int off = w;
+        if constexpr (XW) off += wrap_write(ox, cx);
         if constexpr (YZ) off += wrap_write(oy, cy) + wrap_write(oz, cz);
         T* dst = static_cast<T*>(a.wshift[s]) + off;
-        if (cx == 0) Store2<S>::st(dst, g[s]);
+        if (cx == 0 || !XW) Store2<S>::st(dst, g[s]);
         else Store2x<S>::st(dst, g[s], cx > 0 ? sel_hi : sel_lo);
     }
 }
@@ -494,7 +498,7 @@ __device__ __forceinline__ void halves_packed(const StepArgs& a, int t, int y, i
 // the face rows out of line: their extra offsets keep their registers to themselves
 template <int Q, int S>
 __device__ __noinline__ void halves_packed_faces(const StepArgs& a, int t, int y, int z) {
-    halves_packed<Q, S, 1, true>(a, t, y, z);
+    halves_packed<Q, S, 1, true, true>(a, t, y, z);
 }
 
 // Register caps: D3Q19 FP16 at 56 (9 blocks of 128 per SM), 2 % faster than
@@ -521,7 +525,14 @@ __global__ void __launch_bounds__(128, Q == 27 ? 8 : (S == ST_F16S ? 9 : 10)) co
         }
         return;
     }
-    halves_packed<Q, S, PH, false>(a, t, y, z);
+    // D3Q27 (18 x-shifted slots): only the warps holding a row's first or
+    // last pair take the wrap offsets and byte permutations (warps lie in
+    // one row: the block's x extent is a multiple of 32 threads); FP16
+    // rotor1024_q27 53.2k -> 54.6k MLUPS.  D3Q19 keeps one path for every
+    // warp (the split cost it 0.8 %).
+    const int t0 = t & ~31;
+    if (Q == 19 || (PH == 1 && (t0 == 0 || t0 + 31 >= a.hx - 1))) halves_packed<Q, S, PH, false, true>(a, t, y, z);
+    else halves_packed<Q, S, PH, false, false>(a, t, y, z);
 }
 
 // ---------------------------------------------------------------------------
