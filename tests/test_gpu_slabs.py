@@ -103,6 +103,22 @@ def test_rotor_box_cut_with_band_strain(P):
     _compare(P, W.workload("rotor48"), [0, 24, 96], 100, sigma_band=0.5)
 
 
+@pytest.mark.parametrize("q", [19, 27])
+def test_rotor_boxes_cut_with_z_periodic(P, q):
+    """Flow along x with z periodic (the farm's lateral direction): two rotors
+    whose boxes (planes 2..37 and 42..77) are each cut by a slab face, plus a
+    plain face at the periodic wrap; D3Q19 and D3Q27, 60 steps."""
+    R = 8.0
+    rot = [RotorSpec(center=(24.0, 23.5, 19.5), radius=R, tsr=6.0, phase0=0.3),
+           RotorSpec(center=(24.0, 23.5, 59.5), radius=R, tsr=6.0, phase0=1.9)]
+    wl = Workload("pair_x_cut", 95, 48, 80, q=q, flow_axis=0, turbulence=0.05, rotors=rot)
+    from paper_2510_13726_b300.slabs import rotor_z_extent
+    g = wl.blade_grids()[0]
+    ext = [rotor_z_extent(g, r.center, 0, wl.eps_h) for r in rot]
+    assert ext[0][0] < 20 <= ext[0][1] and ext[1][0] < 60 <= ext[1][1] and ext[0][0] > 0 and ext[1][1] < 80
+    _compare(P, wl, [0, 20, 60, 80], 60)
+
+
 def test_cut_rotor_box_rules(P):
     """A face that cuts a rotor box needs the deep halo (4 planes with y_s =
     2), no torque drive, and the deep import of every step (also before the
