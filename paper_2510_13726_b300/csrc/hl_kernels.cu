@@ -950,22 +950,30 @@ __global__ void evolve_kernel(const StepArgs a) {
 // ---------------------------------------------------------------------------
 // The mass total in fixed point.  B300's FP64 pipe is narrow (one FP64
 // addition per stored value ran the check at 2.5 ms on rotor256, six times
-// its memory time), so each stored value is turned into a multiple of 2^-56
-// (a binary32 scaling and one conversion) and summed in 128-bit integers; a
+// its memory time), so each stored value is turned, with integer
+// operations, into a multiple of 2^-56 and summed in 128-bit integers; a
 // thread's total goes to FP64 once and the block and grid sums are FP64.  A
 // value of magnitude below 8 is taken exactly down to 2^-56 (the bits below
 // are dropped: at most 2^-56 per value); anything larger, and inf or NaN,
 // is added in FP64 instead, so the check still sees it.
 constexpr int FIX_SHIFT = 56;
 
-// value * 2^56 as a signed 64-bit integer, truncated toward zero (|value| < 8),
-// or false when the value needs the FP64 path.  The product by a power of two
-// is exact in binary32 (|value| 2^56 < 2^59, and a subnormal value lands in the
-// normal range), and the conversion truncates: the bits below 2^-56 drop.
-__device__ __forceinline__ bool f32_fixed(float v, long long& out) {
-    if (!(fabsf(v) < 8.0f)) return false;                // |value| >= 8, inf, NaN
-    out = __float2ll_rz(v * 0x1p56f);
+// binary32 bits -> value * 2^56 as a signed 64-bit integer (|value| < 8),
+// or false when the value needs the FP64 path
+__device__ __forceinline__ bool f32_fixed(unsigned u, long long& out) {
+    const int eb = (int)((u >> 23) & 0xffu);
+    if (eb >= 130) return false;                        // |value| >= 8, inf, NaN
+    const long long m = (long long)((u & 0x7fffffu) | (eb ? 0x800000u : 0u));
+    const int sh = (eb ? eb : 1) - 150 + FIX_SHIFT;     // value = m * 2^((eb ? eb : 1) - 150)
+    const long long mag = sh >= 0 ? (m << sh) : (sh > -24 ? (m >> -sh) : 0);
+    out = (u >> 31) ? -mag : mag;
     return true;
+}
+
+template <int S>
+__device__ __forceinline__ unsigned stored_bits(typename Store<S>::T v) {
+    if constexpr (S == ST_F32) return __float_as_uint(v);
+    else return __float_as_uint(Store<S>::ld(&v));      // exact widening of FP16 / BF16
 }
 
 // Eight consecutive stored values (one 16-byte load for 16-bit storage, two
@@ -992,9 +1000,8 @@ __device__ __forceinline__ void sum8_fixed(const Group8<S>& grp, __int128& acc, 
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         long long x;
-        const float v = Store<S>::ld(h + k);             // exact widening of FP16 / BF16
-        if (f32_fixed(v, x)) g += x;
-        else side += (double)v;
+        if (f32_fixed(stored_bits<S>(h[k]), x)) g += x;
+        else side += (double)Store<S>::ld(h + k);
     }
     acc += (__int128)g;
 }
